@@ -1,0 +1,485 @@
+#!/usr/bin/env python
+"""Benchmark of the CGP Poisson path on the 512x256 O-grid (525,312 fine nodes).
+
+One step is one time step of the scale workload: a potential solve (Eq. 12:
+restrict + RHS, PCG to 1e-8, prolong, grad phi and j x B) and a pressure
+solve (Eq. 15: restrict + RHS, PCG to 1e-8, prolong, grad p), each warm-started
+from the previous step's solution, on a synthetic advected vortex train
+(B = k, N = 1).  The metric is CGP Poisson solves per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+Under torchrun every rank runs its own replica of the workload on its own GPU
+(the solves are independent; there is no collective on the data path), and
+rank 0 prints one JSON line with the whole-job rate (sum over ranks of the
+solves / max over ranks of the time).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CGP Poisson solves/s at 526k fine nodes to 1e-8 rel resid; SpMV GB/s vs peak"
+UNIT = "solves/s"
+N_THETA, N_R = 512, 256
+TOL = 1e-8
+SEED = 1
+STUART = 1.0
+B_FIELD = (0.0, 0.0, 1.0)
+RHO_OVER_DT = 20.0
+L2_FLUSH_BYTES = 512 << 20
+SPMV_MESH = (2048, 1024)       # > L2 in FP64 and FP32
+KERNELS_PER_STEP = 8           # 2 x (restrict_rhs, persistent PCG, prolong, lorentz)
+
+
+def workload_config(precision="fp64"):
+    return {"workload": f"CGP potential+pressure step, coarse O-grid {N_THETA}x{N_R} "
+                        f"(131,584 coarse / 525,312 fine nodes), advected vortex train, B=k, N=1",
+            "coarse_mesh": f"{N_THETA}x{N_R}", "fine_nodes": 525312, "coarse_nodes": 131584,
+            "solves_per_step": 2, "tol": TOL, "x0": "previous step", "precision": precision,
+            "l2": "flushed between timed steps (512 MiB write)", "seed": SEED}
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes of the persistent PCG launch (FP64 values, int32 indices)
+# ---------------------------------------------------------------------------
+def spmv_bytes(n, nnz, s=8):
+    """CSR y = A x: values + column indices + row pointers + x once + y."""
+    return nnz * (s + 4) + 4 * (n + 1) + 2 * s * n
+
+
+def pcg_iteration_bytes(n, nnz):
+    """One FP64 CG iteration as the kernel performs it.
+
+    A: read z, p; write p (24 n).  B: SpMV of p, write q (12 nnz + 4 n + 16 n).
+    C: read p, q, x, r, D^-1; write x, r, z (64 n).
+    """
+    return 12 * nnz + 108 * n
+
+
+def pcg_launch_bytes(iters, n, nnz):
+    """Set-up (means, projection, r0 = b - K x0) + iterations + final projection and true residual."""
+    setup = 16 * n + 32 * n + (12 * nnz + 4 * n + 8 * n) + 48 * n
+    final = 24 * n + (12 * nnz + 4 * n + 8 * n) + 8 * n
+    return setup + iters * pcg_iteration_bytes(n, nnz) + final
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_mine(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2003_00082_gb300 import build, cgp, inputs
+
+    build.build()
+    cgp.load()
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+
+    xy, tri = inputs.ogrid(N_THETA, N_R)
+    mesh = cgp.Mesh(xy, tri)
+    xy_f, _, _ = mesh.fine_geometry()
+    n, nnz = mesh.n_c, mesh.nnz
+    W, K = args.warmup, args.steps
+    total_steps = W + K
+
+    # host inputs: one velocity field per time step (pinned for the end-to-end pass)
+    U = torch.empty((total_steps, 2, mesh.n_f), dtype=torch.float64).pin_memory()
+    for k in range(total_steps):
+        u, v = inputs.velocity(xy_f, k, SEED, vortices=True)
+        U[k, 0].copy_(torch.from_numpy(u))
+        U[k, 1].copy_(torch.from_numpy(v))
+    Ud = U.to(dev)
+
+    f64 = dict(dtype=torch.float64, device=dev)
+    b = torch.empty(n, **f64)
+    phi_c = torch.zeros(n, **f64)
+    p_c = torch.zeros(n, **f64)
+    phi_f = torch.empty(mesh.n_f, **f64)
+    p_f = torch.empty(mesh.n_f, **f64)
+    force = torch.empty(2 * mesh.t_f, **f64)
+    grad_phi = torch.empty(2 * mesh.t_f, **f64)
+    grad_p = torch.empty(2 * mesh.t_f, **f64)
+    n_info = 2 * total_steps + 2 * K
+    infos = torch.zeros(n_info * cgp.INFO_BYTES, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    precision = cgp.CGP_MIXED if args.precision == "mixed" else cgp.CGP_FP64
+    info_addr = lambda slot: infos.data_ptr() + slot * cgp.INFO_BYTES  # noqa: E731
+
+    solve_events = []
+
+    def step(uf, vf, warm, slot, timing=False):
+        cgp.cgp_restrict(mesh.handle, cgp.CGP_RHS_POTENTIAL, B_FIELD, RHO_OVER_DT, uf, vf, b)
+        e0 = torch.cuda.Event(enable_timing=True) if timing else None
+        e1 = torch.cuda.Event(enable_timing=True) if timing else None
+        if timing:
+            e0.record(stream)
+        cgp.cgp_poisson_solve_async(mesh.handle, b, phi_c, tol=TOL, use_x0=warm, precision=precision,
+                                    info_dev=info_addr(slot))
+        if timing:
+            e1.record(stream)
+            solve_events.append((e0, e1))
+        cgp.cgp_prolong(mesh.handle, phi_c, phi_f)
+        cgp.cgp_lorentz(mesh.handle, phi_f, uf, vf, B_FIELD, STUART, grad_phi, force)
+        cgp.cgp_restrict(mesh.handle, cgp.CGP_RHS_PRESSURE, B_FIELD, RHO_OVER_DT, uf, vf, b)
+        e2 = torch.cuda.Event(enable_timing=True) if timing else None
+        e3 = torch.cuda.Event(enable_timing=True) if timing else None
+        if timing:
+            e2.record(stream)
+        cgp.cgp_poisson_solve_async(mesh.handle, b, p_c, tol=TOL, use_x0=warm, precision=precision,
+                                    info_dev=info_addr(slot + 1))
+        if timing:
+            e3.record(stream)
+            solve_events.append((e2, e3))
+        cgp.cgp_prolong(mesh.handle, p_c, p_f)
+        cgp.cgp_lorentz(mesh.handle, p_f, None, None, B_FIELD, STUART, grad_p, None)
+
+    # ---- warm-up ----
+    for k in range(W):
+        step(Ud[k, 0], Ud[k, 1], k > 0, 2 * k)
+    torch.cuda.synchronize()
+    phi_keep, p_keep = phi_c.clone(), p_c.clone()
+
+    # ---- timed, inputs resident in HBM ----
+    step_events = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clocks:
+        for j in range(K):
+            k = W + j
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(Ud[k, 0], Ud[k, 1], k > 0, 2 * k, timing=True)
+            e1.record(stream)
+            step_events.append((e0, e1))
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(c) for a, c in step_events]
+    solve_ms = [a.elapsed_time(c) for a, c in solve_events]
+    dev_ms = sum(step_ms)
+
+    # ---- end to end: pinned host inputs in, fine-mesh results out, every step ----
+    phi_c.copy_(phi_keep)
+    p_c.copy_(p_keep)
+    out_host = torch.empty((K, 2, 2 * mesh.t_f), dtype=torch.float64).pin_memory()
+    uf_d = torch.empty(mesh.n_f, **f64)
+    vf_d = torch.empty(mesh.n_f, **f64)
+    e2e_events = []
+    torch.cuda.synchronize()
+    for j in range(K):
+        k = W + j
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        uf_d.copy_(U[k, 0], non_blocking=True)
+        vf_d.copy_(U[k, 1], non_blocking=True)
+        step(uf_d, vf_d, k > 0, 2 * total_steps + 2 * j)
+        out_host[j, 0].copy_(force, non_blocking=True)
+        out_host[j, 1].copy_(grad_p, non_blocking=True)
+        e1.record(stream)
+        e2e_events.append((e0, e1))
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(c) for a, c in e2e_events)
+    h2d = 2 * mesh.n_f * 8
+    d2h = 2 * 2 * mesh.t_f * 8
+
+    # ---- outcome of every solve ----
+    recs = cgp.decode_infos(bytes(infos.cpu().numpy()), n_info)
+    timed = recs[2 * W: 2 * total_steps]
+    bad = [r for r in recs[: 2 * total_steps] + recs[2 * total_steps:] if r["status"] != cgp.CGP_OK]
+    if bad:
+        raise RuntimeError(f"{len(bad)} solves did not converge: {bad[:3]}")
+    its = [r["iterations"] for r in timed]
+
+    # ---- roofline of the dominant kernel (the persistent PCG launch) ----
+    peak, peak_kind = read_peaks()
+    alg_bytes = [pcg_launch_bytes(i if precision == cgp.CGP_FP64 else 0, n, nnz) for i in its]
+    pcg_total_ms = sum(solve_ms)
+    achieved = sum(alg_bytes) / (pcg_total_ms * 1e-3) / 1e9
+
+    result = dict(dev_ms=dev_ms, e2e_ms=e2e_ms, solves=2 * K, step_ms=step_ms, solve_ms=solve_ms, its=its,
+                  achieved=achieved, alg_bytes_per_launch=sum(alg_bytes) / len(alg_bytes),
+                  pcg_share=pcg_total_ms / dev_ms, clocks=clocks.summary(), peak=peak, peak_kind=peak_kind,
+                  h2d=h2d, d2h=d2h, n=n, nnz=nnz,
+                  rel_res_true_max=max(r["rel_res_true"] for r in timed))
+
+    if rank == 0 and not args.no_spmv:
+        result["spmv"] = spmv_bench(cgp, inputs, torch, dev, flush, peak)
+    mesh.close()
+    return result
+
+
+def spmv_bench(cgp, inputs, torch, dev, flush, peak, reps=15):
+    """SpMV y = K x on a matrix larger than L2, every lanes-per-row choice, FP64 and FP32."""
+    xy, tri = inputs.ogrid(*SPMV_MESH)
+    m = cgp.Mesh(xy, tri)
+    n, nnz = m.n_c, m.nnz
+    out = {"matrix": f"P1 Laplacian of a {SPMV_MESH[0]}x{SPMV_MESH[1]} O-grid", "n": n, "nnz": nnz}
+    for prec, dt, s, what in ((cgp.CGP_FP64, torch.float64, 8, cgp.CGP_TUNE_SPMV_FP64),
+                              (cgp.CGP_FP32, torch.float32, 4, cgp.CGP_TUNE_SPMV_FP32)):
+        x = torch.randn(n, dtype=dt, device=dev)
+        y = torch.empty(n, dtype=dt, device=dev)
+        bytes_ = spmv_bytes(n, nnz, s)
+        per = {}
+        for lanes in (1, 2, 4, 8, 32):
+            cgp.cgp_set_tuning(m.handle, what, 256, lanes, 0)
+            times = []
+            for r in range(reps + 2):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                cgp.cgp_spmv(m.handle, prec, x, y)
+                e1.record()
+                torch.cuda.synchronize()
+                if r >= 2:
+                    times.append(e0.elapsed_time(e1))
+            per[lanes] = statistics.median(times)
+        best = min(per, key=per.get)
+        gbs = bytes_ / (per[best] * 1e-3) / 1e9
+        key = "fp64" if prec == cgp.CGP_FP64 else "fp32"
+        out[key] = {"best_lanes": best, "ms": per[best], "gb_s": gbs, "frac": gbs / peak,
+                    "bytes": bytes_, "ms_by_lanes": per}
+    m.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(n_solves_timed=2, warm_steps=1):
+    """Time the oracle as it stands on the 512x256 workload: one warm time step = 2 solves."""
+    import numpy as np
+
+    from oracle import cgp_oracle as O
+    from paper_2003_00082_gb300 import inputs
+
+    xy, tri = inputs.ogrid(N_THETA, N_R)
+    om = O.OracleMesh(xy, tri)
+    x_phi = x_p = None
+    times = []
+    for k in range(warm_steps + 1):
+        u, v = inputs.velocity(om.xy_f, k, SEED, vortices=True)
+        t0 = time.perf_counter()
+        r1 = om.solve(u, v, O.POTENTIAL, B=B_FIELD, sigma=STUART, rho_over_dt=RHO_OVER_DT, tol=TOL, x0=x_phi)
+        r2 = om.solve(u, v, O.PRESSURE, B=B_FIELD, sigma=STUART, rho_over_dt=RHO_OVER_DT, tol=TOL, x0=x_p)
+        t1 = time.perf_counter()
+        x_phi, x_p = r1["phi_c"], r2["phi_c"]
+        times.append(t1 - t0)
+        assert r1["status"] == O.OK and r2["status"] == O.OK
+    secs = times[-1]
+    return {"value": 2.0 / secs, "seconds": secs, "iterations": [r1["iterations"], r2["iterations"]]}
+
+
+def cpu_baseline_subprocess():
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample"], env=env,
+                       capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one warm time step (potential + pressure solve, previous-step x0) of the 512x256 "
+                      "workload after one untimed step; numpy/scipy FP64, single thread",
+            "iterations": d["iterations"]}
+
+
+def run_reference(args, rank):
+    """The reference arm: the CPU oracle as it stands, one CGP solve per step."""
+    if rank != 0:
+        return
+    from oracle import cgp_oracle as O
+    from paper_2003_00082_gb300 import inputs
+
+    xy, tri = inputs.ogrid(N_THETA, N_R)
+    om = O.OracleMesh(xy, tri)
+    x0 = {O.POTENTIAL: None, O.PRESSURE: None}
+    vel = None
+    timed = 0.0
+    for s in range(args.warmup + args.steps):
+        kind = O.POTENTIAL if s % 2 == 0 else O.PRESSURE
+        if kind == O.POTENTIAL:
+            vel = inputs.velocity(om.xy_f, s // 2, SEED, vortices=True)
+        t0 = time.perf_counter()
+        r = om.solve(vel[0], vel[1], kind, B=B_FIELD, sigma=STUART, rho_over_dt=RHO_OVER_DT, tol=TOL,
+                     x0=x0[kind])
+        t1 = time.perf_counter()
+        x0[kind] = r["phi_c"]
+        if s >= args.warmup:
+            timed += t1 - t0
+    value = args.steps / timed
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * timed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config("fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} CGP solves (alternating potential/pressure, "
+                                       f"previous-step x0) of the 512x256 workload, one per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-spmv", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample()), flush=True)
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(v, "1")
+        run_reference(args, rank)
+        return
+
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_subprocess()     # before any GPU work in this process
+
+    res = run_mine(args, rank, world, local_rank)
+    dev_ms, e2e_ms = res["dev_ms"], res["e2e_ms"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=f"cuda:{local_rank}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms, e2e_ms = float(t[0]), float(t[1])
+    total_solves = res["solves"] * world
+    if rank == 0:
+        peak = res["peak"]
+        line = {
+            "metric": METRIC, "value": total_solves / (dev_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic", "config": workload_config(args.precision),
+            "roofline": {"bound": "hbm", "achieved": res["achieved"], "peak": peak, "unit": "GB/s",
+                         "frac": res["achieved"] / peak, "traffic": None,
+                         "kernel": "pcg_persistent_kernel",
+                         "alg_bytes_per_launch": res["alg_bytes_per_launch"],
+                         "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({res['peak_kind']})",
+                         "kernel_share_of_step": res["pcg_share"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": total_solves / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
+                    "d2h_bytes_per_step": res["d2h"]},
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "clocks": res["clocks"],
+            "iterations": {"per_solve_mean": statistics.mean(res["its"]), "min": min(res["its"]),
+                           "max": max(res["its"]), "rel_res_true_max": res["rel_res_true_max"]},
+        }
+        if "spmv" in res:
+            line["spmv"] = res["spmv"]
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * cgp.h - C ABI of the GB300 coarse-grid projection (CGP) Poisson library.
+ *
+ * The library implements the per-time-step hot path of the CGP method for
+ * incompressible MHD (Kashefi, "A coarse-grid projection method for
+ * accelerating incompressible MHD flow simulations", Sect. 2.2-2.3):
+ *
+ *   restrict u_f -> u_c (Eq. 19), form the Poisson right-hand side
+ *   (Eq. 12 potential, Eq. 15 pressure), solve the P1 Laplacian by
+ *   Jacobi-preconditioned CG, prolong the solution back (Eq. 20), and form
+ *   grad(phi) and the Lorentz force j x B per fine triangle (Eqs. 4, 7, 13-14).
+ *
+ * Conventions shared by every call
+ *   - Every function returns a cgp_status; nothing throws and no kernel traps.
+ *     cgp_last_error() gives a human-readable message for the calling thread.
+ *   - "device" pointers are CUDA device (or managed) pointers on the device
+ *     that was current when the mesh was assembled; "host" pointers are plain
+ *     host memory.  The caller owns every buffer it passes; the library owns
+ *     the mesh data and solver scratch it allocates in cgp_assemble and frees
+ *     in cgp_mesh_destroy.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream) unless stated otherwise.
+ *   - Solver scratch lives in the mesh: two solves on the same mesh must not
+ *     overlap on the GPU (use one stream per mesh, or one mesh per stream).
+ *   - Vectors are contiguous FP64 arrays; index i of a coarse vector is
+ *     coarse node i.
+ *
+ * Fine-mesh numbering (the 4-way split of Sect. 2.3, Eq. 18 with k = 1)
+ *   - fine nodes [0, n_c) are the coarse nodes; fine node n_c + e is the
+ *     midpoint of coarse edge e, edges sorted by (min vertex, max vertex);
+ *   - fine triangle 4T + c of coarse triangle T = (a, b, c) is child c of
+ *     (a, m_ab, m_ca), (m_ab, b, m_bc), (m_ca, m_bc, c), (m_ab, m_bc, m_ca).
+ *   Injection (Eq. 19) is therefore the prefix q_f[0, n_c).
+ */
+#ifndef CGP_H
+#define CGP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CGP_OK = 0,
+  CGP_ERR_INVALID_ARG = 1,   /* bad handle, size, pointer or option */
+  CGP_ERR_CUDA = 2,          /* a CUDA runtime call failed (message says which) */
+  CGP_ERR_NOT_CONVERGED = 3, /* max_it reached; x holds the last iterate */
+  CGP_ERR_BREAKDOWN = 4,     /* p.Kp <= 0: the matrix is not positive on the Krylov space */
+  CGP_ERR_NONFINITE = 5,     /* NaN or Inf met in b, x0 or a reduction */
+  CGP_ERR_TIMEOUT = 6,       /* a grid barrier of the persistent solver gave up */
+  CGP_ERR_OOM = 7            /* device allocation failed */
+} cgp_status;
+
+typedef struct cgp_mesh_s* cgp_mesh;
+
+typedef enum { CGP_RHS_POTENTIAL = 0, CGP_RHS_PRESSURE = 1 } cgp_rhs_kind;
+typedef enum { CGP_FP64 = 0, CGP_MIXED = 1 } cgp_precision;
+
+typedef struct {
+  double tol;          /* stop when ||b - K x||_2 <= tol ||b||_2 (b after mean projection) */
+  int max_it;          /* FP64: PCG iteration cap; MIXED: cap on the total inner iterations */
+  int precision;       /* cgp_precision */
+  double inner_tol;    /* MIXED: relative residual reduction of each FP32 inner solve */
+  int use_x0;          /* 1: x holds the initial guess on entry; 0: start from zero */
+  int max_sweeps;      /* MIXED: cap on refinement sweeps (<= 0 selects 50) */
+} cgp_solve_opts;
+
+typedef struct {
+  int iterations;            /* PCG iterations (MIXED: inner iterations summed) */
+  int outer_sweeps;          /* MIXED: refinement sweeps; FP64: 0 */
+  double rel_res_recursive;  /* FP64: recursive-residual norm / ||b||; MIXED: as rel_res_true */
+  double rel_res_true;       /* ||b - K x|| / ||b|| of the returned x */
+  int status;                /* cgp_status of the solve */
+} cgp_solve_info;
+
+/*
+ * cgp_assemble - build a mesh pair and its Galerkin P1 operators (Sect. 2.3).
+ *
+ * xy_c   host, [n_c][2] coarse node coordinates (FP64, interleaved x, y).
+ * tri_c  host, [t_c][3] coarse triangles, counter-clockwise, 0-based.
+ * levels coarsening levels between the fine and the coarse mesh; only k = 1
+ *        (one uniform 4-way split) is supported.
+ * out    receives the handle.
+ *
+ * Builds the fine mesh by the numbering above, the CSR pattern of the coarse
+ * node graph (columns ascending), and on the GPU: K_ij = int grad psi_i .
+ * grad psi_j, Gx_ij = int psi_j d_x psi_i, Gy_ij = int psi_j d_y psi_i,
+ * D^-1 = 1/K_ii (FP64 and FP32 copies) and the fine node coordinates.
+ * Blocks until the device data is ready.  Inputs are copied; the caller may
+ * free them afterwards.  Errors: INVALID_ARG for sizes <= 0, indices out of
+ * range, clockwise or degenerate triangles, or levels != 1; OOM; CUDA.
+ */
+int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t_c, int levels,
+                 cgp_mesh* out);
+
+/* Sizes of a mesh pair; any output pointer may be NULL.  nnz counts K's pattern. */
+int cgp_mesh_query(cgp_mesh m, int* n_c, int* t_c, int* n_e, int* n_f, int* t_f, int* nnz);
+
+/*
+ * cgp_mesh_fine_geometry - host copies of the fine mesh (synchronous).
+ * xy_f  host [n_f][2] or NULL;  tri_f host [t_f][3] or NULL;  edges host [n_e][2] or NULL.
+ */
+int cgp_mesh_fine_geometry(cgp_mesh m, double* xy_f, int* tri_f, int* edges);
+
+/*
+ * cgp_mesh_matrices - host copies of the assembled coarse operators (synchronous).
+ * rowptr [n_c+1], col [nnz], K/Gx/Gy [nnz], dinv [n_c]; any may be NULL.
+ */
+int cgp_mesh_matrices(cgp_mesh m, int* rowptr, int* col, double* K, double* Gx, double* Gy,
+                      double* dinv);
+
+/*
+ * cgp_restrict - restriction by injection (Eq. 19) fused with the Poisson
+ * right-hand side on the coarse mesh (Eq. 12 / Eq. 15 in weak form).
+ *
+ * kind        CGP_RHS_POTENTIAL: F = (u x B) in the x-y plane = (v B_z, -u B_z),
+ *             the source of Delta phi = div(u x B) (Eqs. 5, 6, 12).
+ *             CGP_RHS_PRESSURE: F = rho_over_dt * (u, v), the source of
+ *             Delta p = (rho/dt) div(u~) (Eqs. 9, 15).
+ * B           host [3], the magnetic field (only B_z enters F).
+ * u_f, v_f    device [n_f] fine-node velocity components.
+ * u_c, v_c    device [n_c] restricted velocity, or NULL to skip writing it.
+ * b           device [n_c] output: b_i = sum_j Gx_ij F_x,j + Gy_ij F_y,j
+ *             = int F . grad psi_i, the weak form of Delta x = div F with the
+ *             natural condition d_n x = F . n.  b is not projected; the solver
+ *             removes its mean.
+ */
+int cgp_restrict(cgp_mesh m, int kind, const double* B, double rho_over_dt,
+                 const double* u_f, const double* v_f, double* u_c, double* v_c, double* b,
+                 void* stream);
+
+/*
+ * cgp_poisson_solve - Jacobi-preconditioned CG on the singular Neumann system
+ * K x = b (the coarse Poisson solve of CGP steps 2 and 6, Eqs. 12 and 15).
+ *
+ * b     device [n_c] right-hand side (not modified).
+ * x     device [n_c]: the initial guess on entry when opts->use_x0, else
+ *       ignored; the mean-zero solution on exit.
+ * opts  host; NULL selects tol 1e-8, max_it 20000, FP64, x0 = 0.
+ * info  host or NULL.  When non-NULL the call synchronises the stream once to
+ *       read the solver state and returns the solve's status; when NULL the
+ *       call is fully asynchronous and returns CGP_OK after the launch.
+ *
+ * b and x0 are projected to mean zero (the null space of K is the
+ * constants), CG runs on the projected system, and the result is projected
+ * again.  FP64 runs plain PCG in FP64.  MIXED runs FP64 iterative refinement
+ * (residual b - K x, correction sum and projection in FP64) around FP32 inner
+ * PCG solves to inner_tol.  The whole solve is one persistent cooperative
+ * kernel launch; its grid barriers give up after about two seconds without
+ * progress and report CGP_ERR_TIMEOUT.  Not-converged is non-fatal: x holds
+ * the last iterate.
+ */
+int cgp_poisson_solve(cgp_mesh m, const double* b, double* x, const cgp_solve_opts* opts,
+                      cgp_solve_info* info, void* stream);
+
+/*
+ * cgp_poisson_solve_async - cgp_poisson_solve without any host synchronisation.
+ *
+ * Same arguments and semantics, except that the outcome is written by the
+ * GPU into info_dev, a device pointer to one cgp_solve_info record (or NULL
+ * to discard it): status CGP_ERR_TIMEOUT if a barrier gave up, else the
+ * solve's status.  The call returns after the launch; host-side argument
+ * errors are still returned immediately.  Suitable for back-to-back solves
+ * and for stream capture.
+ */
+int cgp_poisson_solve_async(cgp_mesh m, const double* b, double* x, const cgp_solve_opts* opts,
+                            cgp_solve_info* info_dev, void* stream);
+
+/*
+ * cgp_prolong - prolongation by the P1 shape functions (Eq. 20) for one level:
+ * x_f[i] = x_c[i] for coarse nodes, x_f[n_c + e] = (x_c[a_e] + x_c[b_e]) / 2 at
+ * the midpoint of edge e (shape functions 1/2, 1/2, 0 there).
+ * x_c device [n_c]; x_f device [n_f].
+ */
+int cgp_prolong(cgp_mesh m, const double* x_c, double* x_f, void* stream);
+
+/*
+ * cgp_lorentz - gradient, current density and Lorentz force per fine triangle.
+ *
+ * For fine triangle t: g = grad phi_f (constant on P1), u_bar = vertex mean of
+ * (u_f, v_f), j = sigma (-g + u_bar x B) (Ohm's law, Eqs. 4 and 7, with
+ * g_z = u_z = 0), f = j x B (the source of Eqs. 2 and 8; with B = B_o k it is
+ * the right-hand side of Eqs. 13-14).
+ * phi_f, u_f, v_f  device [n_f].
+ * B                host [3].
+ * grad             device [2 * t_f], SoA: g_x for all triangles, then g_y.
+ * force            device [2 * t_f], SoA: f_x then f_y; NULL computes only grad
+ *                  (the pressure gradient of Eqs. 16-17).
+ */
+int cgp_lorentz(cgp_mesh m, const double* phi_f, const double* u_f, const double* v_f,
+                const double* B, double sigma, double* grad, double* force, void* stream);
+
+/*
+ * cgp_spmv - y = K x with the coarse stiffness matrix (the product inside
+ * every CG iteration).  precision CGP_FP64: x, y device double [n_c];
+ * precision 1 (FP32): x, y device float [n_c] with the FP32 copy of K.
+ */
+int cgp_spmv(cgp_mesh m, int precision, const void* x, void* y, void* stream);
+
+/*
+ * cgp_set_tuning / cgp_get_tuning - launch shape of a kernel family on this mesh.
+ *
+ * what    CGP_TUNE_SOLVE_FP64, CGP_TUNE_SOLVE_MIXED (the persistent solver),
+ *         CGP_TUNE_SPMV_FP64, CGP_TUNE_SPMV_FP32 (cgp_spmv).
+ * block   threads per block: a multiple of 32 in [64, 1024]; 0 = default.
+ * lanes   threads cooperating on one CSR row: 1, 2, 4, 8 or 32 (32 is one
+ *         warp per row); 0 = default.
+ * blocks  solver: blocks of the persistent grid (clamped to what can be
+ *         co-resident); SpMV: grid size; 0 = chosen from the size.
+ * Invalid shapes are rejected with INVALID_ARG.  cgp_autotune sets these.
+ */
+typedef enum {
+  CGP_TUNE_SOLVE_FP64 = 0,
+  CGP_TUNE_SOLVE_MIXED = 1,
+  CGP_TUNE_SPMV_FP64 = 2,
+  CGP_TUNE_SPMV_FP32 = 3
+} cgp_tune_target;
+
+int cgp_set_tuning(cgp_mesh m, int what, int block, int lanes, int blocks);
+int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks);
+
+/*
+ * cgp_barrier_selftest - exercise the persistent solver's grid barrier.
+ * Launches nblk co-resident blocks (1 <= nblk <= 1024) of which the last
+ * `absent` never arrive; the others give up after spin_ns nanoseconds and the
+ * call returns CGP_ERR_TIMEOUT, or CGP_OK when absent == 0.  The GPU context
+ * stays usable either way.  Synchronises the stream.
+ */
+int cgp_barrier_selftest(int nblk, int absent, long long spin_ns, void* stream);
+
+/* Frees the mesh and its device memory (synchronises the device first). */
+int cgp_mesh_destroy(cgp_mesh m);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* cgp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CGP_H */

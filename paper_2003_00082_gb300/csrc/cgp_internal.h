@@ -1,0 +1,105 @@
+// Internal declarations shared by the translation units of libcgp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cgp.h"
+
+namespace cgp {
+
+// thread-local error message; returns the status so callers can `return fail(...)`
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define CGP_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return ::cgp::cuda_fail(e_, #call); \
+  } while (0)
+
+// Result record of one solve, written by the persistent kernel.
+struct SolveResult {
+  int iterations;
+  int sweeps;
+  int status;
+  int timeout;       // set by a block whose barrier gave up
+  double rel_rec;
+  double rel_true;
+  double bnorm;
+};
+
+// Tuning of the persistent solver launch (chosen by the autotuner or defaults).
+struct SolverTuning {
+  int block;          // threads per block
+  int lanes;          // lanes per CSR row in the SpMV phases (1, 2, 4, 8)
+  int blocks;         // blocks per instance (0 = all co-resident blocks)
+};
+
+struct cgp_mesh_impl {
+  int device = 0;
+  int n_c = 0, t_c = 0, n_e = 0, n_f = 0, t_f = 0, nnz = 0;
+
+  // host copies of the integer structure
+  std::vector<int> h_rowptr, h_col, h_tri_c, h_edges, h_tri_mid;
+
+  // one device allocation carved into the arrays below
+  void* d_base = nullptr;
+  size_t d_bytes = 0;
+
+  int* rowptr = nullptr;     // [n_c + 1]
+  int* col = nullptr;        // [nnz]
+  double* K = nullptr;       // [nnz]
+  double* Gx = nullptr;      // [nnz]
+  double* Gy = nullptr;      // [nnz]
+  double* dinv = nullptr;    // [n_c]
+  float* K32 = nullptr;      // [nnz]
+  float* dinv32 = nullptr;   // [n_c]
+  int* tri_c = nullptr;      // [t_c * 3]
+  int* tri_mid = nullptr;    // [t_c * 3]: fine indices of m_ab, m_bc, m_ca
+  int* edges = nullptr;      // [n_e * 2]
+  double* xy_f = nullptr;    // [n_f * 2] interleaved
+  double* xy_c = nullptr;    // [n_c * 2]
+  int* inc_ptr = nullptr;    // [n_c + 1] node -> incident triangles
+  int* inc_tri = nullptr;    // [3 t_c] triangle * 4 + local vertex
+
+  // solver scratch
+  double* bp = nullptr;      // projected b
+  double* r = nullptr;
+  double* z = nullptr;
+  double* p = nullptr;
+  double* q = nullptr;
+  float* r32 = nullptr;
+  float* z32 = nullptr;
+  float* p32 = nullptr;
+  float* q32 = nullptr;
+  float* d32 = nullptr;
+  double* part = nullptr;    // [max_blocks * 4] per-block partial sums
+  unsigned* bar = nullptr;   // grid barrier counter
+  SolveResult* res = nullptr;
+  SolveResult* h_res = nullptr;  // pinned host mirror
+  int max_blocks = 0;
+
+  SolverTuning tune[4] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // indexed by cgp_tune_target
+};
+
+// ---- launchers implemented in the .cu files ----
+int launch_assemble_values(cgp_mesh_impl* m, cudaStream_t s);
+int launch_restrict_rhs(cgp_mesh_impl* m, int kind, double bz, double rho_over_dt,
+                        const double* u_f, const double* v_f, double* u_c, double* v_c,
+                        double* b, cudaStream_t s);
+int launch_prolong(cgp_mesh_impl* m, const double* xc, double* xf, cudaStream_t s);
+int launch_lorentz(cgp_mesh_impl* m, const double* phi, const double* u, const double* v,
+                   const double B[3], double sigma, double* grad, double* force, cudaStream_t s);
+int launch_spmv(cgp_mesh_impl* m, int precision, const void* x, void* y, cudaStream_t s);
+int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opts& o,
+                 cgp_solve_info* info_dev, cudaStream_t s);
+int solver_max_blocks(int device);
+
+}  // namespace cgp
+
+struct cgp_mesh_s : public cgp::cgp_mesh_impl {};
