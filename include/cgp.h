@@ -166,6 +166,32 @@ int cgp_poisson_solve_async(cgp_mesh m, const double* b, double* x, const cgp_so
                             cgp_solve_info* info_dev, void* stream);
 
 /*
+ * cgp_poisson_solve_noalloc - FP64 solve that allocates no memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc when they solve (an application that hands all
+ * device memory to its own pool or arena, a host framework whose allocator
+ * must not be bypassed, a real-time loop where allocating, and the
+ * synchronisation it can imply, is not allowed).  The caller passes the CSR
+ * system K (rowptr [n+1], col [nnz], K [nnz], D^-1 [n], all device, e.g.
+ * copied out with cgp_mesh_matrices) and b, x as in cgp_poisson_solve; the
+ * solver's scratch is a static array inside the library, sized for
+ * n <= CGP_STATIC_MAX_ROWS (65,536 rows, about 2.7 MB held on every GPU that
+ * loads the library until the process exits).  Larger n is rejected with
+ * CGP_ERR_INVALID_ARG.  Only opts->precision == CGP_FP64 is accepted.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * race on it, so serialise them (one stream, one host thread at a time).
+ * info behaves as in cgp_poisson_solve (NULL: asynchronous).
+ */
+#define CGP_STATIC_MAX_ROWS 65536
+int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* col, const double* K,
+                              const double* dinv, const double* b, double* x,
+                              const cgp_solve_opts* opts, cgp_solve_info* info, void* stream);
+
+/*
  * cgp_prolong - prolongation by the P1 shape functions (Eq. 20) for one level:
  * x_f[i] = x_c[i] for coarse nodes, x_f[n_c + e] = (x_c[a_e] + x_c[b_e]) / 2 at
  * the midpoint of edge e (shape functions 1/2, 1/2, 0 there).

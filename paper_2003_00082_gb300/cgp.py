@@ -33,7 +33,8 @@ CGP_MIXED = 1
 CGP_FP32 = 1          # precision argument of cgp_spmv for the FP32 copy of K
 
 EXPORTS = ("cgp_assemble", "cgp_mesh_query", "cgp_mesh_fine_geometry", "cgp_mesh_matrices",
-           "cgp_restrict", "cgp_poisson_solve", "cgp_poisson_solve_async", "cgp_prolong", "cgp_lorentz", "cgp_spmv",
+           "cgp_restrict", "cgp_poisson_solve", "cgp_poisson_solve_async",
+           "cgp_poisson_solve_noalloc", "cgp_prolong", "cgp_lorentz", "cgp_spmv",
            "cgp_set_tuning", "cgp_get_tuning", "cgp_barrier_selftest", "cgp_mesh_destroy",
            "cgp_last_error")
 
@@ -89,6 +90,8 @@ def load(path: str | None = None):
         "cgp_restrict": [vp, i, dp, d, vp, vp, vp, vp, vp, vp],
         "cgp_poisson_solve": [vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp],
         "cgp_poisson_solve_async": [vp, vp, vp, ctypes.POINTER(SolveOpts), vp, vp],
+        "cgp_poisson_solve_noalloc": [i, vp, vp, vp, vp, vp, vp, ctypes.POINTER(SolveOpts),
+                                      ctypes.POINTER(SolveInfo), vp],
         "cgp_prolong": [vp, vp, vp, vp],
         "cgp_lorentz": [vp, vp, vp, vp, dp, d, vp, vp, vp],
         "cgp_spmv": [vp, i, vp, vp, vp],
@@ -215,6 +218,21 @@ def cgp_poisson_solve_async(mesh, b, x, tol=1e-8, max_it=20000, precision=CGP_FP
                      int(max_sweeps))
     _check(load().cgp_poisson_solve_async(mesh, _dev(b), _dev(x), ctypes.byref(opts),
                                           _dev(info_dev, None), _stream(stream)))
+
+
+CGP_STATIC_MAX_ROWS = 65536
+
+
+def cgp_poisson_solve_noalloc(n, rowptr, col, K, dinv, b, x, tol=1e-8, max_it=20000, use_x0=False,
+                              stream=None):
+    """FP64 solve on caller-provided device CSR data; the library allocates nothing (see cgp.h)."""
+    opts = SolveOpts(float(tol), int(max_it), CGP_FP64, 1e-4, int(bool(use_x0)), 1)
+    inf = SolveInfo()
+    st = load().cgp_poisson_solve_noalloc(int(n), _dev(rowptr, "int32"), _dev(col, "int32"), _dev(K), _dev(dinv),
+                                          _dev(b), _dev(x), ctypes.byref(opts), ctypes.byref(inf),
+                                          _stream(stream))
+    _check(st, allow=(CGP_ERR_NOT_CONVERGED, CGP_ERR_BREAKDOWN, CGP_ERR_NONFINITE))
+    return inf.as_dict()
 
 
 def decode_infos(raw: bytes, count: int):

@@ -100,6 +100,29 @@ int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_o
                  cgp_solve_info* info_dev, cudaStream_t s);
 int solver_max_blocks(int device);
 
+// FP64 solve of a caller-described CSR system with caller-provided scratch
+// (the same persistent kernel as launch_solve, default launch shape).
+struct RawSystem {
+  int n;
+  const int* rowptr;
+  const int* col;
+  const double* val;
+  const double* dinv;
+};
+struct RawScratch {
+  double* bp;
+  double* r;
+  double* z;
+  double* p;
+  double* q;
+  double* part;     // [16 * max_blocks]
+  int max_blocks;
+  unsigned* bar;    // zeroed by the caller before the launch
+  SolveResult* res; // zeroed by the caller before the launch
+};
+int launch_solve_fp64_raw(int device, const RawSystem& sys, const RawScratch& scr, const double* b, double* x,
+                          const cgp_solve_opts& o, cudaStream_t s);
+
 }  // namespace cgp
 
 struct cgp_mesh_s : public cgp::cgp_mesh_impl {};

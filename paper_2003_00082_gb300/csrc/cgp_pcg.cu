@@ -648,6 +648,48 @@ void (*spmv_for(int lanes))(int, const int*, const int*, const V*, const V*, V*)
   }
 }
 
+int launch_solve_fp64_raw(int device, const RawSystem& sys, const RawScratch& scr, const double* b, double* x,
+                          const cgp_solve_opts& o, cudaStream_t s) {
+  const int block = 512;
+  PcgFn fn = pcg_kernel_for(1);
+  const int cap = std::min(coresident_blocks(fn, block, device), scr.max_blocks);
+  if (cap <= 0) return fail(CGP_ERR_CUDA, "solver: kernel cannot be resident on this device");
+  int nblk = sys.n <= 16384 ? 1 : (sys.n + block - 1) / block;
+  nblk = std::max(1, std::min(nblk, std::min(cap, sys.n)));
+  const long long max_epochs = 8LL + 4LL * (long long)std::max(o.max_it, 1);
+  if (max_epochs * nblk >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "solver: max_it too large");
+  Desc d{};
+  d.n = sys.n;
+  d.rowptr = sys.rowptr;
+  d.col = sys.col;
+  d.val = sys.val;
+  d.dinv = sys.dinv;
+  d.b = b;
+  d.x = x;
+  d.bp = scr.bp;
+  d.r = scr.r;
+  d.z = scr.z;
+  d.p = scr.p;
+  d.q = scr.q;
+  d.part = scr.part;
+  d.part_stride = scr.max_blocks;
+  d.bar = scr.bar;
+  d.res = scr.res;
+  d.out = nullptr;
+  d.blk0 = 0;
+  d.nblk = nblk;
+  d.tol = o.tol;
+  d.inner_tol = o.inner_tol;
+  d.max_it = o.max_it;
+  d.max_sweeps = 1;
+  d.use_x0 = o.use_x0;
+  d.mixed = 0;
+  d.spin_ns = 2000000000LL;
+  void* args[] = {&d};
+  CGP_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(nblk), dim3(block), args, 0, s));
+  return CGP_OK;
+}
+
 int launch_spmv(cgp_mesh_impl* m, int precision, const void* x, void* y, cudaStream_t s) {
   const int sms = std::max(1, dev_info(m->device).sms);
   const SolverTuning& tu = m->tune[precision == CGP_FP64 ? CGP_TUNE_SPMV_FP64 : CGP_TUNE_SPMV_FP32];

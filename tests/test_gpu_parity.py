@@ -42,8 +42,9 @@ def rel(a, r):
 
 
 def meshes():
-    square = (np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]]), np.array([[0, 1, 2], [0, 2, 3]]))
-    one = (np.array([[0.0, 0.0], [1.0, 0.2], [0.3, 0.9]]), np.array([[0, 1, 2]]))
+    # hand-made meshes sit away from the cylinder axis, where the synthetic flow is singular
+    square = (np.array([[2.0, 1.0], [3.0, 1.0], [3.0, 2.0], [2.0, 2.0]]), np.array([[0, 1, 2], [0, 2, 3]]))
+    one = (np.array([[2.0, 1.0], [3.0, 1.2], [2.3, 1.9]]), np.array([[0, 1, 2]]))
     return {"one-triangle": one, "square": square, "ogrid-7x3": inputs.ogrid(7, 3),
             "ogrid-33x17": inputs.ogrid(33, 17), "ogrid-64x32": inputs.ogrid(64, 32)}
 
