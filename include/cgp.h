@@ -176,7 +176,7 @@ int cgp_poisson_solve_async(cgp_mesh m, const double* b, double* x, const cgp_so
  * system K (rowptr [n+1], col [nnz], K [nnz], D^-1 [n], all device, e.g.
  * copied out with cgp_mesh_matrices) and b, x as in cgp_poisson_solve; the
  * solver's scratch is a static array inside the library, sized for
- * n <= CGP_STATIC_MAX_ROWS (65,536 rows, about 2.7 MB held on every GPU that
+ * n <= CGP_STATIC_MAX_ROWS (65,536 rows, about 3.4 MB held on every GPU that
  * loads the library until the process exits).  Larger n is rejected with
  * CGP_ERR_INVALID_ARG.  Only opts->precision == CGP_FP64 is accepted.
  *
@@ -227,11 +227,14 @@ int cgp_spmv(cgp_mesh m, int precision, const void* x, void* y, void* stream);
  *
  * what    CGP_TUNE_SOLVE_FP64, CGP_TUNE_SOLVE_MIXED (the persistent solver),
  *         CGP_TUNE_SPMV_FP64, CGP_TUNE_SPMV_FP32 (cgp_spmv).
- * block   threads per block: a multiple of 32 in [64, 1024]; 0 = default.
+ * block   threads per block: a multiple of 32 in [64, 512] for the solver,
+ *         [64, 256] for the SpMV; 0 = default.
  * lanes   threads cooperating on one CSR row: 1, 2, 4, 8 or 32 (32 is one
  *         warp per row); 0 = default.
  * blocks  solver: blocks of the persistent grid (clamped to what can be
  *         co-resident); SpMV: grid size; 0 = chosen from the size.
+ * flags   solver: bit 0 keeps each block's rows in global memory instead of
+ *         shared memory; other bits must be 0.
  * Invalid shapes are rejected with INVALID_ARG.  cgp_autotune sets these.
  */
 typedef enum {
@@ -241,8 +244,16 @@ typedef enum {
   CGP_TUNE_SPMV_FP32 = 3
 } cgp_tune_target;
 
-int cgp_set_tuning(cgp_mesh m, int what, int block, int lanes, int blocks);
-int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks);
+int cgp_set_tuning(cgp_mesh m, int what, int block, int lanes, int blocks, int flags);
+int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks, int* flags);
+
+/*
+ * cgp_last_launch - shape of the last persistent solver launch on this mesh.
+ * precision CGP_FP64 or CGP_MIXED; outputs (any may be NULL): grid blocks,
+ * threads per block, whether each block kept its rows in shared memory, and
+ * the dynamic shared memory per block in bytes.  All zero before any solve.
+ */
+int cgp_last_launch(cgp_mesh m, int precision, int* blocks, int* block, int* resident, int* smem_bytes);
 
 /*
  * cgp_barrier_selftest - exercise the persistent solver's grid barrier.

@@ -35,7 +35,7 @@ CGP_FP32 = 1          # precision argument of cgp_spmv for the FP32 copy of K
 EXPORTS = ("cgp_assemble", "cgp_mesh_query", "cgp_mesh_fine_geometry", "cgp_mesh_matrices",
            "cgp_restrict", "cgp_poisson_solve", "cgp_poisson_solve_async",
            "cgp_poisson_solve_noalloc", "cgp_prolong", "cgp_lorentz", "cgp_spmv",
-           "cgp_set_tuning", "cgp_get_tuning", "cgp_barrier_selftest", "cgp_mesh_destroy",
+           "cgp_set_tuning", "cgp_get_tuning", "cgp_last_launch", "cgp_barrier_selftest", "cgp_mesh_destroy",
            "cgp_last_error")
 
 CGP_TUNE_SOLVE_FP64 = 0
@@ -95,8 +95,9 @@ def load(path: str | None = None):
         "cgp_prolong": [vp, vp, vp, vp],
         "cgp_lorentz": [vp, vp, vp, vp, dp, d, vp, vp, vp],
         "cgp_spmv": [vp, i, vp, vp, vp],
-        "cgp_set_tuning": [vp, i, i, i, i],
-        "cgp_get_tuning": [vp, i, ip, ip, ip],
+        "cgp_set_tuning": [vp, i, i, i, i, i],
+        "cgp_get_tuning": [vp, i, ip, ip, ip, ip],
+        "cgp_last_launch": [vp, i, ip, ip, ip, ip],
         "cgp_barrier_selftest": [i, i, ctypes.c_longlong, vp],
         "cgp_mesh_destroy": [vp],
     }
@@ -255,14 +256,20 @@ def cgp_spmv(mesh, precision, x, y, stream=None):
     _check(load().cgp_spmv(mesh, int(precision), _dev(x, dt), _dev(y, dt), _stream(stream)))
 
 
-def cgp_set_tuning(mesh, what, block=0, lanes=0, blocks=0):
-    _check(load().cgp_set_tuning(mesh, int(what), int(block), int(lanes), int(blocks)))
+def cgp_set_tuning(mesh, what, block=0, lanes=0, blocks=0, flags=0):
+    _check(load().cgp_set_tuning(mesh, int(what), int(block), int(lanes), int(blocks), int(flags)))
 
 
 def cgp_get_tuning(mesh, what):
-    v = [ctypes.c_int() for _ in range(3)]
+    v = [ctypes.c_int() for _ in range(4)]
     _check(load().cgp_get_tuning(mesh, int(what), *[ctypes.byref(a) for a in v]))
-    return dict(block=v[0].value, lanes=v[1].value, blocks=v[2].value)
+    return dict(block=v[0].value, lanes=v[1].value, blocks=v[2].value, flags=v[3].value)
+
+
+def cgp_last_launch(mesh, precision=CGP_FP64):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().cgp_last_launch(mesh, int(precision), *[ctypes.byref(a) for a in v]))
+    return dict(blocks=v[0].value, block=v[1].value, resident=v[2].value, smem=v[3].value)
 
 
 def cgp_barrier_selftest(nblk, absent, spin_ns, stream=None):

@@ -1,0 +1,138 @@
+// Exact fixed-point accumulation of FP64 values on the integer pipe.
+//
+// On GB300 a warp-wide FP64 instruction occupies the narrow FP64 pipe for
+// tens of cycles, so a dependent chain of FP64 adds (a reduction tree) is
+// slow.  The reductions of the solver therefore convert each double to a
+// signed 128-bit integer aligned to a common exponent and add integers:
+//
+//   a finite double v = M * 2^(e - 1075), M < 2^53 (e the biased exponent,
+//   with the implicit bit; subnormals use e = 1);
+//   relative to a reference exponent E >= e its fixed-point image is
+//   X = M * 2^(54 - (E - e)), truncated toward zero below 2^0,
+//   i.e. X = v * 2^(1129 - E), |X| < 2^107.
+//
+// Sums of up to 2^20 images fit in 128 bits.  Integer addition is
+// associative, so the total does not depend on the order of the terms (the
+// result is identical in every block and every run), and the only error is
+// the truncation of each term 2^-106 below the largest one: far below FP64
+// rounding.  The total is converted back to the nearest double (ties to
+// even) with integer operations only.
+//
+// The functions are __host__ __device__ so the arithmetic can be checked on
+// the CPU against exact rational sums.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+
+#ifndef __CUDACC__
+#define CGP_HD
+#else
+#define CGP_HD __host__ __device__
+#endif
+
+namespace cgp {
+namespace fx {
+
+constexpr int kFrac = 54;          // fraction bits below the reference exponent's unit
+constexpr int kBadExp = 0x7FFF;    // exponent marker of a non-finite contribution
+
+typedef __int128 I128;
+typedef unsigned __int128 U128;
+
+CGP_HD inline uint64_t dbits(double v) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(v);
+#else
+  uint64_t b;
+  std::memcpy(&b, &v, 8);
+  return b;
+#endif
+}
+
+CGP_HD inline double from_bits(uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double v;
+  std::memcpy(&v, &b, 8);
+  return v;
+#endif
+}
+
+CGP_HD inline int clz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+// Biased exponent used for alignment: 1 for zero and subnormals, kBadExp for
+// Inf and NaN, else the IEEE biased exponent.
+CGP_HD inline int exponent_of(double v) {
+  const int e = (int)((dbits(v) >> 52) & 0x7FF);
+  if (e == 0x7FF) return kBadExp;
+  return e == 0 ? 1 : e;
+}
+
+// Arithmetic shift right by s >= 0 (rounds toward minus infinity).
+CGP_HD inline I128 sar(I128 a, int s) { return a >> (s > 127 ? 127 : s); }
+
+// Fixed-point image of a finite v relative to reference exponent E >= exponent_of(v).
+CGP_HD inline I128 image(double v, int E) {
+  const uint64_t b = dbits(v);
+  const int eb = (int)((b >> 52) & 0x7FF);
+  const uint64_t m = b & ((1ull << 52) - 1);
+  const uint64_t M = eb == 0 ? m : (m | (1ull << 52));
+  const int e = eb == 0 ? 1 : eb;
+  const int sh = kFrac - (E - e);   // shift left when >= 0 (at most 54)
+  const I128 x = sh >= 0 ? (I128)M << sh : (I128)((-sh) >= 64 ? 0 : (M >> (-sh)));
+  return (b >> 63) ? -x : x;
+}
+
+// Nearest double (ties to even) of X * 2^(E - 1075 - kFrac).
+CGP_HD inline double to_double(I128 X, int E) {
+  if (E >= kBadExp) return from_bits(0x7FF8000000000000ull);  // NaN
+  const bool negative = X < 0;
+  const U128 U = negative ? (U128)(-X) : (U128)X;
+  if (U == 0) return 0.0;
+  const uint64_t hi = (uint64_t)(U >> 64), lo = (uint64_t)U;
+  int lead = hi ? 127 - clz64(hi) : 63 - clz64(lo);  // index of the leading one
+  uint64_t mant;
+  if (lead <= 52) {
+    mant = lo << (52 - lead);
+  } else {
+    const int s = lead - 52;  // dropped bits, 1..75
+    mant = (uint64_t)(U >> s);
+    const U128 rem = U & (((U128)1 << s) - 1), half = (U128)1 << (s - 1);
+    if (rem > half || (rem == half && (mant & 1u))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++lead;
+      }
+    }
+  }
+  // value = mant * 2^(lead - 52) * 2^(E - 1129)
+  const uint64_t sign = negative ? (1ull << 63) : 0;
+  const int biased = lead + E - 106;
+  if (biased >= 2047) return from_bits(sign | 0x7FF0000000000000ull);
+  if (biased <= 0) {
+    // subnormal result: shift the 53-bit mantissa into place, rounding to nearest even
+    const int s = 1 - biased;
+    uint64_t m2 = 0;
+    if (s < 64) {
+      m2 = mant >> s;
+      const uint64_t rem = mant & ((1ull << s) - 1), half = 1ull << (s - 1);
+      if (rem > half || (rem == half && (m2 & 1u))) ++m2;
+    }
+    return from_bits(sign | m2);
+  }
+  return from_bits(sign | ((uint64_t)biased << 52) | (mant & ((1ull << 52) - 1)));
+}
+
+CGP_HD inline I128 add(I128 a, I128 b) { return a + b; }
+
+}  // namespace fx
+}  // namespace cgp

@@ -35,9 +35,34 @@ struct SolveResult {
 
 // Tuning of the persistent solver launch (chosen by the autotuner or defaults).
 struct SolverTuning {
-  int block;          // threads per block
-  int lanes;          // lanes per CSR row in the SpMV phases (1, 2, 4, 8)
-  int blocks;         // blocks per instance (0 = all co-resident blocks)
+  int block;          // threads per block (0 = default)
+  int lanes;          // lanes per CSR row in the SpMV phases (1, 2, 4, 8, 32; 0 = default)
+  int blocks;         // blocks of the persistent grid (0 = chosen from the size)
+  int flags;          // bit 0: keep rows in global memory (no shared-memory residency)
+};
+
+// Shape of the last persistent launch on a mesh (for reports and tests).
+struct PlanRecord {
+  int blocks;
+  int block;
+  int resident;
+  int smem;
+};
+
+// Row partition of the coarse system over `nblk` solver blocks (contiguous
+// chunks of ceil(n / nblk) rows) with, per block, the list of columns it
+// reads from rows owned by other blocks.  lcol holds, in CSR order, each
+// entry's column renumbered into the block's local index space: own rows
+// first (j - r0), then the block's halo columns in ascending order.
+struct HaloPlan {
+  int nblk = 0;
+  int max_rows = 0;
+  int max_nnz = 0;
+  int max_halo = 0;
+  int* lcol = nullptr;   // [nnz]
+  int* hptr = nullptr;   // [nblk + 1]
+  int* hidx = nullptr;   // [total halo]
+  void* base = nullptr;  // the one allocation holding the three arrays
 };
 
 struct cgp_mesh_impl {
@@ -72,19 +97,22 @@ struct cgp_mesh_impl {
   double* r = nullptr;
   double* z = nullptr;
   double* p = nullptr;
+  double* p2 = nullptr;
   double* q = nullptr;
   float* r32 = nullptr;
   float* z32 = nullptr;
   float* p32 = nullptr;
   float* q32 = nullptr;
   float* d32 = nullptr;
-  double* part = nullptr;    // [max_blocks * 4] per-block partial sums
+  double* part = nullptr;    // [max_blocks * 32] per-block fixed-point partial sums
   unsigned* bar = nullptr;   // grid barrier counter
   SolveResult* res = nullptr;
   SolveResult* h_res = nullptr;  // pinned host mirror
   int max_blocks = 0;
 
-  SolverTuning tune[4] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // indexed by cgp_tune_target
+  std::vector<HaloPlan> plans;   // cached per block count
+  SolverTuning tune[4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};  // by cgp_tune_target
+  PlanRecord last_plan[2] = {{0, 0, 0, 0}, {0, 0, 0, 0}};                          // FP64, MIXED
 };
 
 // ---- launchers implemented in the .cu files ----
@@ -114,8 +142,9 @@ struct RawScratch {
   double* r;
   double* z;
   double* p;
+  double* p2;
   double* q;
-  double* part;     // [16 * max_blocks]
+  double* part;     // [32 * max_blocks]
   int max_blocks;
   unsigned* bar;    // zeroed by the caller before the launch
   SolveResult* res; // zeroed by the caller before the launch

@@ -223,9 +223,9 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
          o_tri = take(3 * (size_t)t_c * 4), o_mid = take(3 * (size_t)t_c * 4),
          o_edges = take(2 * (size_t)m->n_e * 4), o_xyf = take(2 * (size_t)m->n_f * 8),
          o_xyc = take(2 * n * 8), o_incp = take((n + 1) * 4), o_inc = take(3 * (size_t)t_c * 4),
-         o_bp = take(n * 8), o_r = take(n * 8), o_z = take(n * 8), o_p = take(n * 8), o_q = take(n * 8),
+         o_bp = take(n * 8), o_r = take(n * 8), o_z = take(n * 8), o_p = take(n * 8), o_p2 = take(n * 8), o_q = take(n * 8),
          o_r32 = take(n * 4), o_z32 = take(n * 4), o_p32 = take(n * 4), o_q32 = take(n * 4),
-         o_d32 = take(n * 4), o_part = take((size_t)m->max_blocks * 16 * 8), o_bar = take(64),
+         o_d32 = take(n * 4), o_part = take((size_t)m->max_blocks * 32 * 8), o_bar = take(256),
          o_res = take(sizeof(SolveResult));
   m->d_bytes = off;
   cudaError_t e = cudaMalloc(&m->d_base, m->d_bytes);
@@ -250,6 +250,7 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
   m->r = (double*)(base + o_r);
   m->z = (double*)(base + o_z);
   m->p = (double*)(base + o_p);
+  m->p2 = (double*)(base + o_p2);
   m->q = (double*)(base + o_q);
   m->r32 = (float*)(base + o_r32);
   m->z32 = (float*)(base + o_z32);
@@ -326,6 +327,8 @@ extern "C" int cgp_mesh_matrices(cgp_mesh m, int* rowptr, int* col, double* K, d
 extern "C" int cgp_mesh_destroy(cgp_mesh m) {
   if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_mesh_destroy: NULL mesh");
   cudaDeviceSynchronize();
+  for (auto& pl : m->plans)
+    if (pl.base) cudaFree(pl.base);
   if (m->d_base) cudaFree(m->d_base);
   if (m->h_res) cudaFreeHost(m->h_res);
   delete m;

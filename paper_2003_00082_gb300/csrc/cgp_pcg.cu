@@ -31,13 +31,14 @@
 #include <mutex>
 #include <string>
 
+#include "cgp_fixed.h"
 #include "cgp_internal.h"
 
 namespace cgp {
 namespace {
 
 constexpr int NCOMP = 4;         // partial-sum components per reduction
-constexpr int MAX_BLOCK = 1024;
+constexpr int MAX_BLOCK = 512;   // threads per block of the persistent solver (<= 128 registers each)
 
 struct Desc {
   int n;
@@ -53,6 +54,7 @@ struct Desc {
   double* r;
   double* z;
   double* p;
+  double* p2;         // second buffer of p (FP64 solver)
   double* q;
   float* r32;
   float* z32;
@@ -67,6 +69,11 @@ struct Desc {
   int blk0, nblk;
   double tol, inner_tol;
   int max_it, max_sweeps, use_x0, mixed;
+  int res_nnz_cap;    // RES: capacity of the shared-memory CSR slice
+  int halo_cap;       // RES: capacity of the halo gather buffer
+  const int* lcol;    // RES: columns renumbered per block (halo plan)
+  const int* hptr;    // RES: halo list of each block
+  const int* hidx;
   long long spin_ns;
 };
 
@@ -90,12 +97,30 @@ __device__ __forceinline__ V warp_sum(V v) {
 }
 
 struct Shared {
-  double red[NCOMP * 32];
+  unsigned long long wlo[2][32];  // per-warp fixed-point partials of one reduction
+  long long whi[2][32];
+  int wexp[2][32];
   double tot[NCOMP];
+  double sc[8];                 // scalars computed by one lane and broadcast
+  int isc[4];
   int flag;
 };
 
-// Barrier over the blocks of one instance.
+// Barrier over the blocks of one instance: arrival is a release-add on a
+// counter that only grows; a block waits until the counter reaches
+// epoch * nblk, polling with relaxed loads and finishing with an acquire.
+// The wait gives up after spin_ns of wall-clock time, or as soon as another
+// block has given up, and then reports failure.
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 struct Group {
   unsigned* bar;
   int* timeout;
@@ -109,21 +134,24 @@ struct Group {
     ++epoch;
     if (threadIdx.x == 0) {
       int ok = 1;
-      __threadfence();
-      atomicAdd(bar, 1u);
+      red_release_add(bar, 1u);
       const unsigned target = epoch * nblk;
-      const unsigned long long t0 = global_ns();
+      unsigned long long t0 = 0;
       unsigned spins = 0;
-      while (ld_acquire(bar) < target) {
-        if (*(volatile int*)timeout) { ok = 0; break; }
-        if ((++spins & 31u) == 0 && (long long)(global_ns() - t0) > spin_ns) {
-          atomicExch(timeout, 1);
-          ok = 0;
-          break;
+      while (ld_relaxed(bar) < target) {
+        if ((++spins & 127u) == 0) {
+          if (*(volatile int*)timeout) { ok = 0; break; }
+          const unsigned long long now = global_ns();
+          if (t0 == 0) {
+            t0 = now;
+          } else if ((long long)(now - t0) > spin_ns) {
+            atomicExch(timeout, 1);
+            ok = 0;
+            break;
+          }
         }
-        __nanosleep(32);
       }
-      __threadfence();
+      if (ok) (void)ld_acquire(bar);
       sh.flag = ok;
     }
     __syncthreads();
@@ -131,24 +159,122 @@ struct Group {
   }
 };
 
-// Sum NC per-thread values over the block; thread 0 stores them as this
-// block's partials in bank (red & 1).
+__device__ __forceinline__ fx::I128 shfl_xor_i128(fx::I128 a, int o) {
+  const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)a, o);
+  const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(a >> 64), o);
+  return ((fx::I128)hi << 64) | (fx::I128)lo;
+}
+
+__device__ __forceinline__ fx::I128 warp_sum_i128(fx::I128 a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += shfl_xor_i128(a, o);
+  return a;
+}
+
+// Warp-wide fixed-point sum of one double per lane: returns the warp's common
+// exponent in E and the aligned integer sum (identical on every lane).
+__device__ __forceinline__ fx::I128 warp_fx_sum(double v, int& E) {
+  const int e = fx::exponent_of(v);
+  E = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+  const fx::I128 x = E < fx::kBadExp ? fx::image(v, E) : (fx::I128)0;
+  return warp_sum_i128(x);
+}
+
+// Partial-sum slot of (bank, component, block): {lo, hi, exponent} as 64-bit words.
+__device__ __forceinline__ unsigned long long* part_slot(const Desc& d, int red, int c, int blk) {
+  return reinterpret_cast<unsigned long long*>(d.part) + 4 * ((size_t)((red & 1) * NCOMP + c) * d.part_stride + blk);
+}
+
+// Sum NC (<= 2) per-thread values over the block; thread 0 stores them as
+// this block's partials in bank (red & 1).  The sums are exact fixed-point
+// integer sums (cgp_fixed.h): they run on the integer pipe, cost no FP64
+// instructions, and do not depend on the order of the terms.
 template <int NC>
 __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, double (&v)[NC], Shared& sh) {
+  static_assert(NC <= 2, "at most two components per reduction");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    double s = warp_sum(v[c]);
-    if (lane == 0) sh.red[c * 32 + warp] = s;
+    int E;
+    const fx::I128 x = warp_fx_sum(v[c], E);
+    if (lane == 0) {
+      sh.wlo[c][warp] = (unsigned long long)x;
+      sh.whi[c][warp] = (long long)(x >> 64);
+      sh.wexp[c][warp] = E;
+    }
   }
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      double s = lane < nw ? sh.red[c * 32 + lane] : 0.0;
-      s = warp_sum(s);
-      if (lane == 0) d.part[((red & 1) * NCOMP + c) * d.part_stride + lb] = s;
+      fx::I128 x = 0;
+      int e = 1;
+      if (lane < nw) {
+        x = ((fx::I128)sh.whi[c][lane] << 64) | (fx::I128)sh.wlo[c][lane];
+        e = sh.wexp[c][lane];
+      }
+      const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+      x = warp_sum_i128(E < fx::kBadExp ? fx::sar(x, E - e) : (fx::I128)0);
+      if (lane == 0) {
+        ulonglong2* slot = reinterpret_cast<ulonglong2*>(part_slot(d, red, c, lb));
+        slot[0] = make_ulonglong2((unsigned long long)x, (unsigned long long)(x >> 64));
+        slot[1] = make_ulonglong2((unsigned long long)E, 0ull);
+      }
     }
+  }
+}
+
+// Warp 0: the totals over the group's blocks of NC components of reduction
+// `red`, as doubles on every lane.  All slot loads are issued before any is
+// used; each lane folds its blocks in a fixed order, so every block of the
+// group computes the same bits.
+template <int NC>
+__device__ __forceinline__ void group_totals(const Desc& d, int red, double (&out)[NC]) {
+  constexpr int PRE = 8;  // slots per lane held in registers (groups of up to 256 blocks per pass)
+  const int lane = threadIdx.x & 31;
+  fx::I128 acc[NC];
+  int Ea[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    acc[c] = 0;
+    Ea[c] = 1;
+  }
+  for (int base = 0; base < d.nblk; base += 32 * PRE) {
+    ulonglong2 w0[NC][PRE], w1[NC][PRE];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int t = 0; t < PRE; ++t) {
+        const int j = base + lane + 32 * t;
+        if (j < d.nblk) {
+          const ulonglong2* slot = reinterpret_cast<const ulonglong2*>(part_slot(d, red, c, j));
+          w0[c][t] = __ldcg(slot);
+          w1[c][t] = __ldcg(slot + 1);
+        } else {
+          w0[c][t] = make_ulonglong2(0ull, 0ull);
+          w1[c][t] = make_ulonglong2(1ull, 0ull);
+        }
+      }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      int e = Ea[c];
+#pragma unroll
+      for (int t = 0; t < PRE; ++t) e = max(e, (int)w1[c][t].x);
+      fx::I128 a = fx::sar(acc[c], e - Ea[c]);
+#pragma unroll
+      for (int t = 0; t < PRE; ++t) {
+        const fx::I128 x = ((fx::I128)(long long)w0[c][t].y << 64) | (fx::I128)w0[c][t].x;
+        a += fx::sar(x, e - (int)w1[c][t].x);
+      }
+      acc[c] = a;
+      Ea[c] = e;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)Ea[c]);
+    const fx::I128 t = warp_sum_i128(E < fx::kBadExp ? fx::sar(acc[c], E - Ea[c]) : (fx::I128)0);
+    out[c] = fx::to_double(t, E);
   }
 }
 
@@ -156,14 +282,27 @@ __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, dou
 template <int NC>
 __device__ __forceinline__ void get_totals(const Desc& d, int red, Shared& sh) {
   if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
+    double t[NC];
+    group_totals<NC>(d, red, t);
+    if (threadIdx.x == 0)
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const double* src = d.part + ((red & 1) * NCOMP + c) * d.part_stride;
-      double s = 0.0;
-      for (int j = lane; j < d.nblk; j += 32) s += __ldcg(src + j);
-      s = warp_sum(s);
-      if (lane == 0) sh.tot[c] = s;
+      for (int c = 0; c < NC; ++c) sh.tot[c] = t[c];
+  }
+  __syncthreads();
+}
+
+// As get_totals, then `derive(sh)` runs on one thread to turn the totals
+// into the scalars of the next phase (divisions are done once per block, not
+// once per thread); all threads see them afterwards.
+template <int NC, typename F>
+__device__ __forceinline__ void get_totals_then(const Desc& d, int red, Shared& sh, F derive) {
+  if (threadIdx.x < 32) {
+    double t[NC];
+    group_totals<NC>(d, red, t);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) sh.tot[c] = t[c];
+      derive(sh);
     }
   }
   __syncthreads();
@@ -283,95 +422,344 @@ __device__ bool true_residual(const Desc& d, int lb, int r0, int r1, Group& grp,
   return true;
 }
 
-template <int T>
-__device__ void solve_fp64(const Desc& d, int lb) {
-  __shared__ Shared sh;
+// Own-row storage of one block: in shared memory (RES) or in global scratch.
+struct Local {
+  double* x;
+  double* r;
+  double* z;
+  double* p;
+  double* q;
+  const double* di;
+  double* bp;
+  const int* row;     // [nloc + 1] offsets into col / val
+  const int* col;
+  const double* val;
+};
+
+// Row-wise SpMV over the block's own rows with T lanes per row.  Column j of
+// an own row reads own(j - r0) when j is owned by this block and halo(j)
+// (a value published by another block) otherwise.  op(il, s) receives
+// s = (A v)_{r0 + il} on lane 0 of the row's group.
+template <int T, typename V, typename FOwn, typename FHalo, typename Op>
+__device__ __forceinline__ void spmv_local(const Local& L, int r0, int nloc, FOwn own, FHalo halo, Op op) {
+  const int g = threadIdx.x / T, l = threadIdx.x % T, ng = blockDim.x / T;
+  for (int base = 0; base < nloc; base += ng) {
+    const int il = base + g;
+    V s = V(0);
+    if (il < nloc) {
+      const int k1 = L.row[il + 1];
+      for (int k = L.row[il] + l; k < k1; k += T) {
+        const int jl = L.col[k] - r0;
+        const V v = ((unsigned)jl < (unsigned)nloc) ? own(jl) : halo(jl + r0);
+        s = fma(L.val[k], v, s);
+      }
+    }
+    if (T > 1) {
+#pragma unroll
+      for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, T);
+    }
+    if (il < nloc && l == 0) op(il, s);
+  }
+}
+
+// SpMV over the block's own rows when every column has been renumbered into
+// the block's local space (own rows, then gathered halo values): all reads
+// are shared-memory reads, no branch per entry.
+template <int T, typename Op>
+__device__ __forceinline__ void spmv_ext(const int* __restrict__ row, const int* __restrict__ col,
+                                         const double* __restrict__ val, const double* ext, int nloc, Op op) {
+  const int g = threadIdx.x / T, l = threadIdx.x % T, ng = blockDim.x / T;
+  for (int base = 0; base < nloc; base += ng) {
+    const int il = base + g;
+    double s = 0.0;
+    if (il < nloc) {
+      const int k1 = row[il + 1];
+      for (int k = row[il] + l; k < k1; k += T) s = fma(val[k], ext[col[k]], s);
+    }
+    if (T > 1) {
+#pragma unroll
+      for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, T);
+    }
+    if (il < nloc && l == 0) op(il, s);
+  }
+}
+
+// FP64 Jacobi-PCG with two group barriers per iteration.
+//
+// p is kept twice: each block updates its own rows (p = z + beta p) and
+// publishes them to the buffer of the iteration's parity; a block that needs
+// p_j of a row it does not own recomputes z_j + beta p_j from the published
+// z and the previous iteration's buffer, with the same fused multiply-add the
+// owner used, so both see bit-identical values and the update needs no
+// barrier of its own.
+//
+// RES: the block's CSR rows (columns renumbered by the halo plan), its
+// vectors and a gather buffer for its halo live in shared memory for the
+// whole solve.  Each product first gathers every halo value the block needs
+// with independent loads, then runs from shared memory only.  Without RES
+// the rows and vectors stay in global scratch and halo values are read in
+// place.
+template <int T, bool RES>
+__device__ void solve_fp64(const Desc& d, int lb, Shared& sh) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   const int tid = threadIdx.x, bd = blockDim.x;
   const int chunk = (d.n + d.nblk - 1) / d.nblk;
-  const int r0 = min(d.n, lb * chunk), r1 = min(d.n, r0 + chunk);
+  const int r0 = min(d.n, lb * chunk), r1 = min(d.n, r0 + chunk), nloc = r1 - r0;
   Group grp{d.bar, &d.res->timeout, (unsigned)d.nblk, 0u, d.spin_ns};
   int red = 0;
 
-  const double bnorm = setup(d, lb, r0, r1, grp, sh, red);
-  if (bnorm < 0.0) return;
+  Local L;
+  double* pe = nullptr;     // RES: [own p | halo values]
+  const int* hid = nullptr; // RES: global index of each halo slot
+  int nh = 0;
+  if constexpr (RES) {
+    double* base = reinterpret_cast<double*>(dsm);
+    L.x = base;
+    L.r = base + chunk;
+    L.z = base + 2 * chunk;
+    L.q = base + 3 * chunk;
+    double* di = base + 4 * chunk;
+    L.bp = base + 5 * chunk;
+    pe = base + 6 * chunk;
+    L.p = pe;
+    double* val = pe + chunk + d.halo_cap;
+    int* row = reinterpret_cast<int*>(val + d.res_nnz_cap);
+    int* col = row + chunk + 1;
+    int* hidw = col + d.res_nnz_cap;
+    const int k0 = nloc > 0 ? d.rowptr[r0] : 0;
+    const int nnzl = nloc > 0 ? d.rowptr[r1] - k0 : 0;
+    const int h0 = d.hptr[lb];
+    nh = d.hptr[lb + 1] - h0;
+    for (int i = tid; i <= nloc; i += bd) row[i] = d.rowptr[r0 + i] - k0;
+    for (int k = tid; k < nnzl; k += bd) {
+      col[k] = d.lcol[k0 + k];
+      val[k] = d.val[k0 + k];
+    }
+    for (int h = tid; h < nh; h += bd) hidw[h] = d.hidx[h0 + h];
+    for (int i = tid; i < nloc; i += bd) di[i] = d.dinv[r0 + i];
+    L.di = di;
+    L.row = row;
+    L.col = col;
+    L.val = val;
+    hid = hidw;
+  } else {
+    L.x = d.x + r0;
+    L.r = d.r + r0;
+    L.z = d.z + r0;
+    L.p = nullptr;
+    L.q = d.q + r0;
+    L.di = d.dinv + r0;
+    L.bp = d.bp + r0;
+    L.row = d.rowptr + r0;
+    L.col = d.col;
+    L.val = d.val;
+  }
+
+  // ---- means of b and x0 ----
+  {
+    double v2[2] = {0.0, 0.0};
+    for (int i = tid; i < nloc; i += bd) {
+      v2[0] += d.b[r0 + i];
+      if (d.use_x0) v2[1] += d.x[r0 + i];
+    }
+    put_partials<2>(d, lb, red, v2, sh);
+    if (!grp.sync(sh)) return;
+    get_totals<2>(d, red, sh);
+    ++red;
+  }
+  const double mb = sh.tot[0] / d.n, mx = sh.tot[1] / d.n;
+  // ---- projected b and x0; x0 published for the first product ----
+  {
+    double v1[1] = {0.0};
+    for (int i = tid; i < nloc; i += bd) {
+      const double bi = d.b[r0 + i] - mb;
+      L.bp[i] = bi;
+      v1[0] += bi * bi;
+      const double xi = d.use_x0 ? d.x[r0 + i] - mx : 0.0;
+      L.x[i] = xi;
+      if (RES) {
+        d.x[r0 + i] = xi;
+        pe[i] = xi;
+      }
+    }
+    put_partials<1>(d, lb, red, v1, sh);
+    if (!grp.sync(sh)) return;
+    get_totals<1>(d, red, sh);
+    ++red;
+  }
+  const double bnorm = sqrt(sh.tot[0]);
   if (!isfinite(bnorm)) { finish(d, lb, CGP_ERR_NONFINITE, 0, 0, 0.0, 0.0, bnorm); return; }
   if (bnorm == 0.0) {
-    for (int i = r0 + tid; i < r1; i += bd) d.x[i] = 0.0;
+    for (int i = tid; i < nloc; i += bd) d.x[r0 + i] = 0.0;
     finish(d, lb, CGP_OK, 0, 0, 0.0, 0.0, 0.0);
     return;
   }
-  // r = bp - K x, z = D^-1 r, p = z
+  // ---- r = bp - K x0, z = D^-1 r, p = z (published to buffer 0) ----
+  double v2init[2];
   {
     double v2[2] = {0.0, 0.0};
-    spmv_rows<T, double>(d.rowptr, d.col, d.val, d.x, r0, r1, [&](int i, double s) {
-      const double ri = d.bp[i] - s;
-      const double zi = d.dinv[i] * ri;
-      d.r[i] = ri;
-      d.z[i] = zi;
-      d.p[i] = zi;
+    auto op = [&](int il, double s) {
+      const double ri = L.bp[il] - s;
+      const double zi = L.di[il] * ri;
+      L.r[il] = ri;
+      L.z[il] = zi;
+      if (RES) d.z[r0 + il] = zi;
+      d.p[r0 + il] = zi;
       v2[0] += ri * zi;
       v2[1] += ri * ri;
-    });
-    put_partials<2>(d, lb, red, v2, sh);
-    if (!grp.sync(sh)) return;
+    };
+    if constexpr (RES) {
+      for (int h = tid; h < nh; h += bd) pe[nloc + h] = __ldcg(d.x + hid[h]);
+      __syncthreads();
+      spmv_ext<T>(L.row, L.col, L.val, pe, nloc, op);
+      __syncthreads();
+      for (int i = tid; i < nloc; i += bd) pe[i] = L.z[i];
+    } else {
+      spmv_local<T, double>(
+          L, r0, nloc, [&](int jl) { return L.x[jl]; }, [&](int j) { return __ldcg(d.x + j); }, op);
+    }
+    v2init[0] = v2[0];
+    v2init[1] = v2[1];
   }
   int k = 0, status = CGP_ERR_NOT_CONVERGED;
-  double rz_old = 0.0, rnorm = 0.0;
-  const double stop = d.tol * bnorm;
+  if (tid == 0) {
+    const double stop = d.tol * bnorm;
+    sh.sc[4] = stop * stop;    // the test ||r||^2 <= (tol ||b||)^2 needs no square root
+    sh.sc[3] = 0.0;            // 1 / (r, z) of the previous iteration
+  }
+  // one thread: convergence test and beta from (r,z) and (r,r); everyone reads the outcome
+  // kd: iterations completed when the reduction's values are current
+  int kd = 0;
+  auto derive_rz = [&](Shared& S) {
+    const double rz = S.tot[0], rr = S.tot[1];
+    int st = -1;
+    if (!isfinite(rr) || !isfinite(rz)) st = CGP_ERR_NONFINITE;
+    else if (rr <= S.sc[4]) st = CGP_OK;
+    else if (kd >= d.max_it) st = CGP_ERR_NOT_CONVERGED;
+    S.isc[0] = st;
+    S.sc[0] = rr;
+    S.sc[1] = kd > 0 ? rz * S.sc[3] : 0.0;  // beta = (r,z) / (r,z)_old
+    S.sc[2] = rz;
+  };
+  // the (r,z), (r,r) reduction of the initial residual
+  put_partials<2>(d, lb, red, v2init, sh);
+  if (!grp.sync(sh)) return;
+  get_totals_then<2>(d, red, sh, derive_rz);
+  ++red;
   while (true) {
-    get_totals<2>(d, red, sh);
-    ++red;
-    const double rz = sh.tot[0];
-    rnorm = sqrt(sh.tot[1]);
-    if (!isfinite(rnorm)) { status = CGP_ERR_NONFINITE; break; }
-    if (rnorm <= stop) { status = CGP_OK; break; }
-    if (k >= d.max_it) { status = CGP_ERR_NOT_CONVERGED; break; }
-    if (k > 0) {  // phase A
-      const double beta = rz / rz_old;
-      for (int i = r0 + tid; i < r1; i += bd) d.p[i] = fma(beta, d.p[i], d.z[i]);
-      if (!grp.sync(sh)) return;
+    if (sh.isc[0] >= 0) { status = sh.isc[0]; break; }
+    // one thread of another warp prepares 1 / (r,z) for the next beta, off the critical path
+    if (tid == 32 || (bd == 32 && tid == 0)) sh.sc[3] = 1.0 / sh.sc[2];
+    const double beta = sh.sc[1];
+    double* pcur = (k & 1) ? d.p2 : d.p;
+    const double* pold = (k & 1) ? d.p : d.p2;
+    if (k > 0) {  // own rows: p = z + beta p, published to this iteration's buffer
+      for (int i = tid; i < nloc; i += bd) {
+        if (RES) {
+          const double pi = fma(beta, pe[i], L.z[i]);
+          pe[i] = pi;
+          pcur[r0 + i] = pi;
+        } else {
+          pcur[r0 + i] = fma(beta, pold[r0 + i], L.z[i]);
+        }
+      }
     }
-    rz_old = rz;
-    {  // phase B
+    {  // q = K p; rows owned elsewhere rebuild p_j from the published z_j and p_j
       double v1[1] = {0.0};
-      spmv_rows<T, double>(d.rowptr, d.col, d.val, d.p, r0, r1, [&](int i, double s) {
-        d.q[i] = s;
-        v1[0] += d.p[i] * s;
-      });
+      const double* pown = RES ? pe : pcur + r0;
+      auto op = [&](int il, double s) {
+        L.q[il] = s;
+        v1[0] += pown[il] * s;
+      };
+      if constexpr (RES) {
+        for (int h = tid; h < nh; h += bd) {
+          const int j = hid[h];
+          pe[nloc + h] = k == 0 ? __ldcg(pcur + j) : fma(beta, __ldcg(pold + j), __ldcg(d.z + j));
+        }
+        __syncthreads();
+        spmv_ext<T>(L.row, L.col, L.val, pe, nloc, op);
+      } else {
+        __syncthreads();
+        spmv_local<T, double>(
+            L, r0, nloc, [&](int jl) { return pown[jl]; },
+            [&](int j) { return k == 0 ? __ldcg(pcur + j) : fma(beta, __ldcg(pold + j), __ldcg(d.z + j)); },
+            op);
+      }
       put_partials<1>(d, lb, red, v1, sh);
       if (!grp.sync(sh)) return;
-      get_totals<1>(d, red, sh);
+      get_totals_then<1>(d, red, sh, [&](Shared& S) {
+        const double pq = S.tot[0];
+        S.isc[1] = (pq > 0.0) ? -1 : (isfinite(pq) ? CGP_ERR_BREAKDOWN : CGP_ERR_NONFINITE);
+        S.sc[5] = S.sc[2] / pq;  // alpha
+      });
       ++red;
     }
-    const double pq = sh.tot[0];
-    if (!(pq > 0.0)) { status = isfinite(pq) ? CGP_ERR_BREAKDOWN : CGP_ERR_NONFINITE; break; }
-    const double alpha = rz / pq;
-    {  // phase C
+    if (sh.isc[1] >= 0) { status = sh.isc[1]; break; }
+    const double alpha = sh.sc[5];
+    {  // x += alpha p, r -= alpha q, z = D^-1 r (z published)
       double v2[2] = {0.0, 0.0};
-      for (int i = r0 + tid; i < r1; i += bd) {
-        const double pi = d.p[i];
-        d.x[i] = fma(alpha, pi, d.x[i]);
-        const double ri = fma(-alpha, d.q[i], d.r[i]);
-        const double zi = d.dinv[i] * ri;
-        d.r[i] = ri;
-        d.z[i] = zi;
+      const double* pown = RES ? pe : pcur + r0;
+      for (int i = tid; i < nloc; i += bd) {
+        L.x[i] = fma(alpha, pown[i], L.x[i]);
+        const double ri = fma(-alpha, L.q[i], L.r[i]);
+        const double zi = L.di[i] * ri;
+        L.r[i] = ri;
+        L.z[i] = zi;
+        if (RES) d.z[r0 + i] = zi;
         v2[0] += ri * zi;
         v2[1] += ri * ri;
       }
+      kd = k + 1;
       put_partials<2>(d, lb, red, v2, sh);
       if (!grp.sync(sh)) return;
+      get_totals_then<2>(d, red, sh, derive_rz);
+      ++red;
     }
     ++k;
   }
-  if (!project_x(d, lb, r0, r1, grp, sh, red)) return;
-  double tr = 0.0;
-  if (!true_residual<T>(d, lb, r0, r1, grp, sh, red, tr)) return;
-  finish(d, lb, status, k, 0, rnorm / bnorm, sqrt(tr) / bnorm, bnorm);
+  // ---- x -= mean(x), published; true residual ----
+  {
+    double v1[1] = {0.0};
+    for (int i = tid; i < nloc; i += bd) v1[0] += L.x[i];
+    put_partials<1>(d, lb, red, v1, sh);
+    if (!grp.sync(sh)) return;
+    get_totals<1>(d, red, sh);
+    ++red;
+  }
+  const double mxf = sh.tot[0] / d.n;
+  for (int i = tid; i < nloc; i += bd) {
+    const double xi = L.x[i] - mxf;
+    L.x[i] = xi;
+    if (RES) {
+      d.x[r0 + i] = xi;
+      pe[i] = xi;
+    }
+  }
+  if (!grp.sync(sh)) return;
+  {
+    double v1[1] = {0.0};
+    auto op = [&](int il, double s) {
+      const double t = L.bp[il] - s;
+      v1[0] += t * t;
+    };
+    if constexpr (RES) {
+      for (int h = tid; h < nh; h += bd) pe[nloc + h] = __ldcg(d.x + hid[h]);
+      __syncthreads();
+      spmv_ext<T>(L.row, L.col, L.val, pe, nloc, op);
+    } else {
+      spmv_local<T, double>(
+          L, r0, nloc, [&](int jl) { return L.x[jl]; }, [&](int j) { return __ldcg(d.x + j); }, op);
+    }
+    put_partials<1>(d, lb, red, v1, sh);
+    if (!grp.sync(sh)) return;
+    get_totals<1>(d, red, sh);
+    ++red;
+  }
+  finish(d, lb, status, k, 0, sqrt(sh.sc[0]) / bnorm, sqrt(sh.tot[0]) / bnorm, bnorm);
 }
 
 template <int T>
-__device__ void solve_mixed(const Desc& d, int lb) {
-  __shared__ Shared sh;
+__device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
   const int tid = threadIdx.x, bd = blockDim.x;
   const int chunk = (d.n + d.nblk - 1) / d.nblk;
   const int r0 = min(d.n, lb * chunk), r1 = min(d.n, r0 + chunk);
@@ -499,13 +887,14 @@ __device__ void solve_mixed(const Desc& d, int lb) {
   finish(d, lb, status, total, sweeps, rel, rel, bnorm);
 }
 
-template <int T>
+template <int T, bool RES>
 __global__ void __launch_bounds__(MAX_BLOCK) pcg_persistent_kernel(Desc d) {
+  __shared__ Shared sh;
   mark_pending(d, blockIdx.x);
   if (d.mixed)
-    solve_mixed<T>(d, blockIdx.x);
+    solve_mixed<T>(d, blockIdx.x, sh);
   else
-    solve_fp64<T>(d, blockIdx.x);
+    solve_fp64<T, RES>(d, blockIdx.x, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -534,13 +923,13 @@ __global__ void __launch_bounds__(256) spmv_kernel(int n, const int* __restrict_
 
 using PcgFn = void (*)(Desc);
 
-PcgFn pcg_kernel_for(int lanes) {
+PcgFn pcg_kernel_for(int lanes, bool res) {
   switch (lanes) {
-    case 1: return pcg_persistent_kernel<1>;
-    case 2: return pcg_persistent_kernel<2>;
-    case 4: return pcg_persistent_kernel<4>;
-    case 8: return pcg_persistent_kernel<8>;
-    case 32: return pcg_persistent_kernel<32>;
+    case 1: return res ? pcg_persistent_kernel<1, true> : pcg_persistent_kernel<1, false>;
+    case 2: return res ? pcg_persistent_kernel<2, true> : pcg_persistent_kernel<2, false>;
+    case 4: return res ? pcg_persistent_kernel<4, true> : pcg_persistent_kernel<4, false>;
+    case 8: return res ? pcg_persistent_kernel<8, true> : pcg_persistent_kernel<8, false>;
+    case 32: return res ? pcg_persistent_kernel<32, true> : pcg_persistent_kernel<32, false>;
     default: return nullptr;
   }
 }
@@ -558,10 +947,137 @@ DevInfo dev_info(int device) {
   return cache[device];
 }
 
-int coresident_blocks(PcgFn fn, int block, int device) {
+int coresident_blocks(PcgFn fn, int block, int device, size_t smem = 0) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, block, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return per_sm * dev_info(device).sms;
+}
+
+int optin_smem(int device) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  return v;
+}
+
+struct LaunchPlan {
+  PcgFn fn = nullptr;
+  int nblk = 1;
+  int block = 512;
+  size_t smem = 0;
+  int nnz_cap = 0;
+  int halo_cap = 0;
+  bool res = false;
+  HaloPlan halo;
+};
+
+// Build (once per block count) the row partition and halo lists of a mesh.
+int get_halo_plan(cgp_mesh_impl* m, int nblk, HaloPlan& out) {
+  for (const HaloPlan& p : m->plans)
+    if (p.nblk == nblk) {
+      out = p;
+      return CGP_OK;
+    }
+  const int n = m->n_c, nnz = m->nnz;
+  const int chunk = (n + nblk - 1) / nblk;
+  const std::vector<int>& rp = m->h_rowptr;
+  const std::vector<int>& cl = m->h_col;
+  std::vector<int> lcol(nnz), hptr(nblk + 1, 0), hidx, h;
+  HaloPlan p;
+  p.nblk = nblk;
+  for (int b = 0; b < nblk; ++b) {
+    const int r0 = std::min(n, b * chunk), r1 = std::min(n, r0 + chunk), nloc = r1 - r0;
+    const int k0 = rp[r0], k1 = rp[r1];
+    h.clear();
+    for (int k = k0; k < k1; ++k)
+      if (cl[k] < r0 || cl[k] >= r1) h.push_back(cl[k]);
+    std::sort(h.begin(), h.end());
+    h.erase(std::unique(h.begin(), h.end()), h.end());
+    for (int k = k0; k < k1; ++k) {
+      const int j = cl[k];
+      lcol[k] = (j >= r0 && j < r1) ? j - r0
+                                    : nloc + (int)(std::lower_bound(h.begin(), h.end(), j) - h.begin());
+    }
+    hptr[b + 1] = hptr[b] + (int)h.size();
+    hidx.insert(hidx.end(), h.begin(), h.end());
+    p.max_rows = std::max(p.max_rows, nloc);
+    p.max_nnz = std::max(p.max_nnz, k1 - k0);
+    p.max_halo = std::max(p.max_halo, (int)h.size());
+  }
+  const size_t b_lcol = (size_t)nnz * 4, b_hptr = (size_t)(nblk + 1) * 4, b_hidx = std::max<size_t>(1, hidx.size()) * 4;
+  const size_t o_hptr = (b_lcol + 255) / 256 * 256, o_hidx = o_hptr + (b_hptr + 255) / 256 * 256;
+  CGP_CUDA(cudaMalloc(&p.base, o_hidx + b_hidx));
+  char* base = static_cast<char*>(p.base);
+  p.lcol = (int*)base;
+  p.hptr = (int*)(base + o_hptr);
+  p.hidx = (int*)(base + o_hidx);
+  cudaError_t e = cudaMemcpy(p.lcol, lcol.data(), b_lcol, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p.hptr, hptr.data(), b_hptr, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !hidx.empty()) e = cudaMemcpy(p.hidx, hidx.data(), hidx.size() * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(p.base);
+    return cuda_fail(e, "cudaMemcpy(halo plan)");
+  }
+  m->plans.push_back(p);
+  out = p;
+  return CGP_OK;
+}
+
+// Shape of a persistent launch for an n-row system.  For FP64 on a mesh the
+// block's rows go to shared memory when the largest chunk, its halo and its
+// CSR slice fit and the grid stays co-resident.
+int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const SolverTuning& tu, bool mixed,
+               LaunchPlan& out) {
+  const int lanes = tu.lanes > 0 ? tu.lanes : 1;
+  const int block = tu.block > 0 ? tu.block : 512;
+  PcgFn fn0 = pcg_kernel_for(lanes, false);
+  if (!fn0) return fail(CGP_ERR_INVALID_ARG, "solver tuning: lanes must be 1, 2, 4, 8 or 32");
+  if (block < 64 || block > MAX_BLOCK || block % 32 != 0 || block % lanes != 0)
+    return fail(CGP_ERR_INVALID_ARG, "solver tuning: block must be a multiple of 32 in [64, 512]");
+  const int cap0 = std::min(coresident_blocks(fn0, block, device), max_blocks);
+  if (cap0 <= 0) return fail(CGP_ERR_CUDA, "solver: kernel cannot be resident on this device");
+  const int sms = std::max(1, dev_info(device).sms);
+  int nblk = tu.blocks;
+  if (nblk <= 0) nblk = n <= 4096 ? 1 : std::min(sms, (n + 767) / 768);
+  nblk = std::max(1, std::min(nblk, std::min(cap0, n)));
+  out = LaunchPlan{};
+  out.fn = fn0;
+  out.nblk = nblk;
+  out.block = block;
+  if (mixed || !m || (tu.flags & 1)) return CGP_OK;
+  const int chunk = (n + nblk - 1) / nblk;
+  // rough size check before building a plan
+  const int rough_nnz = m->h_rowptr[std::min(n, chunk)] - m->h_rowptr[0];
+  PcgFn fnr = pcg_kernel_for(lanes, true);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, (const void*)fnr) != cudaSuccess) {
+    cudaGetLastError();
+    return CGP_OK;
+  }
+  const size_t limit = (size_t)std::max(0, optin_smem(device) - (int)fa.sharedSizeBytes - 1024);
+  if ((size_t)chunk * 56 + (size_t)rough_nnz * 12 > limit) return CGP_OK;
+  HaloPlan hp;
+  int st = get_halo_plan(m, nblk, hp);
+  if (st != CGP_OK) return st;
+  size_t smem = 8 * ((size_t)7 * chunk + hp.max_halo + hp.max_nnz) +
+                4 * ((size_t)chunk + 1 + hp.max_nnz + hp.max_halo);
+  smem = (smem + 15) / 16 * 16;
+  if (smem > limit) return CGP_OK;
+  if (cudaFuncSetAttribute((const void*)fnr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return CGP_OK;
+  }
+  if (coresident_blocks(fnr, block, device, smem) < nblk) return CGP_OK;
+  out.fn = fnr;
+  out.smem = smem;
+  out.nnz_cap = hp.max_nnz;
+  out.halo_cap = hp.max_halo;
+  out.res = true;
+  out.halo = hp;
+  return CGP_OK;
 }
 
 }  // namespace
@@ -576,17 +1092,10 @@ int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_o
                  cudaStream_t s) {
   const bool mixed = o.precision == CGP_MIXED;
   const SolverTuning& tu = m->tune[mixed ? CGP_TUNE_SOLVE_MIXED : CGP_TUNE_SOLVE_FP64];
-  const int lanes = tu.lanes > 0 ? tu.lanes : 1;
-  const int block = tu.block > 0 ? tu.block : 512;
-  PcgFn fn = pcg_kernel_for(lanes);
-  if (!fn) return fail(CGP_ERR_INVALID_ARG, "solver tuning: lanes must be 1, 2, 4, 8 or 32");
-  if (block < 64 || block > MAX_BLOCK || block % 32 != 0 || block % lanes != 0)
-    return fail(CGP_ERR_INVALID_ARG, "solver tuning: block must be a multiple of 32 in [64, 1024]");
-  const int cap = std::min(coresident_blocks(fn, block, m->device), m->max_blocks);
-  if (cap <= 0) return fail(CGP_ERR_CUDA, "solver: kernel cannot be resident on this device");
-  int nblk = tu.blocks;
-  if (nblk <= 0) nblk = m->n_c <= 16384 ? 1 : (m->n_c + block - 1) / block;
-  nblk = std::max(1, std::min(nblk, std::min(cap, m->n_c)));
+  LaunchPlan plan;
+  int st = plan_solve(m, m->device, m->n_c, m->max_blocks, tu, mixed, plan);
+  if (st != CGP_OK) return st;
+  const int nblk = plan.nblk;
   // barrier epochs stay far below 2^32 / nblk
   const long long max_epochs = 8LL + 4LL * (long long)std::max(o.max_it, 1) + 8LL * std::max(o.max_sweeps, 1);
   if (max_epochs * nblk >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "solver: max_it too large");
@@ -605,6 +1114,7 @@ int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_o
   d.r = m->r;
   d.z = m->z;
   d.p = m->p;
+  d.p2 = m->p2;
   d.q = m->q;
   d.r32 = m->r32;
   d.z32 = m->z32;
@@ -624,12 +1134,18 @@ int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_o
   d.max_sweeps = o.max_sweeps;
   d.use_x0 = o.use_x0;
   d.mixed = mixed ? 1 : 0;
+  d.res_nnz_cap = plan.nnz_cap;
+  d.halo_cap = plan.halo_cap;
+  d.lcol = plan.halo.lcol;
+  d.hptr = plan.halo.hptr;
+  d.hidx = plan.halo.hidx;
   d.spin_ns = 2000000000LL;
 
-  CGP_CUDA(cudaMemsetAsync(m->bar, 0, 64, s));
+  CGP_CUDA(cudaMemsetAsync(m->bar, 0, 256, s));
   CGP_CUDA(cudaMemsetAsync(m->res, 0, sizeof(SolveResult), s));
   void* args[] = {&d};
-  CGP_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(nblk), dim3(block), args, 0, s));
+  CGP_CUDA(cudaLaunchCooperativeKernel((const void*)plan.fn, dim3(nblk), dim3(plan.block), args, plan.smem, s));
+  m->last_plan[mixed ? 1 : 0] = PlanRecord{nblk, plan.block, plan.res ? 1 : 0, (int)plan.smem};
   return CGP_OK;
 }
 
@@ -650,12 +1166,11 @@ void (*spmv_for(int lanes))(int, const int*, const int*, const V*, const V*, V*)
 
 int launch_solve_fp64_raw(int device, const RawSystem& sys, const RawScratch& scr, const double* b, double* x,
                           const cgp_solve_opts& o, cudaStream_t s) {
-  const int block = 512;
-  PcgFn fn = pcg_kernel_for(1);
-  const int cap = std::min(coresident_blocks(fn, block, device), scr.max_blocks);
-  if (cap <= 0) return fail(CGP_ERR_CUDA, "solver: kernel cannot be resident on this device");
-  int nblk = sys.n <= 16384 ? 1 : (sys.n + block - 1) / block;
-  nblk = std::max(1, std::min(nblk, std::min(cap, sys.n)));
+  LaunchPlan plan;
+  const SolverTuning tu{0, 1, 0, 1};   // default shape, vectors in global scratch
+  int st = plan_solve(nullptr, device, sys.n, scr.max_blocks, tu, false, plan);
+  if (st != CGP_OK) return st;
+  const int nblk = plan.nblk;
   const long long max_epochs = 8LL + 4LL * (long long)std::max(o.max_it, 1);
   if (max_epochs * nblk >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "solver: max_it too large");
   Desc d{};
@@ -670,6 +1185,7 @@ int launch_solve_fp64_raw(int device, const RawSystem& sys, const RawScratch& sc
   d.r = scr.r;
   d.z = scr.z;
   d.p = scr.p;
+  d.p2 = scr.p2;
   d.q = scr.q;
   d.part = scr.part;
   d.part_stride = scr.max_blocks;
@@ -684,9 +1200,10 @@ int launch_solve_fp64_raw(int device, const RawSystem& sys, const RawScratch& sc
   d.max_sweeps = 1;
   d.use_x0 = o.use_x0;
   d.mixed = 0;
+  d.res_nnz_cap = 0;
   d.spin_ns = 2000000000LL;
   void* args[] = {&d};
-  CGP_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(nblk), dim3(block), args, 0, s));
+  CGP_CUDA(cudaLaunchCooperativeKernel((const void*)plan.fn, dim3(nblk), dim3(plan.block), args, 0, s));
   return CGP_OK;
 }
 
@@ -778,28 +1295,43 @@ extern "C" int cgp_poisson_solve(cgp_mesh m, const double* b, double* x, const c
   return CGP_OK;
 }
 
-static bool valid_shape(int block, int lanes) {
-  if (block != 0 && (block < 64 || block > MAX_BLOCK || block % 32 != 0)) return false;
+static bool valid_shape(int what, int block, int lanes) {
+  const int max_block = (what == CGP_TUNE_SOLVE_FP64 || what == CGP_TUNE_SOLVE_MIXED) ? MAX_BLOCK : 256;
+  if (block != 0 && (block < 64 || block > max_block || block % 32 != 0)) return false;
   if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 32) return false;
   return true;
 }
 
-extern "C" int cgp_set_tuning(cgp_mesh m, int what, int block, int lanes, int blocks) {
+extern "C" int cgp_set_tuning(cgp_mesh m, int what, int block, int lanes, int blocks, int flags) {
   if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: NULL mesh");
   if (what < 0 || what > 3) return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: unknown target");
-  if (!valid_shape(block, lanes) || blocks < 0)
-    return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: block must be 0 or a multiple of 32 in [64, 1024], "
-                                     "lanes 0, 1, 2, 4, 8 or 32, blocks >= 0");
-  m->tune[what] = SolverTuning{block, lanes, blocks};
+  if (!valid_shape(what, block, lanes) || blocks < 0 || (flags & ~1))
+    return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: block must be 0 or a multiple of 32 in [64, 512] "
+                                     "(solver) or [64, 256] (SpMV), "
+                                     "lanes 0, 1, 2, 4, 8 or 32, blocks >= 0, flags 0 or 1");
+  m->tune[what] = SolverTuning{block, lanes, blocks, flags};
   return CGP_OK;
 }
 
-extern "C" int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks) {
+extern "C" int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks, int* flags) {
   if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_get_tuning: NULL mesh");
   if (what < 0 || what > 3) return fail(CGP_ERR_INVALID_ARG, "cgp_get_tuning: unknown target");
   if (block) *block = m->tune[what].block;
   if (lanes) *lanes = m->tune[what].lanes;
   if (blocks) *blocks = m->tune[what].blocks;
+  if (flags) *flags = m->tune[what].flags;
+  return CGP_OK;
+}
+
+extern "C" int cgp_last_launch(cgp_mesh m, int precision, int* blocks, int* block, int* resident,
+                               int* smem_bytes) {
+  if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_last_launch: NULL mesh");
+  if (precision != CGP_FP64 && precision != CGP_MIXED) return fail(CGP_ERR_INVALID_ARG, "cgp_last_launch: precision");
+  const PlanRecord& r = m->last_plan[precision == CGP_MIXED ? 1 : 0];
+  if (blocks) *blocks = r.blocks;
+  if (block) *block = r.block;
+  if (resident) *resident = r.resident;
+  if (smem_bytes) *smem_bytes = r.smem;
   return CGP_OK;
 }
 

@@ -31,9 +31,10 @@ constexpr size_t kOffBp = 0;
 constexpr size_t kOffR = kOffBp + kVec;
 constexpr size_t kOffZ = kOffR + kVec;
 constexpr size_t kOffP = kOffZ + kVec;
-constexpr size_t kOffQ = kOffP + kVec;
+constexpr size_t kOffP2 = kOffP + kVec;
+constexpr size_t kOffQ = kOffP2 + kVec;
 constexpr size_t kOffPart = kOffQ + kVec;
-constexpr size_t kOffBar = kOffPart + (size_t)16 * kStaticMaxBlocks * sizeof(double);
+constexpr size_t kOffBar = kOffPart + (size_t)32 * kStaticMaxBlocks * sizeof(double);
 constexpr size_t kOffRes = kOffBar + 256;
 constexpr size_t kStaticBytes = kOffRes + 256;
 static_assert(sizeof(cgp::SolveResult) <= 256, "result record must fit its slot");
@@ -88,6 +89,7 @@ extern "C" int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* co
   scr.r = reinterpret_cast<double*>(base + kOffR);
   scr.z = reinterpret_cast<double*>(base + kOffZ);
   scr.p = reinterpret_cast<double*>(base + kOffP);
+  scr.p2 = reinterpret_cast<double*>(base + kOffP2);
   scr.q = reinterpret_cast<double*>(base + kOffQ);
   scr.part = reinterpret_cast<double*>(base + kOffPart);
   scr.max_blocks = kStaticMaxBlocks;

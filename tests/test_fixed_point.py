@@ -1,0 +1,99 @@
+"""The solver's integer-pipe reductions against exact rational sums (CPU only).
+
+Dot products inside the persistent CG kernel are summed as 128-bit
+fixed-point integers aligned to a common exponent (per warp, per block and
+across blocks) and converted back to the nearest double.  These tests build
+the same arithmetic on the host and compare it with the correctly rounded
+exact sum of the same doubles, computed with Python fractions.
+"""
+import math
+import os
+import shutil
+import struct
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    out = tmp_path_factory.mktemp("fx") / "fx_harness"
+    subprocess.check_call([cxx, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_2003_00082_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "fixed_point_harness.cpp"), "-o", str(out)])
+    return str(out)
+
+
+def bits(v):
+    return struct.unpack("<Q", struct.pack("<d", float(v)))[0]
+
+
+def run(harness, groups):
+    text = "".join(f"G {len(g)}\n" + " ".join(f"{bits(v):x}" for v in g) + "\n" for g in groups)
+    r = subprocess.run([harness], input=text, capture_output=True, text=True, check=True)
+    return struct.unpack("<d", struct.pack("<Q", int(r.stdout.strip(), 16)))[0]
+
+
+def exact(groups):
+    return float(sum((Fraction(float(v)) for g in groups for v in g), Fraction(0)))
+
+
+def ulp_diff(a, b):
+    if a == b:
+        return 0
+    return abs(a - b) / math.ulp(max(abs(a), abs(b)))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_fixed_point_sum_is_the_correctly_rounded_sum(harness, seed):
+    rng = np.random.default_rng(seed)
+    ngroups = int(rng.integers(1, 40))
+    groups = []
+    for _ in range(ngroups):
+        n = int(rng.integers(1, 64))
+        scale = 10.0 ** rng.uniform(-8, 8, size=n)
+        groups.append(list(rng.standard_normal(n) * scale))
+    got = run(harness, groups)
+    want = exact(groups)
+    assert ulp_diff(got, want) <= 1, (got, want)
+
+
+def test_cancellation_and_signs(harness):
+    groups = [[1e16, 1.0, -1e16], [3.0, -3.0], [2.0 ** -40]]
+    assert run(harness, groups) == exact(groups)
+    groups = [[0.1] * 10, [-0.1] * 10]
+    assert run(harness, groups) == 0.0
+    assert run(harness, [[0.0, -0.0]]) == 0.0
+
+
+def test_ties_round_to_even(harness):
+    # 2^53 + 1 is a tie between 2^53 and 2^53 + 2: rounds to the even 2^53
+    groups = [[2.0 ** 53, 1.0]]
+    assert run(harness, groups) == 2.0 ** 53
+    groups = [[2.0 ** 53, 3.0]]
+    assert run(harness, groups) == 2.0 ** 53 + 4.0
+
+
+def test_subnormal_and_tiny_values(harness):
+    tiny = 5e-324
+    assert run(harness, [[tiny, tiny]]) == 2 * tiny
+    groups = [[1e-310, 2e-310], [-5e-311]]
+    assert run(harness, groups) == exact(groups)
+
+
+def test_non_finite_input_gives_nan(harness):
+    assert math.isnan(run(harness, [[1.0, float("inf")], [2.0]]))
+    assert math.isnan(run(harness, [[float("nan")]]))
+
+
+def test_large_sums_do_not_overflow(harness):
+    groups = [[1.7e308 / 4096] * 64 for _ in range(32)]     # 2048 terms near the top of the range
+    got = run(harness, groups)
+    want = exact(groups)
+    assert ulp_diff(got, want) <= 1

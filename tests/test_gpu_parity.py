@@ -150,16 +150,22 @@ def oracle_rhs(om, u, v, kind=0, B=(0.0, 1.0, 1.0)):
 SHAPES = [(128, 1, 1), (128, 2, 5), (128, 4, 3), (256, 8, 7), (64, 32, 2), (64, 1, 13), (512, 1, 0)]
 
 
+@pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("block,lanes,blocks", SHAPES)
-def test_fp64_solve_matches_oracle(pair, cgp, block, lanes, blocks):
+def test_fp64_solve_matches_oracle(pair, cgp, block, lanes, blocks, flags):
     m, om = pair
     u, v = velocity_for(om)
     b = oracle_rhs(om, u, v)
     ref = O.pcg(om.K, om.d, b, tol=1e-12)
-    cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64, block, lanes, blocks)
+    cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64, block, lanes, blocks, flags)
     x = torch.zeros(m.n_c, dtype=torch.float64, device=DEV)
     info = cgp.cgp_poisson_solve(m.handle, T(b), x, tol=1e-12)
-    cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64, 0, 0, 0)
+    launch = cgp.cgp_last_launch(m.handle)
+    cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64, 0, 0, 0, 0)
+    if flags == 1:
+        assert launch["resident"] == 0
+    elif m.n_c <= 600:
+        assert launch["resident"] == 1, launch     # these systems always fit in shared memory
     assert info["status"] == cgp.CGP_OK, info
     assert abs(info["iterations"] - ref["iterations"]) <= 2
     xs = x.cpu().numpy()

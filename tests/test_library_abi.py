@@ -67,7 +67,7 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert e.value.status == cgp.CGP_ERR_INVALID_ARG
     # NULL handles
     assert lib.cgp_prolong(None, None, None, None) == cgp.CGP_ERR_INVALID_ARG
-    assert lib.cgp_set_tuning(None, 0, 0, 0, 0) == cgp.CGP_ERR_INVALID_ARG
+    assert lib.cgp_set_tuning(None, 0, 0, 0, 0, 0) == cgp.CGP_ERR_INVALID_ARG
     assert lib.cgp_barrier_selftest(0, 0, 1, None) == cgp.CGP_ERR_INVALID_ARG
     assert b"nblk" in lib.cgp_last_error()
 
