@@ -99,11 +99,9 @@ struct cgp_mesh_impl {
   double* p = nullptr;
   double* p2 = nullptr;
   double* q = nullptr;
-  float* r32 = nullptr;
-  float* z32 = nullptr;
-  float* p32 = nullptr;
-  float* q32 = nullptr;
-  float* d32 = nullptr;
+  float* f32pub = nullptr;   // [6 n] mixed: published R[2], W[2], S[2]
+  float* f32own = nullptr;   // [6 n] mixed without shared-memory residency: own inner vectors
+  float* fpart = nullptr;    // [8 * max_blocks] FP32 partial sums
   double* part = nullptr;    // [max_blocks * 32] per-block fixed-point partial sums
   unsigned* bar = nullptr;   // grid barrier counter
   SolveResult* res = nullptr;

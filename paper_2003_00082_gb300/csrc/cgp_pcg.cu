@@ -20,7 +20,8 @@
 // The Neumann null space (constants) is handled by mean-zero projection of
 // b, of x0 and of the final x.  MIXED precision wraps FP32 inner solves in
 // FP64 iterative refinement: r = b - K x, r -= mean(r), stop test, inner
-// PCG32 on K32 d = r32 to inner_tol, x += d, x -= mean(x).
+// FP32 CG (single-reduction form) on K32 e = r to inner_tol, x += e,
+// x -= mean(x).
 //
 // Barriers spin on a counter with a wall-clock limit; a block that gives up
 // raises a flag that makes every other block leave at its next barrier, and
@@ -56,11 +57,9 @@ struct Desc {
   double* p;
   double* p2;         // second buffer of p (FP64 solver)
   double* q;
-  float* r32;
-  float* z32;
-  float* p32;
-  float* q32;
-  float* d32;
+  float* f32pub;      // mixed: published R[2], W[2], S[2] ([6][n])
+  float* f32own;      // mixed without RES: own r, u, w, p, s, e ([6][n])
+  float* fpart;       // mixed: FP32 partial slots [2][NCOMP][part_stride]
   double* part;
   int part_stride;
   unsigned* bar;
@@ -103,6 +102,9 @@ struct Shared {
   double tot[NCOMP];
   double sc[8];                 // scalars computed by one lane and broadcast
   int isc[4];
+  float fred[4][32];            // FP32 reductions of the inner solve
+  float ftot[4];
+  float fsc[8];
   int flag;
 };
 
@@ -308,28 +310,6 @@ __device__ __forceinline__ void get_totals_then(const Desc& d, int red, Shared& 
   __syncthreads();
 }
 
-// Row-wise SpMV over rows [r0, r1) with T lanes per row; `op(i, s)` is called
-// by lane 0 of the row's group with s = (A x)_i.  x is read through L2 (it is
-// written by other blocks between barriers).
-template <int T, typename V, typename Op>
-__device__ __forceinline__ void spmv_rows(const int* __restrict__ rowptr, const int* __restrict__ col,
-                                          const V* __restrict__ val, const V* x, int r0, int r1, Op op) {
-  const int g = threadIdx.x / T, l = threadIdx.x % T, ng = blockDim.x / T;
-  for (int base = r0; base < r1; base += ng) {
-    const int i = base + g;
-    V s = V(0);
-    if (i < r1) {
-      const int k1 = rowptr[i + 1];
-      for (int k = rowptr[i] + l; k < k1; k += T) s = fma(val[k], __ldcg(x + col[k]), s);
-    }
-    if (T > 1) {
-#pragma unroll
-      for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, T);
-    }
-    if (i < r1 && l == 0) op(i, s);
-  }
-}
-
 __device__ void finish(const Desc& d, int lb, int status, int its, int sweeps, double rel_rec, double rel_true,
                        double bnorm) {
   if (lb == 0 && threadIdx.x == 0) {
@@ -360,66 +340,6 @@ __device__ __forceinline__ void mark_pending(const Desc& d, int lb) {
     d.out->rel_res_true = 0.0;
     d.out->status = CGP_ERR_TIMEOUT;
   }
-}
-
-// Set-up shared by both precisions: bp = b - mean(b), x = x0 - mean(x0) or 0.
-// Returns ||bp|| (identical in all blocks), or a negative value if the group
-// barrier failed.
-__device__ double setup(const Desc& d, int lb, int r0, int r1, Group& grp, Shared& sh, int& red) {
-  const int tid = threadIdx.x, bd = blockDim.x;
-  double v2[2] = {0.0, 0.0};
-  for (int i = r0 + tid; i < r1; i += bd) {
-    v2[0] += d.b[i];
-    if (d.use_x0) v2[1] += d.x[i];
-  }
-  put_partials<2>(d, lb, red, v2, sh);
-  if (!grp.sync(sh)) return -1.0;
-  get_totals<2>(d, red, sh);
-  ++red;
-  const double mb = sh.tot[0] / d.n, mx = sh.tot[1] / d.n;
-  double v1[1] = {0.0};
-  for (int i = r0 + tid; i < r1; i += bd) {
-    const double bi = d.b[i] - mb;
-    d.bp[i] = bi;
-    v1[0] += bi * bi;
-    d.x[i] = d.use_x0 ? d.x[i] - mx : 0.0;
-  }
-  put_partials<1>(d, lb, red, v1, sh);
-  if (!grp.sync(sh)) return -1.0;
-  get_totals<1>(d, red, sh);
-  ++red;
-  return sqrt(sh.tot[0]);
-}
-
-// x -= mean(x) over the group, leaving x complete after a barrier.
-__device__ bool project_x(const Desc& d, int lb, int r0, int r1, Group& grp, Shared& sh, int& red) {
-  const int tid = threadIdx.x, bd = blockDim.x;
-  double v1[1] = {0.0};
-  for (int i = r0 + tid; i < r1; i += bd) v1[0] += d.x[i];
-  put_partials<1>(d, lb, red, v1, sh);
-  if (!grp.sync(sh)) return false;
-  get_totals<1>(d, red, sh);
-  ++red;
-  const double mx = sh.tot[0] / d.n;
-  for (int i = r0 + tid; i < r1; i += bd) d.x[i] -= mx;
-  return grp.sync(sh);
-}
-
-// ||bp - K x||^2 over the group (x complete).
-template <int T>
-__device__ bool true_residual(const Desc& d, int lb, int r0, int r1, Group& grp, Shared& sh, int& red,
-                              double& out) {
-  double v1[1] = {0.0};
-  spmv_rows<T, double>(d.rowptr, d.col, d.val, d.x, r0, r1, [&](int i, double s) {
-    const double t = d.bp[i] - s;
-    v1[0] += t * t;
-  });
-  put_partials<1>(d, lb, red, v1, sh);
-  if (!grp.sync(sh)) return false;
-  get_totals<1>(d, red, sh);
-  ++red;
-  out = sh.tot[0];
-  return true;
 }
 
 // Own-row storage of one block: in shared memory (RES) or in global scratch.
@@ -758,48 +678,251 @@ __device__ void solve_fp64(const Desc& d, int lb, Shared& sh) {
   finish(d, lb, status, k, 0, sqrt(sh.sc[0]) / bnorm, sqrt(sh.tot[0]) / bnorm, bnorm);
 }
 
-template <int T>
+// ---------------------------------------------------------------------------
+// FP32 reductions of the inner solve: warp trees on the FP32 pipe, one slot
+// per block, every block sums the slots in the same order (deterministic).
+// ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ void put_partials_f(const Desc& d, int lb, int red, const float (&v)[NC], Shared& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const float s = warp_sum(v[c]);
+    if (lane == 0) sh.fred[c][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float s = lane < nw ? sh.fred[c][lane] : 0.0f;
+      s = warp_sum(s);
+      if (lane == 0) d.fpart[((red & 1) * NCOMP + c) * d.part_stride + lb] = s;
+    }
+  }
+}
+
+template <int NC, typename F>
+__device__ __forceinline__ void get_totals_f_then(const Desc& d, int red, Shared& sh, F derive) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float* src = d.fpart + ((red & 1) * NCOMP + c) * d.part_stride;
+      float s = 0.0f;
+      for (int j = lane; j < d.nblk; j += 32) s += __ldcg(src + j);
+      s = warp_sum(s);
+      if (lane == 0) sh.ftot[c] = s;
+    }
+    if (lane == 0) derive(sh);
+  }
+  __syncthreads();
+}
+
+// FP32 SpMV over the block's rows reading the global CSR: own columns from
+// own(jl), other columns from halo(j).
+template <int T, typename FOwn, typename FHalo, typename Op>
+__device__ __forceinline__ void spmv_local_f(const int* __restrict__ row, const int* __restrict__ col,
+                                             const float* __restrict__ val, int r0, int nloc, FOwn own,
+                                             FHalo halo, Op op) {
+  const int g = threadIdx.x / T, l = threadIdx.x % T, ng = blockDim.x / T;
+  for (int base = 0; base < nloc; base += ng) {
+    const int il = base + g;
+    float s = 0.0f;
+    if (il < nloc) {
+      const int k1 = row[il + 1];
+      for (int k = row[il] + l; k < k1; k += T) {
+        const int jl = col[k] - r0;
+        const float v = ((unsigned)jl < (unsigned)nloc) ? own(jl) : halo(jl + r0);
+        s = fmaf(val[k], v, s);
+      }
+    }
+    if (T > 1) {
+#pragma unroll
+      for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, T);
+    }
+    if (il < nloc && l == 0) op(il, s);
+  }
+}
+
+// FP32 SpMV over the block's rows with a gathered local vector (RES) or with
+// halo values computed on the fly from published buffers (no RES).
+template <int T, typename Op>
+__device__ __forceinline__ void spmv_ext32(const int* __restrict__ row, const int* __restrict__ col,
+                                           const float* __restrict__ val, const float* ext, int nloc, Op op) {
+  const int g = threadIdx.x / T, l = threadIdx.x % T, ng = blockDim.x / T;
+  for (int base = 0; base < nloc; base += ng) {
+    const int il = base + g;
+    float s = 0.0f;
+    if (il < nloc) {
+      const int k1 = row[il + 1];
+      for (int k = row[il] + l; k < k1; k += T) s = fmaf(val[k], ext[col[k]], s);
+    }
+    if (T > 1) {
+#pragma unroll
+      for (int o = T / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, T);
+    }
+    if (il < nloc && l == 0) op(il, s);
+  }
+}
+
+// Mixed precision: FP64 iterative refinement around FP32 inner solves.
+//
+// Outer (FP64, global memory): r = bp - K x, r -= mean(r), stop when
+// ||r|| <= tol ||bp||; after each inner solve x += e, x -= mean(x).
+// Inner (FP32): Jacobi-preconditioned CG in the single-reduction form of
+// Chronopoulos and Gear (the recurrence s = w + beta s replaces the product
+// A p, and (r,u), (w,u), (r,r) share one reduction), solving K e = r from
+// e = 0 to ||r_inner|| <= inner_tol ||r||.  One barrier per inner
+// iteration: the product w = A u needs u_j of rows owned elsewhere, which
+// each block rebuilds from the owner's published r_j, w_j, s_j (kept in two
+// buffers by iteration parity) with the owner's own FMAs.
+template <int T, bool RES>
 __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   const int tid = threadIdx.x, bd = blockDim.x;
   const int chunk = (d.n + d.nblk - 1) / d.nblk;
-  const int r0 = min(d.n, lb * chunk), r1 = min(d.n, r0 + chunk);
+  const int r0 = min(d.n, lb * chunk), r1 = min(d.n, r0 + chunk), nloc = r1 - r0;
+  const size_t n = d.n;
   Group grp{d.bar, &d.res->timeout, (unsigned)d.nblk, 0u, d.spin_ns};
   int red = 0;
 
-  const double bnorm = setup(d, lb, r0, r1, grp, sh, red);
-  if (bnorm < 0.0) return;
+  // published buffers (global): R0/R1, W0/W1, S0/S1 by iteration parity
+  float* const R0 = d.f32pub;
+  float* const R1 = d.f32pub + n;
+  float* const W0 = d.f32pub + 2 * n;
+  float* const W1 = d.f32pub + 3 * n;
+  float* const S0 = d.f32pub + 4 * n;
+  float* const S1 = d.f32pub + 5 * n;
+  // own inner vectors and the local system
+  float *ir, *iu, *iw, *ip, *is, *ie, *ext = nullptr, *dih = nullptr;
+  const float* di;
+  const int *row, *col, *hid = nullptr;
+  const float* val;
+  int nh = 0;
+  if constexpr (RES) {
+    float* f = reinterpret_cast<float*>(dsm);
+    ir = f;
+    iu = f + chunk;
+    iw = f + 2 * chunk;
+    ip = f + 3 * chunk;
+    is = f + 4 * chunk;
+    ie = f + 5 * chunk;
+    float* dil = f + 6 * chunk;
+    ext = f + 7 * chunk;                   // [chunk + halo_cap]
+    dih = ext + chunk + d.halo_cap;        // [halo_cap]
+    float* vl = dih + d.halo_cap;          // [nnz_cap]
+    int* rw = reinterpret_cast<int*>(vl + d.res_nnz_cap);
+    int* cl = rw + chunk + 1;
+    int* hd = cl + d.res_nnz_cap;
+    const int k0 = nloc > 0 ? d.rowptr[r0] : 0;
+    const int nnzl = nloc > 0 ? d.rowptr[r1] - k0 : 0;
+    const int h0 = d.hptr[lb];
+    nh = d.hptr[lb + 1] - h0;
+    for (int i = tid; i <= nloc; i += bd) rw[i] = d.rowptr[r0 + i] - k0;
+    for (int k = tid; k < nnzl; k += bd) {
+      cl[k] = d.lcol[k0 + k];
+      vl[k] = d.val32[k0 + k];
+    }
+    for (int h = tid; h < nh; h += bd) {
+      const int j = d.hidx[h0 + h];
+      hd[h] = j;
+      dih[h] = d.dinv32[j];
+    }
+    for (int i = tid; i < nloc; i += bd) dil[i] = d.dinv32[r0 + i];
+    di = dil;
+    row = rw;
+    col = cl;
+    val = vl;
+    hid = hd;
+  } else {
+    float* o = d.f32own;
+    ir = o + r0;
+    iu = o + n + r0;
+    iw = o + 2 * n + r0;
+    ip = o + 3 * n + r0;
+    is = o + 4 * n + r0;
+    ie = o + 5 * n + r0;
+    di = d.dinv32 + r0;
+    row = d.rowptr + r0;
+    col = d.col;
+    val = d.val32;
+  }
+  // outer FP64 storage (global)
+  double* x = d.x + r0;
+  double* bp = d.bp + r0;
+  double* r64 = d.r + r0;
+
+  // ---- projected b and x0 ----
+  {
+    double v2[2] = {0.0, 0.0};
+    for (int i = tid; i < nloc; i += bd) {
+      v2[0] += d.b[r0 + i];
+      if (d.use_x0) v2[1] += x[i];
+    }
+    put_partials<2>(d, lb, red, v2, sh);
+    if (!grp.sync(sh)) return;
+    get_totals<2>(d, red, sh);
+    ++red;
+  }
+  {
+    const double mb = sh.tot[0] / d.n, mx = sh.tot[1] / d.n;
+    double v1[1] = {0.0};
+    for (int i = tid; i < nloc; i += bd) {
+      const double bi = d.b[r0 + i] - mb;
+      bp[i] = bi;
+      v1[0] += bi * bi;
+      x[i] = d.use_x0 ? x[i] - mx : 0.0;
+    }
+    put_partials<1>(d, lb, red, v1, sh);
+    if (!grp.sync(sh)) return;
+    get_totals<1>(d, red, sh);
+    ++red;
+  }
+  const double bnorm = sqrt(sh.tot[0]);
   if (!isfinite(bnorm)) { finish(d, lb, CGP_ERR_NONFINITE, 0, 0, 0.0, 0.0, bnorm); return; }
   if (bnorm == 0.0) {
-    for (int i = r0 + tid; i < r1; i += bd) d.x[i] = 0.0;
+    for (int i = tid; i < nloc; i += bd) x[i] = 0.0;
     finish(d, lb, CGP_OK, 0, 0, 0.0, 0.0, 0.0);
     return;
   }
+  // FP64 view of the local rows for the outer residual (global arrays)
+  Local L;
+  L.row = d.rowptr + r0;
+  L.col = d.col;
+  L.val = d.val;
+
   int total = 0, sweeps = 0, status = CGP_ERR_NOT_CONVERGED;
   double rel = 0.0;
   while (true) {
-    // ---- FP64 residual r = bp - K x and its projection ----
+    // ---- FP64 residual r = bp - K x, projected; x is complete (barrier above) ----
     {
       double v1[1] = {0.0};
-      spmv_rows<T, double>(d.rowptr, d.col, d.val, d.x, r0, r1, [&](int i, double s) {
-        const double ri = d.bp[i] - s;
-        d.r[i] = ri;
-        v1[0] += ri;
-      });
+      spmv_local<T, double>(
+          L, r0, nloc, [&](int jl) { return x[jl]; }, [&](int j) { return __ldcg(d.x + j); },
+          [&](int il, double s) {
+            const double ri = bp[il] - s;
+            r64[il] = ri;
+            v1[0] += ri;
+          });
       put_partials<1>(d, lb, red, v1, sh);
       if (!grp.sync(sh)) return;
       get_totals<1>(d, red, sh);
       ++red;
     }
-    const double mr = sh.tot[0] / d.n;
     {
+      const double mr = sh.tot[0] / d.n;
       double v1[1] = {0.0};
-      for (int i = r0 + tid; i < r1; i += bd) {
-        const double ri = d.r[i] - mr;
+      for (int i = tid; i < nloc; i += bd) {
+        const double ri = r64[i] - mr;
         v1[0] += ri * ri;
-        d.r32[i] = (float)ri;
+        const float rf = (float)ri;
+        ir[i] = rf;
+        iu[i] = di[i] * rf;
+        ie[i] = 0.0f;
+        R0[r0 + i] = rf;
       }
       put_partials<1>(d, lb, red, v1, sh);
-      if (!grp.sync(sh)) return;
+      if (!grp.sync(sh)) return;   // also publishes r_0 for the first product
       get_totals<1>(d, red, sh);
       ++red;
     }
@@ -808,81 +931,135 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
     if (rel <= d.tol) { status = CGP_OK; break; }
     if (sweeps >= d.max_sweeps || total >= d.max_it) { status = CGP_ERR_NOT_CONVERGED; break; }
 
-    // ---- FP32 inner PCG: K32 e = r32 from e = 0 ----
+    // ---- FP32 inner solve, single-reduction CG ----
+    // w_0 = A u_0 (u_j = D^-1_j r_j from the published r_0)
+    if constexpr (RES) {
+      for (int i = tid; i < nloc; i += bd) ext[i] = iu[i];
+      for (int h = tid; h < nh; h += bd) ext[nloc + h] = dih[h] * __ldcg(R0 + hid[h]);
+      __syncthreads();
+    }
     {
-      double v2[2] = {0.0, 0.0};
-      for (int i = r0 + tid; i < r1; i += bd) {
-        const float ri = d.r32[i];
-        const float zi = d.dinv32[i] * ri;
-        d.z32[i] = zi;
-        d.p32[i] = zi;
-        d.d32[i] = 0.0f;
-        v2[0] += (double)(ri * zi);
-        v2[1] += (double)(ri * ri);
+      float v3[3] = {0.0f, 0.0f, 0.0f};
+      auto op = [&](int il, float s) {
+        iw[il] = s;
+        W0[r0 + il] = s;
+        const float u = iu[il], r = ir[il];
+        v3[0] = fmaf(r, u, v3[0]);
+        v3[1] = fmaf(s, u, v3[1]);
+        v3[2] = fmaf(r, r, v3[2]);
+      };
+      if constexpr (RES) {
+        spmv_ext32<T>(row, col, val, ext, nloc, op);
+      } else {
+        spmv_local_f<T>(row, col, val, r0, nloc, [&](int jl) { return iu[jl]; },
+                        [&](int j) { return d.dinv32[j] * __ldcg(R0 + j); }, op);
       }
-      put_partials<2>(d, lb, red, v2, sh);
+      put_partials_f<3>(d, lb, red, v3, sh);
       if (!grp.sync(sh)) return;
     }
+    // scalars (thread 0): sc[0] alpha, sc[1] beta, sc[2] gamma, isc[0] stop flag
     int k = 0;
-    float rz_old = 0.0f;
-    float r0n = -1.0f;
-    bool inner_bad = false, capped = false;
+    auto derive = [&](Shared& S) {
+      const float g = S.ftot[0], dl = S.ftot[1], rr = S.ftot[2];
+      int st = -1;
+      if (k == 0) S.fsc[3] = rr;                                       // ||r_0||^2 of this sweep
+      if (!isfinite(rr) || !isfinite(g) || !isfinite(dl)) st = 1;     // non-finite
+      else if (rr <= S.fsc[4] * S.fsc[3]) st = 0;                     // inner tolerance reached
+      else if (total + k >= d.max_it) st = 0;
+      float beta = 0.0f, alpha;
+      if (k == 0) {
+        alpha = g / dl;
+      } else {
+        beta = g / S.fsc[2];
+        alpha = g / (dl - beta * g / S.fsc[0]);
+      }
+      if (st < 0 && !(g > 0.0f && alpha > 0.0f && isfinite(alpha))) st = 2;  // breakdown
+      S.isc[0] = st;
+      S.fsc[0] = alpha;
+      S.fsc[1] = beta;
+      S.fsc[2] = g;
+    };
+    if (tid == 0) sh.fsc[4] = (float)(d.inner_tol * d.inner_tol);
+    get_totals_f_then<3>(d, red, sh, derive);
+    ++red;
+    bool bad = false;
     while (true) {
-      get_totals<2>(d, red, sh);
-      ++red;
-      const float rz = (float)sh.tot[0];
-      const float rn = sqrtf((float)sh.tot[1]);
-      if (r0n < 0.0f) r0n = rn;
-      if (!isfinite(rn)) { inner_bad = true; break; }
-      if (rn <= (float)d.inner_tol * r0n) break;
-      if (total + k >= d.max_it) { capped = true; break; }
-      if (k > 0) {
-        const float beta = rz / rz_old;
-        for (int i = r0 + tid; i < r1; i += bd) d.p32[i] = fmaf(beta, d.p32[i], d.z32[i]);
-        if (!grp.sync(sh)) return;
+      const int st = sh.isc[0];
+      if (st >= 0) {
+        bad = st == 1;
+        break;
       }
-      rz_old = rz;
-      {
-        double v1[1] = {0.0};
-        float acc = 0.0f;
-        spmv_rows<T, float>(d.rowptr, d.col, d.val32, d.p32, r0, r1, [&](int i, float s) {
-          d.q32[i] = s;
-          acc = fmaf(d.p32[i], s, acc);
-        });
-        v1[0] = acc;
-        put_partials<1>(d, lb, red, v1, sh);
-        if (!grp.sync(sh)) return;
-        get_totals<1>(d, red, sh);
-        ++red;
+      const float alpha = sh.fsc[0], beta = sh.fsc[1];
+      const float* Rc = (k & 1) ? R1 : R0;
+      const float* Wc = (k & 1) ? W1 : W0;
+      const float* Sc = (k & 1) ? S1 : S0;
+      float* Rn = (k & 1) ? R0 : R1;
+      float* Wn = (k & 1) ? W0 : W1;
+      float* Sn = (k & 1) ? S0 : S1;
+      // own rows: p, s, e, r, u
+      for (int i = tid; i < nloc; i += bd) {
+        const float pi = k == 0 ? iu[i] : fmaf(beta, ip[i], iu[i]);
+        const float si = k == 0 ? iw[i] : fmaf(beta, is[i], iw[i]);
+        ip[i] = pi;
+        is[i] = si;
+        ie[i] = fmaf(alpha, pi, ie[i]);
+        const float ri = fmaf(-alpha, si, ir[i]);
+        ir[i] = ri;
+        iu[i] = di[i] * ri;
+        Rn[r0 + i] = ri;
+        Sn[r0 + i] = si;
+        if (RES) ext[i] = di[i] * ri;
       }
-      const float pq = (float)sh.tot[0];
-      if (!(pq > 0.0f)) { inner_bad = !isfinite(pq); break; }
-      const float alpha = rz / pq;
-      {
-        float a0 = 0.0f, a1 = 0.0f;
-        for (int i = r0 + tid; i < r1; i += bd) {
-          const float pi = d.p32[i];
-          d.d32[i] = fmaf(alpha, pi, d.d32[i]);
-          const float ri = fmaf(-alpha, d.q32[i], d.r32[i]);
-          const float zi = d.dinv32[i] * ri;
-          d.r32[i] = ri;
-          d.z32[i] = zi;
-          a0 = fmaf(ri, zi, a0);
-          a1 = fmaf(ri, ri, a1);
-        }
-        double v2[2] = {(double)a0, (double)a1};
-        put_partials<2>(d, lb, red, v2, sh);
-        if (!grp.sync(sh)) return;
+      // halo: u_j = D^-1_j (r_j - alpha (w_j + beta s_j)) from the owner's published values
+      auto halo_u = [&](int j, float dj) {
+        const float sj = k == 0 ? __ldcg(Wc + j) : fmaf(beta, __ldcg(Sc + j), __ldcg(Wc + j));
+        return dj * fmaf(-alpha, sj, __ldcg(Rc + j));
+      };
+      if constexpr (RES) {
+        for (int h = tid; h < nh; h += bd) ext[nloc + h] = halo_u(hid[h], dih[h]);
       }
+      __syncthreads();
+      float v3[3] = {0.0f, 0.0f, 0.0f};
+      auto op = [&](int il, float s) {
+        iw[il] = s;
+        Wn[r0 + il] = s;
+        const float u = iu[il], r = ir[il];
+        v3[0] = fmaf(r, u, v3[0]);
+        v3[1] = fmaf(s, u, v3[1]);
+        v3[2] = fmaf(r, r, v3[2]);
+      };
+      if constexpr (RES) {
+        spmv_ext32<T>(row, col, val, ext, nloc, op);
+      } else {
+        spmv_local_f<T>(row, col, val, r0, nloc, [&](int jl) { return iu[jl]; },
+                        [&](int j) { return halo_u(j, d.dinv32[j]); }, op);
+      }
+      put_partials_f<3>(d, lb, red, v3, sh);
+      if (!grp.sync(sh)) return;
       ++k;
+      get_totals_f_then<3>(d, red, sh, derive);
+      ++red;
     }
     total += k;
-    if (inner_bad) { status = CGP_ERR_NONFINITE; break; }
-    // ---- FP64 correction and projection ----
-    for (int i = r0 + tid; i < r1; i += bd) d.x[i] += (double)d.d32[i];
-    if (!project_x(d, lb, r0, r1, grp, sh, red)) return;
+    if (bad) { status = CGP_ERR_NONFINITE; break; }
+    // ---- FP64 correction and projection; x published for the next residual ----
+    {
+      double v1[1] = {0.0};
+      for (int i = tid; i < nloc; i += bd) {
+        const double xi = x[i] + (double)ie[i];
+        x[i] = xi;
+        v1[0] += xi;
+      }
+      put_partials<1>(d, lb, red, v1, sh);
+      if (!grp.sync(sh)) return;
+      get_totals<1>(d, red, sh);
+      ++red;
+      const double mx = sh.tot[0] / d.n;
+      for (int i = tid; i < nloc; i += bd) x[i] -= mx;
+      if (!grp.sync(sh)) return;
+    }
     ++sweeps;
-    if (k == 0 && !capped) { status = CGP_ERR_BREAKDOWN; break; }  // the inner solve made no progress
+    if (k == 0 && total < d.max_it) { status = CGP_ERR_BREAKDOWN; break; }  // no inner progress
   }
   finish(d, lb, status, total, sweeps, rel, rel, bnorm);
 }
@@ -892,7 +1069,7 @@ __global__ void __launch_bounds__(MAX_BLOCK) pcg_persistent_kernel(Desc d) {
   __shared__ Shared sh;
   mark_pending(d, blockIdx.x);
   if (d.mixed)
-    solve_mixed<T>(d, blockIdx.x, sh);
+    solve_mixed<T, RES>(d, blockIdx.x, sh);
   else
     solve_fp64<T, RES>(d, blockIdx.x, sh);
 }
@@ -1046,7 +1223,7 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
   out.fn = fn0;
   out.nblk = nblk;
   out.block = block;
-  if (mixed || !m || (tu.flags & 1)) return CGP_OK;
+  if (!m || (tu.flags & 1)) return CGP_OK;
   const int chunk = (n + nblk - 1) / nblk;
   // rough size check before building a plan
   const int rough_nnz = m->h_rowptr[std::min(n, chunk)] - m->h_rowptr[0];
@@ -1061,8 +1238,9 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
   HaloPlan hp;
   int st = get_halo_plan(m, nblk, hp);
   if (st != CGP_OK) return st;
-  size_t smem = 8 * ((size_t)7 * chunk + hp.max_halo + hp.max_nnz) +
-                4 * ((size_t)chunk + 1 + hp.max_nnz + hp.max_halo);
+  size_t smem = mixed ? 4 * ((size_t)9 * chunk + 3 * (size_t)hp.max_halo + 2 * (size_t)hp.max_nnz + 1)
+                     : 8 * ((size_t)7 * chunk + hp.max_halo + hp.max_nnz) +
+                           4 * ((size_t)chunk + 1 + hp.max_nnz + hp.max_halo);
   smem = (smem + 15) / 16 * 16;
   if (smem > limit) return CGP_OK;
   if (cudaFuncSetAttribute((const void*)fnr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -1116,11 +1294,9 @@ int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_o
   d.p = m->p;
   d.p2 = m->p2;
   d.q = m->q;
-  d.r32 = m->r32;
-  d.z32 = m->z32;
-  d.p32 = m->p32;
-  d.q32 = m->q32;
-  d.d32 = m->d32;
+  d.f32pub = m->f32pub;
+  d.f32own = m->f32own;
+  d.fpart = m->fpart;
   d.part = m->part;
   d.part_stride = m->max_blocks;
   d.bar = m->bar;

@@ -187,14 +187,23 @@ def test_fp64_solve_with_initial_guess(pair, cgp):
     assert rel(x.cpu().numpy(), ref["x"]) <= 1e-9
 
 
-def test_mixed_precision_reaches_the_fp64_answer(pair, cgp):
+MIXED_SHAPES = [(0, 0, 0, 0), (128, 1, 3, 0), (128, 2, 5, 1), (256, 4, 7, 0), (64, 8, 2, 1), (64, 1, 13, 0)]
+
+
+@pytest.mark.parametrize("block,lanes,blocks,flags", MIXED_SHAPES)
+def test_mixed_precision_reaches_the_fp64_answer(pair, cgp, block, lanes, blocks, flags):
     m, om = pair
     u, v = velocity_for(om)
     b = oracle_rhs(om, u, v)
     exact = O.pcg(om.K, om.d, b, tol=1e-14)["x"]
     ref = O.mixed_ir(om.K, om.d, b, tol=1e-8, inner_tol=1e-4)
     x = torch.zeros(m.n_c, dtype=torch.float64, device=DEV)
+    cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_MIXED, block, lanes, blocks, flags)
     info = cgp.cgp_poisson_solve(m.handle, T(b), x, tol=1e-8, precision=cgp.CGP_MIXED, inner_tol=1e-4)
+    launch = cgp.cgp_last_launch(m.handle, cgp.CGP_MIXED)
+    cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_MIXED, 0, 0, 0, 0)
+    if flags == 1:
+        assert launch["resident"] == 0
     assert info["status"] == cgp.CGP_OK, info
     assert info["rel_res_true"] <= 1e-8
     assert abs(info["outer_sweeps"] - ref["outer_sweeps"]) <= 1
