@@ -192,6 +192,57 @@ int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* col, const do
                               const cgp_solve_opts* opts, cgp_solve_info* info, void* stream);
 
 /*
+ * Batched solves: many independent systems in one persistent launch.
+ *
+ * A batch fixes a list of distinct meshes (count >= 1; sizes may differ),
+ * one right-hand side b[i] and one solution/initial-guess buffer x[i] per
+ * mesh (device pointers, caller-owned, length n_c of that mesh; host arrays
+ * of pointers, copied) and the solve options.  cgp_batch_solve then runs
+ * every system's Jacobi-PCG (FP64 or mixed precision, as in
+ * cgp_poisson_solve) in ONE cooperative launch: the grid is split into one
+ * group of blocks per system, sized in proportion to the system's work
+ * (nnz * sqrt(n)), each group with its own barriers and reductions, so the
+ * systems progress side by side.  The launch needs no host work, so it can
+ * be captured in a CUDA graph and replayed.  This is the many-instance
+ * workload of the spec addition (2); the paper solves one system per
+ * time step (Sect. 2.2).
+ *
+ * cgp_batch_create    plans the launch (blocks per system, shared-memory
+ *                     residency, halo lists) and allocates the batch's small
+ *                     device descriptors; synchronous.  INVALID_ARG if a
+ *                     mesh repeats (their scratch would be shared) or there
+ *                     are more systems than co-resident blocks.
+ * cgp_batch_solve     one launch on `stream`, asynchronous.
+ * cgp_batch_info      synchronises the device and reads each system's
+ *                     outcome; seconds[i] (nullable) is the device time from
+ *                     the launch's start to system i's finish.  Returns the
+ *                     first non-OK status among the systems.
+ * cgp_batch_set_tuning  re-plans with threads per block, lanes per CSR row,
+ *                     blocks per SM (0 = as many as fit) and flags (bit 0:
+ *                     rows in global memory).
+ * cgp_batch_autotune  times a set of launch shapes on the batch's own
+ *                     systems (from x = 0) and keeps the fastest; writes the
+ *                     best time in ms to best_ms (nullable).  Synchronous;
+ *                     overwrites the x buffers.
+ * cgp_batch_query     grid size, block, lanes, residency and blocks per
+ *                     system (host [count], nullable).
+ * cgp_poisson_solve_batched  one-shot create + solve (+ info when infos is
+ *                     non-NULL) + destroy.
+ */
+typedef struct cgp_batch_s* cgp_batch;
+
+int cgp_batch_create(const cgp_mesh* meshes, int count, const double* const* b, double* const* x,
+                     const cgp_solve_opts* opts, cgp_batch* out);
+int cgp_batch_solve(cgp_batch batch, void* stream);
+int cgp_batch_info(cgp_batch batch, cgp_solve_info* infos, double* seconds);
+int cgp_batch_set_tuning(cgp_batch batch, int block, int lanes, int blocks_per_sm, int flags);
+int cgp_batch_autotune(cgp_batch batch, void* stream, double* best_ms);
+int cgp_batch_query(cgp_batch batch, int* grid, int* block, int* lanes, int* resident, int* blocks);
+int cgp_batch_destroy(cgp_batch batch);
+int cgp_poisson_solve_batched(const cgp_mesh* meshes, int count, const double* const* b, double* const* x,
+                              const cgp_solve_opts* opts, cgp_solve_info* infos, void* stream);
+
+/*
  * cgp_prolong - prolongation by the P1 shape functions (Eq. 20) for one level:
  * x_f[i] = x_c[i] for coarse nodes, x_f[n_c + e] = (x_c[a_e] + x_c[b_e]) / 2 at
  * the midpoint of edge e (shape functions 1/2, 1/2, 0 there).

@@ -35,7 +35,9 @@ CGP_FP32 = 1          # precision argument of cgp_spmv for the FP32 copy of K
 EXPORTS = ("cgp_assemble", "cgp_mesh_query", "cgp_mesh_fine_geometry", "cgp_mesh_matrices",
            "cgp_restrict", "cgp_poisson_solve", "cgp_poisson_solve_async",
            "cgp_poisson_solve_noalloc", "cgp_prolong", "cgp_lorentz", "cgp_spmv",
-           "cgp_set_tuning", "cgp_get_tuning", "cgp_last_launch", "cgp_barrier_selftest", "cgp_mesh_destroy",
+           "cgp_set_tuning", "cgp_get_tuning", "cgp_last_launch", "cgp_barrier_selftest",
+           "cgp_batch_create", "cgp_batch_solve", "cgp_batch_info", "cgp_batch_set_tuning",
+           "cgp_batch_autotune", "cgp_batch_query", "cgp_batch_destroy", "cgp_poisson_solve_batched", "cgp_mesh_destroy",
            "cgp_last_error")
 
 CGP_TUNE_SOLVE_FP64 = 0
@@ -100,6 +102,16 @@ def load(path: str | None = None):
         "cgp_last_launch": [vp, i, ip, ip, ip, ip],
         "cgp_barrier_selftest": [i, i, ctypes.c_longlong, vp],
         "cgp_mesh_destroy": [vp],
+        "cgp_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                             ctypes.POINTER(SolveOpts), ctypes.POINTER(vp)],
+        "cgp_batch_solve": [vp, vp],
+        "cgp_batch_info": [vp, ctypes.POINTER(SolveInfo), dp],
+        "cgp_batch_set_tuning": [vp, i, i, i, i],
+        "cgp_batch_autotune": [vp, vp, dp],
+        "cgp_batch_query": [vp, ip, ip, ip, ip, ip],
+        "cgp_batch_destroy": [vp],
+        "cgp_poisson_solve_batched": [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                      ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -280,6 +292,107 @@ def cgp_barrier_selftest(nblk, absent, spin_ns, stream=None):
 
 def cgp_mesh_destroy(mesh):
     _check(load().cgp_mesh_destroy(mesh))
+
+
+def _ptr_array(items, what):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, t in enumerate(items):
+        arr[i] = _dev(t, what).value if t is not None else None
+    return arr
+
+
+class Batch:
+    """Many systems solved in one persistent launch (cgp_batch_* calls)."""
+
+    def __init__(self, meshes, b, x, tol=1e-8, max_it=20000, precision=CGP_FP64, inner_tol=1e-4, use_x0=False,
+                 max_sweeps=50):
+        L = load()
+        self.count = len(meshes)
+        handles = (ctypes.c_void_p * self.count)(*[m.handle.value if hasattr(m, "handle") else m.value
+                                                   for m in meshes])
+        opts = SolveOpts(float(tol), int(max_it), int(precision), float(inner_tol), int(bool(use_x0)),
+                         int(max_sweeps))
+        self.handle = ctypes.c_void_p()
+        self._keep = (list(meshes), list(b), list(x))
+        _check(L.cgp_batch_create(handles, self.count, _ptr_array(b, "float64"), _ptr_array(x, "float64"),
+                                  ctypes.byref(opts), ctypes.byref(self.handle)))
+
+    def solve(self, stream=None):
+        _check(load().cgp_batch_solve(self.handle, _stream(stream)))
+
+    def info(self):
+        """(list of info dicts, list of per-system seconds); synchronises."""
+        infos = (SolveInfo * self.count)()
+        secs = (ctypes.c_double * self.count)()
+        st = load().cgp_batch_info(self.handle, infos, secs)
+        _check(st, allow=(CGP_ERR_NOT_CONVERGED, CGP_ERR_BREAKDOWN, CGP_ERR_NONFINITE))
+        return [i.as_dict() for i in infos], list(secs)
+
+    def set_tuning(self, block=0, lanes=0, blocks_per_sm=0, flags=0):
+        _check(load().cgp_batch_set_tuning(self.handle, int(block), int(lanes), int(blocks_per_sm), int(flags)))
+
+    def autotune(self, stream=None):
+        best = ctypes.c_double()
+        _check(load().cgp_batch_autotune(self.handle, _stream(stream), ctypes.byref(best)))
+        return best.value
+
+    def query(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        blocks = (ctypes.c_int * self.count)()
+        _check(load().cgp_batch_query(self.handle, *[ctypes.byref(a) for a in v], blocks))
+        return dict(grid=v[0].value, block=v[1].value, lanes=v[2].value, resident=v[3].value, blocks=list(blocks))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().cgp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cgp_poisson_solve_batched(meshes, b, x, tol=1e-8, max_it=20000, precision=CGP_FP64, inner_tol=1e-4,
+                              use_x0=False, max_sweeps=50, stream=None):
+    """One-shot batched solve; returns the list of info dicts."""
+    n = len(meshes)
+    handles = (ctypes.c_void_p * n)(*[m.handle.value if hasattr(m, "handle") else m.value for m in meshes])
+    opts = SolveOpts(float(tol), int(max_it), int(precision), float(inner_tol), int(bool(use_x0)), int(max_sweeps))
+    infos = (SolveInfo * n)()
+    st = load().cgp_poisson_solve_batched(handles, n, _ptr_array(b, "float64"), _ptr_array(x, "float64"),
+                                          ctypes.byref(opts), infos, _stream(stream))
+    _check(st, allow=(CGP_ERR_NOT_CONVERGED, CGP_ERR_BREAKDOWN, CGP_ERR_NONFINITE))
+    return [i.as_dict() for i in infos]
+
+
+def cgp_batch_create(*a, **k):
+    return Batch(*a, **k)
+
+
+def cgp_batch_solve(batch, stream=None):
+    batch.solve(stream)
+
+
+def cgp_batch_info(batch):
+    return batch.info()
+
+
+def cgp_batch_set_tuning(batch, *a, **k):
+    batch.set_tuning(*a, **k)
+
+
+def cgp_batch_autotune(batch, stream=None):
+    return batch.autotune(stream)
+
+
+def cgp_batch_query(batch):
+    return batch.query()
+
+
+def cgp_batch_destroy(batch):
+    batch.close()
 
 
 class Mesh:

@@ -31,6 +31,7 @@ struct SolveResult {
   double rel_rec;
   double rel_true;
   double bnorm;
+  unsigned long long t_end;  // device clock (ns) when the solve finished
 };
 
 // Tuning of the persistent solver launch (chosen by the autotuner or defaults).

@@ -30,7 +30,9 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <cstring>
 #include <string>
+#include <vector>
 
 #include "cgp_fixed.h"
 #include "cgp_internal.h"
@@ -313,6 +315,7 @@ __device__ __forceinline__ void get_totals_then(const Desc& d, int red, Shared& 
 __device__ void finish(const Desc& d, int lb, int status, int its, int sweeps, double rel_rec, double rel_true,
                        double bnorm) {
   if (lb == 0 && threadIdx.x == 0) {
+    d.res->t_end = global_ns();
     d.res->status = status;
     d.res->iterations = its;
     d.res->sweeps = sweeps;
@@ -1074,6 +1077,23 @@ __global__ void __launch_bounds__(MAX_BLOCK) pcg_persistent_kernel(Desc d) {
     solve_fp64<T, RES>(d, blockIdx.x, sh);
 }
 
+// Many independent systems in one launch: block b runs instance
+// blk_inst[b] as local block b - blk0 of that instance's group.
+template <int T, bool RES>
+__global__ void __launch_bounds__(MAX_BLOCK)
+    pcg_batched_kernel(const Desc* __restrict__ descs, const int* __restrict__ blk_inst,
+                       unsigned long long* t_start) {
+  __shared__ Shared sh;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *t_start = global_ns();
+  const Desc& d = descs[blk_inst[blockIdx.x]];
+  const int lb = blockIdx.x - d.blk0;
+  mark_pending(d, lb);
+  if (d.mixed)
+    solve_mixed<T, RES>(d, lb, sh);
+  else
+    solve_fp64<T, RES>(d, lb, sh);
+}
+
 // ---------------------------------------------------------------------------
 // standalone SpMV: T lanes per row, grid-stride over row groups
 // ---------------------------------------------------------------------------
@@ -1107,6 +1127,19 @@ PcgFn pcg_kernel_for(int lanes, bool res) {
     case 4: return res ? pcg_persistent_kernel<4, true> : pcg_persistent_kernel<4, false>;
     case 8: return res ? pcg_persistent_kernel<8, true> : pcg_persistent_kernel<8, false>;
     case 32: return res ? pcg_persistent_kernel<32, true> : pcg_persistent_kernel<32, false>;
+    default: return nullptr;
+  }
+}
+
+using BatchFn = void (*)(const Desc*, const int*, unsigned long long*);
+
+BatchFn batched_kernel_for(int lanes, bool res) {
+  switch (lanes) {
+    case 1: return res ? pcg_batched_kernel<1, true> : pcg_batched_kernel<1, false>;
+    case 2: return res ? pcg_batched_kernel<2, true> : pcg_batched_kernel<2, false>;
+    case 4: return res ? pcg_batched_kernel<4, true> : pcg_batched_kernel<4, false>;
+    case 8: return res ? pcg_batched_kernel<8, true> : pcg_batched_kernel<8, false>;
+    case 32: return res ? pcg_batched_kernel<32, true> : pcg_batched_kernel<32, false>;
     default: return nullptr;
   }
 }
@@ -1202,6 +1235,16 @@ int get_halo_plan(cgp_mesh_impl* m, int nblk, HaloPlan& out) {
   return CGP_OK;
 }
 
+// Dynamic shared memory of a block that keeps its rows resident: FP64 needs
+// seven vectors, the halo buffer and an FP64 CSR slice; the mixed solver six
+// FP32 vectors, D^-1, the halo buffer and D^-1 of the halo, and an FP32 slice.
+size_t res_smem_bytes(bool mixed, int chunk, const HaloPlan& hp) {
+  const size_t s = mixed ? 4 * ((size_t)9 * chunk + 3 * (size_t)hp.max_halo + 2 * (size_t)hp.max_nnz + 1)
+                         : 8 * ((size_t)7 * chunk + hp.max_halo + hp.max_nnz) +
+                               4 * ((size_t)chunk + 1 + hp.max_nnz + hp.max_halo);
+  return (s + 15) / 16 * 16;
+}
+
 // Shape of a persistent launch for an n-row system.  For FP64 on a mesh the
 // block's rows go to shared memory when the largest chunk, its halo and its
 // CSR slice fit and the grid stays co-resident.
@@ -1238,10 +1281,7 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
   HaloPlan hp;
   int st = get_halo_plan(m, nblk, hp);
   if (st != CGP_OK) return st;
-  size_t smem = mixed ? 4 * ((size_t)9 * chunk + 3 * (size_t)hp.max_halo + 2 * (size_t)hp.max_nnz + 1)
-                     : 8 * ((size_t)7 * chunk + hp.max_halo + hp.max_nnz) +
-                           4 * ((size_t)chunk + 1 + hp.max_nnz + hp.max_halo);
-  smem = (smem + 15) / 16 * 16;
+  const size_t smem = res_smem_bytes(mixed, chunk, hp);
   if (smem > limit) return CGP_OK;
   if (cudaFuncSetAttribute((const void*)fnr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
@@ -1266,18 +1306,11 @@ int solver_max_blocks(int device) {
   return sms * 32;  // upper bound on co-resident blocks of >= 64 threads
 }
 
-int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opts& o, cgp_solve_info* info_dev,
-                 cudaStream_t s) {
-  const bool mixed = o.precision == CGP_MIXED;
-  const SolverTuning& tu = m->tune[mixed ? CGP_TUNE_SOLVE_MIXED : CGP_TUNE_SOLVE_FP64];
-  LaunchPlan plan;
-  int st = plan_solve(m, m->device, m->n_c, m->max_blocks, tu, mixed, plan);
-  if (st != CGP_OK) return st;
-  const int nblk = plan.nblk;
-  // barrier epochs stay far below 2^32 / nblk
-  const long long max_epochs = 8LL + 4LL * (long long)std::max(o.max_it, 1) + 8LL * std::max(o.max_sweeps, 1);
-  if (max_epochs * nblk >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "solver: max_it too large");
+namespace {
 
+// Descriptor of one system solved by `nblk` blocks (blk0 set by the caller).
+Desc make_desc(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opts& o, int nblk,
+               const LaunchPlan& plan, unsigned* bar, SolveResult* res) {
   Desc d{};
   d.n = m->n_c;
   d.rowptr = m->rowptr;
@@ -1299,9 +1332,9 @@ int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_o
   d.fpart = m->fpart;
   d.part = m->part;
   d.part_stride = m->max_blocks;
-  d.bar = m->bar;
-  d.res = m->res;
-  d.out = info_dev;
+  d.bar = bar;
+  d.res = res;
+  d.out = nullptr;
   d.blk0 = 0;
   d.nblk = nblk;
   d.tol = o.tol;
@@ -1309,13 +1342,32 @@ int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_o
   d.max_it = o.max_it;
   d.max_sweeps = o.max_sweeps;
   d.use_x0 = o.use_x0;
-  d.mixed = mixed ? 1 : 0;
+  d.mixed = o.precision == CGP_MIXED ? 1 : 0;
   d.res_nnz_cap = plan.nnz_cap;
   d.halo_cap = plan.halo_cap;
   d.lcol = plan.halo.lcol;
   d.hptr = plan.halo.hptr;
   d.hidx = plan.halo.hidx;
   d.spin_ns = 2000000000LL;
+  return d;
+}
+
+}  // namespace
+
+int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opts& o, cgp_solve_info* info_dev,
+                 cudaStream_t s) {
+  const bool mixed = o.precision == CGP_MIXED;
+  const SolverTuning& tu = m->tune[mixed ? CGP_TUNE_SOLVE_MIXED : CGP_TUNE_SOLVE_FP64];
+  LaunchPlan plan;
+  int st = plan_solve(m, m->device, m->n_c, m->max_blocks, tu, mixed, plan);
+  if (st != CGP_OK) return st;
+  const int nblk = plan.nblk;
+  // barrier epochs stay far below 2^32 / nblk
+  const long long max_epochs = 8LL + 4LL * (long long)std::max(o.max_it, 1) + 8LL * std::max(o.max_sweeps, 1);
+  if (max_epochs * nblk >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "solver: max_it too large");
+
+  Desc d = make_desc(m, b, x, o, nblk, plan, m->bar, m->res);
+  d.out = info_dev;
 
   CGP_CUDA(cudaMemsetAsync(m->bar, 0, 256, s));
   CGP_CUDA(cudaMemsetAsync(m->res, 0, sizeof(SolveResult), s));
@@ -1417,6 +1469,179 @@ __global__ void barrier_selftest_kernel(unsigned* bar, int* timeout, int nblk, i
   const bool ok = grp.sync(sh);
   if (threadIdx.x == 0 && ok) atomicAdd(ok_count, 1);
 }
+
+// ---------------------------------------------------------------------------
+// Batched solves: many meshes, one persistent cooperative launch
+// ---------------------------------------------------------------------------
+struct BatchShape {
+  int block = 512;
+  int lanes = 1;
+  int per_sm = 0;   // blocks per SM (0: as many as can be co-resident)
+  int flags = 0;    // bit 0: rows in global memory
+};
+
+}  // namespace cgp
+
+struct cgp_batch_s {
+  int device = 0;
+  int count = 0;
+  std::vector<cgp::cgp_mesh_impl*> meshes;
+  std::vector<const double*> b;
+  std::vector<double*> x;
+  cgp_solve_opts opts{};
+  cgp::BatchShape shape;
+  // plan
+  int grid = 0;
+  bool res = false;
+  size_t smem = 0;
+  cgp::BatchFn fn = nullptr;
+  std::vector<int> nblk;
+  // device buffers: descriptors, block -> instance map, control area
+  void* d_desc = nullptr;
+  int* d_blk_inst = nullptr;
+  unsigned char* d_ctrl = nullptr;   // per instance: barrier (256 B) + result (256 B); then t_start
+  size_t ctrl_bytes = 0;
+};
+
+namespace cgp {
+namespace {
+
+constexpr size_t kCtrlPerInstance = 512;
+
+int batch_plan(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
+  const int lanes = sh.lanes > 0 ? sh.lanes : 1;
+  const int block = sh.block > 0 ? sh.block : 512;
+  const bool mixed = o.precision == CGP_MIXED;
+  BatchFn fn0 = batched_kernel_for(lanes, false);
+  if (!fn0 || block < 64 || block > MAX_BLOCK || block % 32 != 0 || block % lanes != 0)
+    return fail(CGP_ERR_INVALID_ARG, "batch tuning: bad block or lanes");
+  const int sms = std::max(1, dev_info(B->device).sms);
+  int per_sm0 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm0, (const void*)fn0, block, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CGP_ERR_CUDA, "batch: occupancy query failed");
+  }
+  int G = per_sm0 * sms;
+  if (sh.per_sm > 0) G = std::min(G, sh.per_sm * sms);
+  const int count = B->count;
+  if (G < count) return fail(CGP_ERR_INVALID_ARG, "batch: more instances than co-resident blocks");
+  // blocks per instance in proportion to nnz * sqrt(n) (work of a CG solve on a 2-D mesh)
+  std::vector<double> w(count);
+  double W = 0.0;
+  for (int i = 0; i < count; ++i) {
+    w[i] = (double)B->meshes[i]->nnz * std::sqrt((double)B->meshes[i]->n_c);
+    W += w[i];
+  }
+  std::vector<int> nb(count), cap(count);
+  int total = 0;
+  for (int i = 0; i < count; ++i) {
+    cap[i] = std::max(1, std::min(B->meshes[i]->n_c / 64, B->meshes[i]->max_blocks));
+    nb[i] = std::max(1, std::min(cap[i], (int)std::floor(G * w[i] / W)));
+    total += nb[i];
+  }
+  while (total > G) {  // shrink the instance with the most blocks
+    int j = (int)(std::max_element(nb.begin(), nb.end()) - nb.begin());
+    if (nb[j] <= 1) break;
+    --nb[j];
+    --total;
+  }
+  while (total < G) {  // grow the instance with the most work per block
+    int j = -1;
+    double best = 0.0;
+    for (int i = 0; i < count; ++i)
+      if (nb[i] < cap[i] && w[i] / nb[i] > best) {
+        best = w[i] / nb[i];
+        j = i;
+      }
+    if (j < 0) break;
+    ++nb[j];
+    ++total;
+  }
+  // shared-memory residency when every instance's chunk fits
+  std::vector<HaloPlan> hp(count);
+  bool res = !(sh.flags & 1);
+  size_t smem = 0;
+  BatchFn fnr = batched_kernel_for(lanes, true);
+  cudaFuncAttributes fa{};
+  if (res && cudaFuncGetAttributes(&fa, (const void*)fnr) != cudaSuccess) {
+    cudaGetLastError();
+    res = false;
+  }
+  const size_t limit = res ? (size_t)std::max(0, optin_smem(B->device) - (int)fa.sharedSizeBytes - 1024) : 0;
+  for (int i = 0; res && i < count; ++i) {
+    cgp_mesh_impl* m = B->meshes[i];
+    const int chunk = (m->n_c + nb[i] - 1) / nb[i];
+    const int rough_nnz = m->h_rowptr[std::min(m->n_c, chunk)] - m->h_rowptr[0];
+    if ((size_t)chunk * 56 + (size_t)rough_nnz * 12 > limit) {
+      res = false;
+      break;
+    }
+    int st = get_halo_plan(m, nb[i], hp[i]);
+    if (st != CGP_OK) return st;
+    smem = std::max(smem, res_smem_bytes(mixed, chunk, hp[i]));
+    if (smem > limit) res = false;
+  }
+  if (res) {
+    if (cudaFuncSetAttribute((const void*)fnr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      res = false;
+    } else {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fnr, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+      }
+      if (per_sm * sms < total) res = false;
+    }
+  }
+  if (!res) smem = 0;
+  // descriptors
+  std::vector<Desc> desc(count);
+  std::vector<int> blk_inst(total);
+  int blk0 = 0;
+  for (int i = 0; i < count; ++i) {
+    cgp_mesh_impl* m = B->meshes[i];
+    LaunchPlan lp;
+    lp.nblk = nb[i];
+    lp.block = block;
+    if (res) {
+      lp.res = true;
+      lp.nnz_cap = hp[i].max_nnz;
+      lp.halo_cap = hp[i].max_halo;
+      lp.halo = hp[i];
+    }
+    unsigned char* ctrl = B->d_ctrl + kCtrlPerInstance * i;
+    desc[i] = make_desc(m, B->b[i], B->x[i], o, nb[i], lp, reinterpret_cast<unsigned*>(ctrl),
+                        reinterpret_cast<SolveResult*>(ctrl + 256));
+    desc[i].blk0 = blk0;
+    const long long max_epochs = 8LL + 4LL * (long long)std::max(o.max_it, 1) + 8LL * std::max(o.max_sweeps, 1);
+    if (max_epochs * nb[i] >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "batch: max_it too large");
+    for (int k = 0; k < nb[i]; ++k) blk_inst[blk0 + k] = i;
+    blk0 += nb[i];
+  }
+  CGP_CUDA(cudaMemcpy(B->d_desc, desc.data(), sizeof(Desc) * count, cudaMemcpyHostToDevice));
+  CGP_CUDA(cudaMemcpy(B->d_blk_inst, blk_inst.data(), sizeof(int) * total, cudaMemcpyHostToDevice));
+  B->grid = total;
+  B->res = res;
+  B->smem = smem;
+  B->fn = res ? fnr : fn0;
+  B->nblk = nb;
+  B->shape = BatchShape{block, lanes, sh.per_sm, sh.flags};
+  return CGP_OK;
+}
+
+int batch_launch(cgp_batch_s* B, cudaStream_t s) {
+  CGP_CUDA(cudaMemsetAsync(B->d_ctrl, 0, B->ctrl_bytes, s));
+  unsigned long long* t_start = reinterpret_cast<unsigned long long*>(B->d_ctrl + kCtrlPerInstance * B->count);
+  const Desc* descs = static_cast<const Desc*>(B->d_desc);
+  const int* bi = B->d_blk_inst;
+  void* args[] = {&descs, &bi, &t_start};
+  CGP_CUDA(cudaLaunchCooperativeKernel((const void*)B->fn, dim3(B->grid), dim3(B->shape.block), args, B->smem, s));
+  return CGP_OK;
+}
+
+}  // namespace
 
 }  // namespace cgp
 
@@ -1548,4 +1773,172 @@ extern "C" int cgp_spmv(cgp_mesh m, int precision, const void* x, void* y, void*
   if (!x || !y) return fail(CGP_ERR_INVALID_ARG, "cgp_spmv: NULL vector");
   if (precision != CGP_FP64 && precision != 1) return fail(CGP_ERR_INVALID_ARG, "cgp_spmv: unknown precision");
   return launch_spmv(m, precision, x, y, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// batch C ABI
+// ---------------------------------------------------------------------------
+extern "C" int cgp_batch_create(const cgp_mesh* meshes, int count, const double* const* b, double* const* x,
+                                const cgp_solve_opts* opts, cgp_batch* out) {
+  if (!out) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_create: out is NULL");
+  *out = nullptr;
+  if (!meshes || !b || !x || count < 1) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_create: bad arguments");
+  cgp_solve_opts o;
+  for (int i = 0; i < count; ++i) {
+    if (!meshes[i] || !b[i] || !x[i]) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_create: NULL entry");
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == meshes[i])
+        return fail(CGP_ERR_INVALID_ARG, "cgp_batch_create: a mesh appears twice (its scratch would be shared)");
+  }
+  int st = check_solve_args(meshes[0], b[0], x[0], opts, o);
+  if (st != CGP_OK) return st;
+  cgp_batch_s* B = new cgp_batch_s();
+  B->count = count;
+  B->opts = o;
+  cudaError_t e = cudaGetDevice(&B->device);
+  if (e != cudaSuccess) {
+    delete B;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  for (int i = 0; i < count; ++i) {
+    B->meshes.push_back(meshes[i]);
+    B->b.push_back(b[i]);
+    B->x.push_back(x[i]);
+  }
+  B->ctrl_bytes = kCtrlPerInstance * count + 256;
+  const int sms = std::max(1, dev_info(B->device).sms);
+  const size_t max_grid = (size_t)sms * 32;
+  e = cudaMalloc(&B->d_desc, sizeof(Desc) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_blk_inst, sizeof(int) * max_grid);
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_ctrl, B->ctrl_bytes);
+  if (e != cudaSuccess) {
+    cgp_batch_destroy(B);
+    return cuda_fail(e, "cudaMalloc(batch)");
+  }
+  st = batch_plan(B, BatchShape{}, o);
+  if (st != CGP_OK) {
+    cgp_batch_destroy(B);
+    return st;
+  }
+  *out = B;
+  return CGP_OK;
+}
+
+extern "C" int cgp_batch_set_tuning(cgp_batch batch, int block, int lanes, int blocks_per_sm, int flags) {
+  if (!batch) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_set_tuning: NULL batch");
+  if (!valid_shape(CGP_TUNE_SOLVE_FP64, block, lanes) || blocks_per_sm < 0 || (flags & ~1))
+    return fail(CGP_ERR_INVALID_ARG, "cgp_batch_set_tuning: bad shape");
+  return batch_plan(batch, BatchShape{block, lanes, blocks_per_sm, flags}, batch->opts);
+}
+
+extern "C" int cgp_batch_solve(cgp_batch batch, void* stream) {
+  if (!batch) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_solve: NULL batch");
+  return batch_launch(batch, (cudaStream_t)stream);
+}
+
+extern "C" int cgp_batch_info(cgp_batch batch, cgp_solve_info* infos, double* seconds) {
+  if (!batch) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_info: NULL batch");
+  std::vector<unsigned char> h(batch->ctrl_bytes);
+  CGP_CUDA(cudaDeviceSynchronize());
+  CGP_CUDA(cudaMemcpy(h.data(), batch->d_ctrl, batch->ctrl_bytes, cudaMemcpyDeviceToHost));
+  unsigned long long t0 = 0;
+  std::memcpy(&t0, h.data() + kCtrlPerInstance * batch->count, sizeof(t0));
+  int worst = CGP_OK;
+  for (int i = 0; i < batch->count; ++i) {
+    SolveResult r;
+    std::memcpy(&r, h.data() + kCtrlPerInstance * i + 256, sizeof(r));
+    const int status = r.timeout ? CGP_ERR_TIMEOUT : r.status;
+    if (infos) {
+      infos[i].iterations = r.iterations;
+      infos[i].outer_sweeps = r.sweeps;
+      infos[i].rel_res_recursive = r.rel_rec;
+      infos[i].rel_res_true = r.rel_true;
+      infos[i].status = status;
+    }
+    if (seconds) seconds[i] = r.t_end > t0 ? (double)(r.t_end - t0) * 1e-9 : 0.0;
+    if (status != CGP_OK && worst == CGP_OK) worst = status;
+  }
+  if (worst != CGP_OK) return fail(worst, "cgp_batch_info: at least one instance did not converge");
+  return CGP_OK;
+}
+
+extern "C" int cgp_batch_query(cgp_batch batch, int* grid, int* block, int* lanes, int* resident, int* blocks) {
+  if (!batch) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_query: NULL batch");
+  if (grid) *grid = batch->grid;
+  if (block) *block = batch->shape.block;
+  if (lanes) *lanes = batch->shape.lanes;
+  if (resident) *resident = batch->res ? 1 : 0;
+  if (blocks)
+    for (int i = 0; i < batch->count; ++i) blocks[i] = batch->nblk[i];
+  return CGP_OK;
+}
+
+extern "C" int cgp_batch_autotune(cgp_batch batch, void* stream, double* best_ms) {
+  if (!batch) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_autotune: NULL batch");
+  cudaStream_t s = (cudaStream_t)stream;
+  cgp_solve_opts o = batch->opts;
+  o.use_x0 = 0;  // every candidate solves the same problem from zero
+  cudaEvent_t e0, e1;
+  CGP_CUDA(cudaEventCreate(&e0));
+  CGP_CUDA(cudaEventCreate(&e1));
+  BatchShape best{};
+  float best_t = 1e30f;
+  const int blocks[2] = {256, 512};
+  const int lanes[2] = {1, 2};
+  const int per_sm[2] = {1, 2};
+  for (int fl = 0; fl < 2; ++fl)
+    for (int bk : blocks)
+      for (int ln : lanes)
+        for (int ps : per_sm) {
+          BatchShape cand{bk, ln, ps, fl};
+          if (batch_plan(batch, cand, o) != CGP_OK) continue;
+          float t = 1e30f;
+          for (int rep = 0; rep < 2; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess || batch_launch(batch, s) != CGP_OK ||
+                cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+              break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t = std::min(t, ms);
+          }
+          if (t < best_t) {
+            best_t = t;
+            best = cand;
+          }
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_t >= 1e29f) return fail(CGP_ERR_CUDA, "cgp_batch_autotune: no candidate ran");
+  int st = batch_plan(batch, best, batch->opts);
+  if (st != CGP_OK) return st;
+  if (best_ms) *best_ms = best_t;
+  return CGP_OK;
+}
+
+extern "C" int cgp_batch_destroy(cgp_batch batch) {
+  if (!batch) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_destroy: NULL batch");
+  cudaDeviceSynchronize();
+  if (batch->d_desc) cudaFree(batch->d_desc);
+  if (batch->d_blk_inst) cudaFree(batch->d_blk_inst);
+  if (batch->d_ctrl) cudaFree(batch->d_ctrl);
+  delete batch;
+  return CGP_OK;
+}
+
+extern "C" int cgp_poisson_solve_batched(const cgp_mesh* meshes, int count, const double* const* b,
+                                         double* const* x, const cgp_solve_opts* opts, cgp_solve_info* infos,
+                                         void* stream) {
+  cgp_batch batch = nullptr;
+  int st = cgp_batch_create(meshes, count, b, x, opts, &batch);
+  if (st != CGP_OK) return st;
+  st = cgp_batch_solve(batch, stream);
+  if (st == CGP_OK && infos) st = cgp_batch_info(batch, infos, nullptr);
+  if (st == CGP_OK && !infos) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+  }
+  const std::string msg = cgp_last_error();
+  cgp_batch_destroy(batch);
+  if (st != CGP_OK) fail(st, msg);
+  return st;
 }
