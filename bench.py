@@ -39,6 +39,7 @@ RHO_OVER_DT = 20.0
 L2_FLUSH_BYTES = 512 << 20
 SPMV_MESH = (2048, 1024)       # > L2 in FP64 and FP32
 KERNELS_PER_STEP = 8           # 2 x (restrict_rhs, persistent PCG, prolong, lorentz)
+FP64_PEAK_TFLOPS = 1.25        # nominal dense FP64 of a GB300
 
 
 def workload_config(precision="fp64"):
@@ -80,6 +81,20 @@ def pcg_launch_bytes(iters, n, nnz):
     setup = 16 * n + 32 * n + (12 * nnz + 4 * n + 8 * n) + 48 * n
     final = 24 * n + (12 * nnz + 4 * n + 8 * n) + 8 * n
     return setup + iters * pcg_iteration_bytes(n, nnz) + final
+
+
+def pcg_launch_flops(iters, n, nnz):
+    """FP64 flops of the FP64 launch: per iteration 2 nnz (SpMV) + 13 n (updates, D^-1 r, three dots)."""
+    return iters * (2 * nnz + 13 * n) + 4 * nnz + 20 * n
+
+
+def mixed_launch_bytes(inner_iters, sweeps, n, nnz):
+    """Mixed launch: per inner FP32 iteration of the single-reduction CG, the FP32 SpMV
+    (8 nnz + 4(n+1) + 8 n) and 15 FP32 vector streams (p, s, e, r, u updates, r/w/s published);
+    per sweep the FP64 residual SpMV and 6 FP64 vector streams."""
+    inner = 8 * nnz + 4 * (n + 1) + 8 * n + 60 * n
+    outer = 12 * nnz + 4 * (n + 1) + 16 * n + 48 * n
+    return inner_iters * inner + (sweeps + 1) * outer
 
 
 # ---------------------------------------------------------------------------
@@ -160,6 +175,7 @@ def run_mine(args, rank, world, local_rank):
     n, nnz = mesh.n_c, mesh.nnz
     W, K = args.warmup, args.steps
     total_steps = W + K
+    precision = cgp.CGP_MIXED if args.precision == "mixed" else cgp.CGP_FP64
 
     # host inputs: one velocity field per time step (pinned for the end-to-end pass)
     U = torch.empty((total_steps, 2, mesh.n_f), dtype=torch.float64).pin_memory()
@@ -181,18 +197,28 @@ def run_mine(args, rank, world, local_rank):
     n_info = 2 * total_steps + 2 * K
     infos = torch.zeros(n_info * cgp.INFO_BYTES, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    precision = cgp.CGP_MIXED if args.precision == "mixed" else cgp.CGP_FP64
     info_addr = lambda slot: infos.data_ptr() + slot * cgp.INFO_BYTES  # noqa: E731
+
+    # launch shapes for this mesh, picked by timing on the first step's potential RHS
+    cgp.cgp_restrict(mesh.handle, cgp.CGP_RHS_POTENTIAL, B_FIELD, RHO_OVER_DT, Ud[0, 0], Ud[0, 1], b)
+    tune_x = torch.zeros(n, **f64)
+    tuned = {}
+    for prec in (cgp.CGP_FP64, cgp.CGP_MIXED):
+        best_ms = cgp.cgp_autotune(mesh.handle, prec, b, tune_x)
+        what = cgp.CGP_TUNE_SOLVE_MIXED if prec == cgp.CGP_MIXED else cgp.CGP_TUNE_SOLVE_FP64
+        tuned["mixed" if prec else "fp64"] = dict(cgp.cgp_get_tuning(mesh.handle, what), ms=best_ms)
+    del tune_x
 
     solve_events = []
 
     def step(uf, vf, warm, slot, timing=False):
+        prec = precision
         cgp.cgp_restrict(mesh.handle, cgp.CGP_RHS_POTENTIAL, B_FIELD, RHO_OVER_DT, uf, vf, b)
         e0 = torch.cuda.Event(enable_timing=True) if timing else None
         e1 = torch.cuda.Event(enable_timing=True) if timing else None
         if timing:
             e0.record(stream)
-        cgp.cgp_poisson_solve_async(mesh.handle, b, phi_c, tol=TOL, use_x0=warm, precision=precision,
+        cgp.cgp_poisson_solve_async(mesh.handle, b, phi_c, tol=TOL, use_x0=warm, precision=prec,
                                     info_dev=info_addr(slot))
         if timing:
             e1.record(stream)
@@ -204,7 +230,7 @@ def run_mine(args, rank, world, local_rank):
         e3 = torch.cuda.Event(enable_timing=True) if timing else None
         if timing:
             e2.record(stream)
-        cgp.cgp_poisson_solve_async(mesh.handle, b, p_c, tol=TOL, use_x0=warm, precision=precision,
+        cgp.cgp_poisson_solve_async(mesh.handle, b, p_c, tol=TOL, use_x0=warm, precision=prec,
                                     info_dev=info_addr(slot + 1))
         if timing:
             e3.record(stream)
@@ -274,22 +300,136 @@ def run_mine(args, rank, world, local_rank):
         raise RuntimeError(f"{len(bad)} solves did not converge: {bad[:3]}")
     its = [r["iterations"] for r in timed]
 
+    # ---- the same timed steps in the other precision: speed and agreement ----
+    other = cgp.CGP_FP64 if precision == cgp.CGP_MIXED else cgp.CGP_MIXED
+    alt = {}
+    if not args.no_variants:
+        phi_c.copy_(phi_keep)
+        p_c.copy_(p_keep)
+        main_fields = []
+        # reference fields of the main precision for the first timed step
+        phi_c.copy_(phi_keep)
+        p_c.copy_(p_keep)
+        step(Ud[W, 0], Ud[W, 1], W > 0, 2 * W)
+        torch.cuda.synchronize()
+        main_fields = [phi_f.clone(), force.clone(), grad_p.clone()]
+        phi_c.copy_(phi_keep)
+        p_c.copy_(p_keep)
+        saved_prec = precision
+        precision = other
+        alt_events = []
+        for j in range(K):
+            k = W + j
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(Ud[k, 0], Ud[k, 1], k > 0, 2 * k)
+            e1.record(stream)
+            alt_events.append((e0, e1))
+            if j == 0:
+                torch.cuda.synchronize()
+                rel = lambda a, r: float(torch.linalg.norm(a - r) / torch.linalg.norm(r))  # noqa: E731
+                alt["rel_err_vs_main"] = {"phi_f": rel(phi_f, main_fields[0]), "force": rel(force, main_fields[1]),
+                                          "grad_p": rel(grad_p, main_fields[2])}
+        torch.cuda.synchronize()
+        alt_ms = sum(a.elapsed_time(c) for a, c in alt_events)
+        alt_recs = cgp.decode_infos(bytes(infos.cpu().numpy()), n_info)[2 * W: 2 * total_steps]
+        alt.update(precision="mixed" if other == cgp.CGP_MIXED else "fp64", value=2 * K / (alt_ms * 1e-3),
+                   ms_per_step=alt_ms / K,
+                   inner_iterations_mean=statistics.mean(r["iterations"] for r in alt_recs),
+                   sweeps_mean=statistics.mean(r["outer_sweeps"] for r in alt_recs),
+                   all_converged=all(r["status"] == cgp.CGP_OK for r in alt_recs),
+                   rel_res_true_max=max(r["rel_res_true"] for r in alt_recs))
+        precision = saved_prec
+
+
     # ---- roofline of the dominant kernel (the persistent PCG launch) ----
     peak, peak_kind = read_peaks()
-    alg_bytes = [pcg_launch_bytes(i if precision == cgp.CGP_FP64 else 0, n, nnz) for i in its]
+    if precision == cgp.CGP_FP64:
+        alg_bytes = [pcg_launch_bytes(r["iterations"], n, nnz) for r in timed]
+    else:
+        alg_bytes = [mixed_launch_bytes(r["iterations"], r["outer_sweeps"], n, nnz) for r in timed]
+    fp64_flops = sum(pcg_launch_flops(r["iterations"], n, nnz) for r in timed) if precision == cgp.CGP_FP64 else 0
     pcg_total_ms = sum(solve_ms)
     achieved = sum(alg_bytes) / (pcg_total_ms * 1e-3) / 1e9
 
     result = dict(dev_ms=dev_ms, e2e_ms=e2e_ms, solves=2 * K, step_ms=step_ms, solve_ms=solve_ms, its=its,
                   achieved=achieved, alg_bytes_per_launch=sum(alg_bytes) / len(alg_bytes),
+                  fp64_tflops=fp64_flops / (pcg_total_ms * 1e-3) / 1e12, tuned=tuned, variant=alt,
                   pcg_share=pcg_total_ms / dev_ms, clocks=clocks.summary(), peak=peak, peak_kind=peak_kind,
                   h2d=h2d, d2h=d2h, n=n, nnz=nnz,
                   rel_res_true_max=max(r["rel_res_true"] for r in timed))
 
     if rank == 0 and not args.no_spmv:
         result["spmv"] = spmv_bench(cgp, inputs, torch, dev, flush, peak)
+    if rank == 0 and not args.no_variants:
+        from paper_2003_00082_gb300 import configs
+        result["batched"] = run_batched(cgp, inputs, configs, torch, dev, flush, peak)
     mesh.close()
     return result
+
+
+def run_batched(cgp, inputs, configs, torch, dev, flush, peak, reps=5):
+    """64 uneven CGP potential solves (n_theta in {64,...,512}) in one persistent launch, mixed precision."""
+    insts = configs.batched_instances()
+    meshes, bs, xs = [], [], []
+    for inst in insts:
+        xy, tri = inputs.ogrid(inst["n_theta"], inst["n_r"])
+        m = cgp.Mesh(xy, tri)
+        xy_f, _, _ = m.fine_geometry()
+        u, v = inputs.velocity(xy_f, 0, inst["seed"], vortices=True)
+        b = torch.empty(m.n_c, dtype=torch.float64, device=dev)
+        cgp.cgp_restrict(m.handle, cgp.CGP_RHS_POTENTIAL, inst["B"], RHO_OVER_DT, torch.as_tensor(u, device=dev),
+                         torch.as_tensor(v, device=dev), b)
+        meshes.append(m)
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    batch = cgp.Batch(meshes, bs, xs, tol=TOL, precision=cgp.CGP_MIXED, inner_tol=1e-4)
+    tune_ms = batch.autotune()
+    # capture the launch once; replays need no host work
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=side):
+        batch.solve()
+    times, lat, infos = [], [], None
+    for r in range(reps + 1):
+        for x in xs:
+            x.zero_()
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        infos, secs = batch.info()
+        if r > 0:
+            times.append(e0.elapsed_time(e1))
+            lat.extend(secs)
+    ms = statistics.median(times)
+    lat_ms = sorted(1e3 * t for t in lat)
+    pct = lambda q: lat_ms[min(len(lat_ms) - 1, int(round(q * (len(lat_ms) - 1))))]  # noqa: E731
+    alg = sum(mixed_launch_bytes(i["iterations"], i["outer_sweeps"], m.n_c, m.nnz) for i, m in zip(infos, meshes))
+    q = batch.query()
+    out = {"workload": "64 CGP potential solves, coarse O-grids n_theta ~ U{64,128,256,512} (n_r = n_theta/2), "
+                       "N ~ U[0.5,5], B = (cos a, sin a, 1), one persistent launch replayed from a CUDA graph",
+           "instances": len(meshes), "coarse_rows_total": sum(m.n_c for m in meshes),
+           "fine_nodes_total": sum(m.n_f for m in meshes), "precision": "fp32 inner + fp64 refinement",
+           "tol": TOL, "value": len(meshes) / (ms * 1e-3), "unit": "solves/s", "ms_per_batch": ms,
+           "latency_ms_p50": pct(0.5), "latency_ms_p99": pct(0.99),
+           "all_converged": all(i["status"] == cgp.CGP_OK for i in infos),
+           "rel_res_true_max": max(i["rel_res_true"] for i in infos),
+           "inner_iterations_max": max(i["iterations"] for i in infos),
+           "hbm": {"achieved_gb_s": alg / (ms * 1e-3) / 1e9, "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                   "alg_bytes": alg},
+           "launch": {"grid": q["grid"], "block": q["block"], "lanes": q["lanes"], "resident": q["resident"]},
+           "autotune_best_ms": tune_ms}
+    batch.close()
+    for m in meshes:
+        m.close()
+    return out
 
 
 def spmv_bench(cgp, inputs, torch, dev, flush, peak, reps=15):
@@ -412,6 +552,7 @@ def main():
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-spmv", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the other-precision and batched passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -463,7 +604,10 @@ def main():
                          "kernel": "pcg_persistent_kernel",
                          "alg_bytes_per_launch": res["alg_bytes_per_launch"],
                          "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({res['peak_kind']})",
-                         "kernel_share_of_step": res["pcg_share"]},
+                         "kernel_share_of_step": res["pcg_share"],
+                         "fp64_alu": {"achieved_tflops": res["fp64_tflops"], "peak_tflops": FP64_PEAK_TFLOPS,
+                                      "frac": res["fp64_tflops"] / FP64_PEAK_TFLOPS,
+                                      "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s)"}},
             "cpu_baseline": cpu,
             "e2e": {"value": total_solves / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},
@@ -474,6 +618,11 @@ def main():
         }
         if "spmv" in res:
             line["spmv"] = res["spmv"]
+        if res.get("variant"):
+            line["other_precision"] = res["variant"]
+        if "batched" in res:
+            line["batched"] = res["batched"]
+        line["tuned_launch"] = res["tuned"]
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -299,6 +299,22 @@ int cgp_set_tuning(cgp_mesh m, int what, int block, int lanes, int blocks, int f
 int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks, int* flags);
 
 /*
+ * cgp_autotune - pick the solver's launch shape for this mesh by timing.
+ *
+ * Runs the solve (precision CGP_FP64 or CGP_MIXED, tol 1e-8, from x = 0) on
+ * the caller's right-hand side b (device [n_c]) for every candidate of
+ * threads per block {256, 512}, lanes per CSR row {1, 2, 4}, grid size (a
+ * few counts around the SM count, and 1..16 blocks for small systems) and
+ * shared-memory residency, and keeps the fastest with cgp_set_tuning.  x
+ * (device [n_c]) is overwritten.  cache_path (nullable) names a text file of
+ * earlier results keyed by GPU name, n, nnz and target: a hit applies the
+ * cached shape without timing (best_ms = -1), a miss appends the new
+ * result.  Synchronous.
+ */
+int cgp_autotune(cgp_mesh m, int precision, const double* b, double* x, const char* cache_path, void* stream,
+                 double* best_ms);
+
+/*
  * cgp_last_launch - shape of the last persistent solver launch on this mesh.
  * precision CGP_FP64 or CGP_MIXED; outputs (any may be NULL): grid blocks,
  * threads per block, whether each block kept its rows in shared memory, and

@@ -35,7 +35,7 @@ CGP_FP32 = 1          # precision argument of cgp_spmv for the FP32 copy of K
 EXPORTS = ("cgp_assemble", "cgp_mesh_query", "cgp_mesh_fine_geometry", "cgp_mesh_matrices",
            "cgp_restrict", "cgp_poisson_solve", "cgp_poisson_solve_async",
            "cgp_poisson_solve_noalloc", "cgp_prolong", "cgp_lorentz", "cgp_spmv",
-           "cgp_set_tuning", "cgp_get_tuning", "cgp_last_launch", "cgp_barrier_selftest",
+           "cgp_set_tuning", "cgp_get_tuning", "cgp_autotune", "cgp_last_launch", "cgp_barrier_selftest",
            "cgp_batch_create", "cgp_batch_solve", "cgp_batch_info", "cgp_batch_set_tuning",
            "cgp_batch_autotune", "cgp_batch_query", "cgp_batch_destroy", "cgp_poisson_solve_batched", "cgp_mesh_destroy",
            "cgp_last_error")
@@ -100,6 +100,7 @@ def load(path: str | None = None):
         "cgp_set_tuning": [vp, i, i, i, i, i],
         "cgp_get_tuning": [vp, i, ip, ip, ip, ip],
         "cgp_last_launch": [vp, i, ip, ip, ip, ip],
+        "cgp_autotune": [vp, i, vp, vp, ctypes.c_char_p, vp, dp],
         "cgp_barrier_selftest": [i, i, ctypes.c_longlong, vp],
         "cgp_mesh_destroy": [vp],
         "cgp_batch_create": [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -276,6 +277,14 @@ def cgp_get_tuning(mesh, what):
     v = [ctypes.c_int() for _ in range(4)]
     _check(load().cgp_get_tuning(mesh, int(what), *[ctypes.byref(a) for a in v]))
     return dict(block=v[0].value, lanes=v[1].value, blocks=v[2].value, flags=v[3].value)
+
+
+def cgp_autotune(mesh, precision, b, x, cache_path=None, stream=None):
+    """Time the solver's launch shapes on b and keep the fastest; returns the best time in ms (-1: cache hit)."""
+    best = ctypes.c_double()
+    path = cache_path.encode() if cache_path else None
+    _check(load().cgp_autotune(mesh, int(precision), _dev(b), _dev(x), path, _stream(stream), ctypes.byref(best)))
+    return best.value
 
 
 def cgp_last_launch(mesh, precision=CGP_FP64):

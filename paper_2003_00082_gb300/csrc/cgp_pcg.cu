@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -1941,4 +1942,110 @@ extern "C" int cgp_poisson_solve_batched(const cgp_mesh* meshes, int count, cons
   cgp_batch_destroy(batch);
   if (st != CGP_OK) fail(st, msg);
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner for single solves
+// ---------------------------------------------------------------------------
+namespace {
+
+std::string device_name(int device) {
+  cudaDeviceProp p{};
+  if (cudaGetDeviceProperties(&p, device) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string n = p.name;
+  for (char& c : n)
+    if (c == ' ') c = '_';
+  return n;
+}
+
+// Cache lines: "<gpu> <n> <nnz> <target> <block> <lanes> <blocks> <flags> <ms>"
+bool cache_lookup(const char* path, const std::string& gpu, int n, int nnz, int what, SolverTuning& out) {
+  if (!path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char name[256];
+  int cn, cnnz, cw, b, l, k, fl;
+  double ms;
+  bool found = false;
+  while (std::fscanf(f, "%255s %d %d %d %d %d %d %d %lf", name, &cn, &cnnz, &cw, &b, &l, &k, &fl, &ms) == 9) {
+    if (gpu == name && cn == n && cnnz == nnz && cw == what) {
+      out = SolverTuning{b, l, k, fl};
+      found = true;  // the last matching line wins
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& gpu, int n, int nnz, int what, const SolverTuning& t,
+                 double ms) {
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %d %d %d %d %d %.6f\n", gpu.c_str(), n, nnz, what, t.block, t.lanes, t.blocks,
+               t.flags, ms);
+  std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" int cgp_autotune(cgp_mesh m, int precision, const double* b, double* x, const char* cache_path,
+                            void* stream, double* best_ms) {
+  if (!m || !b || !x) return fail(CGP_ERR_INVALID_ARG, "cgp_autotune: NULL argument");
+  if (precision != CGP_FP64 && precision != CGP_MIXED) return fail(CGP_ERR_INVALID_ARG, "cgp_autotune: precision");
+  const int what = precision == CGP_MIXED ? CGP_TUNE_SOLVE_MIXED : CGP_TUNE_SOLVE_FP64;
+  const std::string gpu = device_name(m->device);
+  SolverTuning cached{};
+  if (cache_lookup(cache_path, gpu, m->n_c, m->nnz, what, cached)) {
+    m->tune[what] = cached;
+    if (best_ms) *best_ms = -1.0;
+    return CGP_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cgp_solve_opts o{1e-8, 20000, precision, 1e-4, 0, 50};
+  const int sms = std::max(1, dev_info(m->device).sms);
+  std::vector<int> counts;
+  if (m->n_c <= 16384) counts = {1, 2, 4, 8, 16};
+  for (int c : {sms / 2, sms, 2 * sms})
+    if (c >= 1 && c <= m->n_c / 32) counts.push_back(c);
+  if (counts.empty()) counts.push_back(1);
+  cudaEvent_t e0, e1;
+  CGP_CUDA(cudaEventCreate(&e0));
+  CGP_CUDA(cudaEventCreate(&e1));
+  const SolverTuning saved = m->tune[what];
+  SolverTuning best{};
+  float best_t = 1e30f;
+  for (int fl = 0; fl < 2; ++fl)
+    for (int bk : {256, 512})
+      for (int ln : {1, 2, 4})
+        for (int c : counts) {
+          m->tune[what] = SolverTuning{bk, ln, c, fl};
+          float t = 1e30f;
+          for (int rep = 0; rep < 2; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess || launch_solve(m, b, x, o, nullptr, s) != CGP_OK ||
+                cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+              break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t = std::min(t, ms);
+          }
+          cudaGetLastError();
+          if (t < best_t) {
+            best_t = t;
+            best = m->tune[what];
+          }
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_t >= 1e29f) {
+    m->tune[what] = saved;
+    return fail(CGP_ERR_CUDA, "cgp_autotune: no candidate ran");
+  }
+  m->tune[what] = best;
+  cache_store(cache_path, gpu, m->n_c, m->nnz, what, best, best_t);
+  if (best_ms) *best_ms = best_t;
+  return CGP_OK;
 }

@@ -350,3 +350,26 @@ def test_spmv_matches_oracle(pair, cgp, lanes):
     scale = np.abs(om.K) @ np.abs(x)
     assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-15 * 8 * scale + 1e-300)
     assert np.all(np.abs(y32.cpu().numpy() - ref) <= 1e-6 * 8 * scale + 1e-30)
+
+
+def test_autotune_times_candidates_and_caches_the_choice(cgp, tmp_path):
+    xy, tri = inputs.ogrid(64, 32)
+    m = cgp.Mesh(xy, tri)
+    om = O.OracleMesh(xy, tri)
+    u, v = velocity_for(om)
+    b = T(oracle_rhs(om, u, v))
+    x = torch.zeros(m.n_c, dtype=torch.float64, device=DEV)
+    cache = str(tmp_path / "tune.txt")
+    best = cgp.cgp_autotune(m.handle, cgp.CGP_FP64, b, x, cache)
+    assert best > 0.0
+    chosen = cgp.cgp_get_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64)
+    assert chosen["block"] in (256, 512) and chosen["lanes"] in (1, 2, 4)
+    cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64, 0, 0, 0, 0)
+    assert cgp.cgp_autotune(m.handle, cgp.CGP_FP64, b, x, cache) == -1.0      # cache hit
+    assert cgp.cgp_get_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64) == chosen
+    x.zero_()
+    info = cgp.cgp_poisson_solve(m.handle, b, x, tol=1e-10)
+    ref = O.pcg(om.K, om.d, b.cpu().numpy(), tol=1e-10)
+    assert info["status"] == cgp.CGP_OK
+    assert rel(x.cpu().numpy(), ref["x"]) <= 1e-8
+    m.close()
