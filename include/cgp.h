@@ -243,6 +243,53 @@ int cgp_poisson_solve_batched(const cgp_mesh* meshes, int count, const double* c
                               const cgp_solve_opts* opts, cgp_solve_info* infos, void* stream);
 
 /*
+ * Learned initial guess: a message-passing network on the coarse mesh's edges.
+ *
+ * The paper has no learned component; this is the spec addition (4)
+ * that predicts the PCG starting point of the potential solve (Eq. 12) from
+ * the right-hand side b and the two previous solutions.  Per coarse node i,
+ * f_i = [b/s_b, phi1/s_phi, phi2/s_phi, x/15, y/15] (s = rms over nodes);
+ * h0 = relu(We f + be); three layers of m_ij = relu(Wm [h_i; h_j; e_ij] + bm)
+ * over the directed mesh edges i <- j (e_ij = (dx, dy, |d|) / mean edge
+ * length), a_i = sum_j m_ij, h_i += relu(Wu [h_i; a_i] + bu); out = Wd h + bd;
+ * x0 = phi1 + s_phi * out (the solver projects x0 to mean zero).  Hidden width
+ * 64; the dense layers run on the tensor cores in BF16 with FP32
+ * accumulation; weights are kept in FP32 for Adam (lr given per step, betas
+ * 0.9 / 0.999, eps 1e-8).  The training target is (phi(t) - phi1) / s_phi
+ * and the loss the mean squared error over all nodes of the batch.
+ *
+ * Parameters are one FP32 vector of cgp_gnn_param_count() values in this
+ * order, row-major: We [64][5], be [64], then for l = 0, 1, 2: Wm_l [64][131],
+ * bm_l [64], Wu_l [64][128], bu_l [64]; then Wd [64], bd [1].
+ *
+ * cgp_gnn_create   network for mesh m, training batches up to max_batch
+ *                  samples; params host [param_count].  Allocates its device
+ *                  memory; synchronous.
+ * cgp_gnn_predict  x0 (device [n_c]) from b, phi1, phi2 (device [n_c]); async.
+ * cgp_gnn_train_step  forward, loss, backward and one Adam step on `batch`
+ *                  samples stacked sample-major (device [batch][n_c] each,
+ *                  phi_t the solutions to learn); loss_dev (device float,
+ *                  nullable) receives the batch loss; async.
+ * cgp_gnn_gradients  forward + backward without the update; copies the
+ *                  gradient (host [param_count]), the raw outputs (host
+ *                  [batch][n_c]) and the loss (host) when non-NULL; synchronous.
+ * cgp_gnn_get_params / cgp_gnn_set_params  host copies of the FP32 weights
+ *                  (set also resets the Adam state); synchronous.
+ */
+typedef struct cgp_gnn_s* cgp_gnn;
+
+int cgp_gnn_param_count(void);
+int cgp_gnn_create(cgp_mesh m, int max_batch, const float* params, cgp_gnn* out);
+int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, const double* phi2, double* x0, void* stream);
+int cgp_gnn_train_step(cgp_gnn g, int batch, const double* b, const double* phi1, const double* phi2,
+                       const double* phi_t, float lr, float* loss_dev, void* stream);
+int cgp_gnn_gradients(cgp_gnn g, int batch, const double* b, const double* phi1, const double* phi2,
+                      const double* phi_t, float* grads, float* out, float* loss, void* stream);
+int cgp_gnn_get_params(cgp_gnn g, float* params);
+int cgp_gnn_set_params(cgp_gnn g, const float* params);
+int cgp_gnn_destroy(cgp_gnn g);
+
+/*
  * cgp_prolong - prolongation by the P1 shape functions (Eq. 20) for one level:
  * x_f[i] = x_c[i] for coarse nodes, x_f[n_c + e] = (x_c[a_e] + x_c[b_e]) / 2 at
  * the midpoint of edge e (shape functions 1/2, 1/2, 0 there).

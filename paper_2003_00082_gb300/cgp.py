@@ -37,7 +37,9 @@ EXPORTS = ("cgp_assemble", "cgp_mesh_query", "cgp_mesh_fine_geometry", "cgp_mesh
            "cgp_poisson_solve_noalloc", "cgp_prolong", "cgp_lorentz", "cgp_spmv",
            "cgp_set_tuning", "cgp_get_tuning", "cgp_autotune", "cgp_last_launch", "cgp_barrier_selftest",
            "cgp_batch_create", "cgp_batch_solve", "cgp_batch_info", "cgp_batch_set_tuning",
-           "cgp_batch_autotune", "cgp_batch_query", "cgp_batch_destroy", "cgp_poisson_solve_batched", "cgp_mesh_destroy",
+           "cgp_batch_autotune", "cgp_batch_query", "cgp_batch_destroy", "cgp_poisson_solve_batched",
+           "cgp_gnn_param_count", "cgp_gnn_create", "cgp_gnn_predict", "cgp_gnn_train_step", "cgp_gnn_gradients",
+           "cgp_gnn_get_params", "cgp_gnn_set_params", "cgp_gnn_destroy", "cgp_mesh_destroy",
            "cgp_last_error")
 
 CGP_TUNE_SOLVE_FP64 = 0
@@ -113,6 +115,14 @@ def load(path: str | None = None):
         "cgp_batch_destroy": [vp],
         "cgp_poisson_solve_batched": [ctypes.POINTER(vp), i, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                       ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp],
+        "cgp_gnn_param_count": [],
+        "cgp_gnn_create": [vp, i, vp, ctypes.POINTER(vp)],
+        "cgp_gnn_predict": [vp, vp, vp, vp, vp, vp],
+        "cgp_gnn_train_step": [vp, i, vp, vp, vp, vp, ctypes.c_float, vp, vp],
+        "cgp_gnn_gradients": [vp, i, vp, vp, vp, vp, vp, vp, vp, vp],
+        "cgp_gnn_get_params": [vp, vp],
+        "cgp_gnn_set_params": [vp, vp],
+        "cgp_gnn_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -402,6 +412,88 @@ def cgp_batch_query(batch):
 
 def cgp_batch_destroy(batch):
     batch.close()
+
+
+def cgp_gnn_param_count():
+    return load().cgp_gnn_param_count()
+
+
+class GNN:
+    """The learned initial-guess network of a mesh (cgp_gnn_* calls)."""
+
+    def __init__(self, mesh, max_batch, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != cgp_gnn_param_count():
+            raise ValueError("params has the wrong length")
+        self.n = mesh.n_c
+        self.handle = ctypes.c_void_p()
+        _check(load().cgp_gnn_create(mesh.handle, int(max_batch), p.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.byref(self.handle)))
+
+    def predict(self, b, phi1, phi2, x0, stream=None):
+        _check(load().cgp_gnn_predict(self.handle, _dev(b), _dev(phi1), _dev(phi2), _dev(x0), _stream(stream)))
+
+    def train_step(self, batch, b, phi1, phi2, phi_t, lr=1e-3, loss_dev=None, stream=None):
+        _check(load().cgp_gnn_train_step(self.handle, int(batch), _dev(b), _dev(phi1), _dev(phi2), _dev(phi_t),
+                                         float(lr), _dev(loss_dev, "float32"), _stream(stream)))
+
+    def gradients(self, batch, b, phi1, phi2, phi_t, stream=None):
+        """(grads [P], raw outputs [batch, n], loss); synchronous."""
+        g = np.empty(cgp_gnn_param_count(), dtype=np.float32)
+        out = np.empty((batch, self.n), dtype=np.float32)
+        loss = np.empty(1, dtype=np.float32)
+        _check(load().cgp_gnn_gradients(self.handle, int(batch), _dev(b), _dev(phi1), _dev(phi2), _dev(phi_t),
+                                        g.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                                        loss.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+        return g, out, float(loss[0])
+
+    def get_params(self):
+        p = np.empty(cgp_gnn_param_count(), dtype=np.float32)
+        _check(load().cgp_gnn_get_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)))
+        return p
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().cgp_gnn_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().cgp_gnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cgp_gnn_create(mesh, max_batch, params):
+    return GNN(mesh, max_batch, params)
+
+
+def cgp_gnn_predict(g, b, phi1, phi2, x0, stream=None):
+    g.predict(b, phi1, phi2, x0, stream)
+
+
+def cgp_gnn_train_step(g, *a, **k):
+    g.train_step(*a, **k)
+
+
+def cgp_gnn_gradients(g, *a, **k):
+    return g.gradients(*a, **k)
+
+
+def cgp_gnn_get_params(g):
+    return g.get_params()
+
+
+def cgp_gnn_set_params(g, params):
+    g.set_params(params)
+
+
+def cgp_gnn_destroy(g):
+    g.close()
 
 
 class Mesh:

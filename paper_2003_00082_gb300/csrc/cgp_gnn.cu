@@ -1,0 +1,837 @@
+// Learned PCG initial guess: a message-passing network on the coarse mesh's
+// edges (hidden width 64, three layers), with its training step.
+//
+//   f_i  = [b/s_b, phi1/s_phi, phi2/s_phi, x/15, y/15]          s = rms over nodes
+//   h0   = relu(We f + be)
+//   m_ij = relu(Wm_l [h_i ; h_j ; e_ij] + bm_l)     (directed edge i <- j, e_ij = (dx, dy, |d|)/ell)
+//   a_i  = sum_j m_ij
+//   h_i  = h_i + relu(Wu_l [h_i ; a_i] + bu_l)
+//   out  = Wd h + bd,   x0 = phi1 + s_phi out       (the solver projects x0 to mean zero)
+//
+// The two dense layers of every message-passing step run on the tensor
+// cores as BF16 x BF16 -> FP32 mma.sync tiles (16 rows x 64 outputs per
+// warp), with the edge gather in the prologue and bias + ReLU + BF16
+// rounding in the epilogue.  Activations h, messages m, aggregates a and
+// the dense weights are stored in BF16; master weights, Adam moments,
+// gradients and every sum are FP32.  Aggregations and all gradient sums run
+// in a fixed order (no atomics), so training is deterministic.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cgp_internal.h"
+
+namespace cgp {
+namespace gnn {
+
+constexpr int H = 64;
+constexpr int NL = 3;
+constexpr int FIN = 5;
+constexpr int KM = 2 * H + 3;       // message input width
+constexpr int KMP = 144;            // padded to a multiple of 16
+constexpr int KU = 2 * H;           // update input width
+constexpr int LDM = KMP + 8;        // smem row strides (bank spread)
+constexpr int LDU = KU + 8;
+constexpr int TILE = 128;           // rows per tensor-core block (8 warps x 16)
+
+// parameter layout (FP32, row-major), identical to the oracle's order
+constexpr int OFF_WE = 0, OFF_BE = OFF_WE + H * FIN;
+constexpr int LAYER0 = OFF_BE + H;
+constexpr int L_WM = 0, L_BM = H * KM, L_WU = L_BM + H, L_BU = L_WU + H * KU, L_SIZE = L_BU + H;
+constexpr int OFF_WD = LAYER0 + NL * L_SIZE, OFF_BD = OFF_WD + H;
+constexpr int NPARAM = OFF_BD + 1;
+
+__host__ __device__ constexpr int layer_off(int l) { return LAYER0 + l * L_SIZE; }
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// One warp: acc[16 x 64] += X[16 rows x K] * W^T, X row-major (ldx), W stored
+// as [64 outputs][K] (K contiguous, ldw), K a multiple of 16.
+template <int K>
+__device__ __forceinline__ void warp_tile_mma(const bf16* X, int ldx, const bf16* W, int ldw, float (&acc)[8][4]) {
+  const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const unsigned a0 = *reinterpret_cast<const unsigned*>(X + gid * ldx + k0 + tig * 2);
+    const unsigned a1 = *reinterpret_cast<const unsigned*>(X + (gid + 8) * ldx + k0 + tig * 2);
+    const unsigned a2 = *reinterpret_cast<const unsigned*>(X + gid * ldx + k0 + 8 + tig * 2);
+    const unsigned a3 = *reinterpret_cast<const unsigned*>(X + (gid + 8) * ldx + k0 + 8 + tig * 2);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const bf16* w = W + (nt * 8 + gid) * ldw + k0 + tig * 2;
+      const unsigned b0 = *reinterpret_cast<const unsigned*>(w);
+      const unsigned b1 = *reinterpret_cast<const unsigned*>(w + 8);
+      mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// set-up: mean edge length and edge features
+// ---------------------------------------------------------------------------
+__global__ void edge_length_kernel(int E, const int* __restrict__ dst, const int* __restrict__ src,
+                                   const double2* __restrict__ xy, double* __restrict__ ell) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    const double2 a = xy[dst[e]], b = xy[src[e]];
+    const double dx = b.x - a.x, dy = b.y - a.y;
+    s += sqrt(dx * dx + dy * dy);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) *ell = t / E;
+  }
+}
+
+__global__ void edge_feature_kernel(int E, const int* __restrict__ dst, const int* __restrict__ src,
+                                    const double2* __restrict__ xy, const double* __restrict__ ell,
+                                    bf16* __restrict__ ef) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const double2 a = xy[dst[e]], b = xy[src[e]];
+  const double dx = b.x - a.x, dy = b.y - a.y, L = *ell;
+  ef[4 * e + 0] = __float2bfloat16_rn((float)(dx / L));
+  ef[4 * e + 1] = __float2bfloat16_rn((float)(dy / L));
+  ef[4 * e + 2] = __float2bfloat16_rn((float)(sqrt(dx * dx + dy * dy) / L));
+  ef[4 * e + 3] = __float2bfloat16_rn(0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+// One block per sample: scales, input features and (when phi_t is given) targets.
+__global__ void features_kernel(int n, const double* __restrict__ b, const double* __restrict__ phi1,
+                                const double* __restrict__ phi2, const double* __restrict__ phi_t,
+                                const double2* __restrict__ xy, float* __restrict__ f, double* __restrict__ scale,
+                                float* __restrict__ target) {
+  __shared__ double red[2][32];
+  __shared__ double sc[2];
+  const int s = blockIdx.x;
+  const size_t base = (size_t)s * n;
+  double sb = 0.0, sp = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double bi = b[base + i], pi = phi1[base + i];
+    sb += bi * bi;
+    sp += pi * pi;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    sp += __shfl_xor_sync(0xffffffffu, sp, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sb;
+    red[1][threadIdx.x >> 5] = sp;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double tb = threadIdx.x < (blockDim.x >> 5) ? red[0][threadIdx.x] : 0.0;
+    double tp = threadIdx.x < (blockDim.x >> 5) ? red[1][threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      tb += __shfl_xor_sync(0xffffffffu, tb, o);
+      tp += __shfl_xor_sync(0xffffffffu, tp, o);
+    }
+    if (threadIdx.x == 0) {
+      double rb = sqrt(tb / n), rp = sqrt(tp / n);
+      sc[0] = rb > 1e-30 ? rb : 1.0;
+      sc[1] = rp > 1e-30 ? rp : 1.0;
+      scale[s] = sc[1];
+    }
+  }
+  __syncthreads();
+  const double ib = 1.0 / sc[0], ip = 1.0 / sc[1];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 p = xy[i];
+    float* fi = f + (base + i) * FIN;
+    fi[0] = (float)(b[base + i] * ib);
+    fi[1] = (float)(phi1[base + i] * ip);
+    fi[2] = (float)(phi2[base + i] * ip);
+    fi[3] = (float)(p.x / 15.0);
+    fi[4] = (float)(p.y / 15.0);
+    if (phi_t) target[base + i] = (float)((phi_t[base + i] - phi1[base + i]) * ip);
+  }
+}
+
+__global__ void encode_kernel(int rows, const float* __restrict__ P, const float* __restrict__ f,
+                              float* __restrict__ z0, bf16* __restrict__ h0) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * H) return;
+  const int r = t / H, c = t % H;
+  const float* w = P + OFF_WE + c * FIN;
+  float z = P[OFF_BE + c];
+#pragma unroll
+  for (int k = 0; k < FIN; ++k) z = fmaf(w[k], f[(size_t)r * FIN + k], z);
+  z0[t] = z;
+  h0[t] = __float2bfloat16_rn(fmaxf(z, 0.0f));
+}
+
+// Messages of layer l for TILE directed edges (all samples stacked): gather
+// [h_dst | h_src | e | 0] into shared memory, tensor-core product with Wm,
+// bias, ReLU, BF16.
+__global__ void __launch_bounds__(256) message_fwd_kernel(int n, int E, int rows, const int* __restrict__ dst,
+                                                          const int* __restrict__ src, const bf16* __restrict__ ef,
+                                                          const bf16* __restrict__ h, const bf16* __restrict__ Wb,
+                                                          const float* __restrict__ bias, bf16* __restrict__ m) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16* W = reinterpret_cast<bf16*>(smem);            // [H][LDM]
+  bf16* X = W + H * LDM;                              // [TILE][LDM]
+  const int tid = threadIdx.x;
+  for (int i = tid; i < H * KMP / 8; i += blockDim.x) {
+    const int o = i / (KMP / 8), k8 = i % (KMP / 8);
+    *reinterpret_cast<uint4*>(W + o * LDM + k8 * 8) = *reinterpret_cast<const uint4*>(Wb + o * KMP + k8 * 8);
+  }
+  const int r0 = blockIdx.x * TILE;
+  // 18 16-byte pieces per row: 8 of h_dst, 8 of h_src, 1 of edge features, 1 of zeros
+  for (int i = tid; i < TILE * 18; i += blockDim.x) {
+    const int rr = i / 18, piece = i % 18, r = r0 + rr;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r < rows) {
+      const int s = r / E, e = r % E;
+      if (piece < 8) {
+        v = *reinterpret_cast<const uint4*>(h + ((size_t)s * n + dst[e]) * H + piece * 8);
+      } else if (piece < 16) {
+        v = *reinterpret_cast<const uint4*>(h + ((size_t)s * n + src[e]) * H + (piece - 8) * 8);
+      } else if (piece == 16) {
+        const uint2 q = *reinterpret_cast<const uint2*>(ef + 4 * (size_t)e);
+        v = make_uint4(q.x, q.y & 0xffffu, 0u, 0u);   // keep the three features, zero the pad
+      }
+    }
+    *reinterpret_cast<uint4*>(X + rr * LDM + piece * 8) = v;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+  warp_tile_mma<KMP>(X + warp * 16 * LDM, LDM, W, LDM, acc);
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int c = nt * 8 + tig * 2;
+    const float b0 = bias[c], b1 = bias[c + 1];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int r = r0 + warp * 16 + gid + half * 8;
+      if (r < rows) {
+        __nv_bfloat162 v;
+        v.x = __float2bfloat16_rn(fmaxf(acc[nt][2 * half] + b0, 0.0f));
+        v.y = __float2bfloat16_rn(fmaxf(acc[nt][2 * half + 1] + b1, 0.0f));
+        *reinterpret_cast<__nv_bfloat162*>(m + (size_t)r * H + c) = v;
+      }
+    }
+  }
+}
+
+// a_i = sum over the in-edges of i, in edge order (FP32 sum of BF16 messages), stored in BF16.
+__global__ void aggregate_kernel(int n, int E, int B, const int* __restrict__ in_ptr, const bf16* __restrict__ m,
+                                 bf16* __restrict__ a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * n * H) return;
+  const int c = t % H, node = (t / H) % n, s = t / (H * n);
+  float acc = 0.0f;
+  for (int e = in_ptr[node]; e < in_ptr[node + 1]; ++e) acc += __bfloat162float(m[((size_t)s * E + e) * H + c]);
+  a[t] = __float2bfloat16_rn(acc);
+}
+
+// Node update of layer l for TILE nodes: [h | a] x Wu on the tensor cores,
+// u stored for the backward pass, h_new = bf16(h + relu(u)).
+__global__ void __launch_bounds__(256) update_fwd_kernel(int rows, const bf16* __restrict__ h,
+                                                         const bf16* __restrict__ a, const bf16* __restrict__ Wb,
+                                                         const float* __restrict__ bias, float* __restrict__ u,
+                                                         bf16* __restrict__ hout) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16* W = reinterpret_cast<bf16*>(smem);            // [H][LDU]
+  bf16* X = W + H * LDU;                              // [TILE][LDU]
+  const int tid = threadIdx.x;
+  for (int i = tid; i < H * KU / 8; i += blockDim.x) {
+    const int o = i / (KU / 8), k8 = i % (KU / 8);
+    *reinterpret_cast<uint4*>(W + o * LDU + k8 * 8) = *reinterpret_cast<const uint4*>(Wb + o * KU + k8 * 8);
+  }
+  const int r0 = blockIdx.x * TILE;
+  for (int i = tid; i < TILE * 16; i += blockDim.x) {
+    const int rr = i / 16, piece = i % 16, r = r0 + rr;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r < rows)
+      v = piece < 8 ? *reinterpret_cast<const uint4*>(h + (size_t)r * H + piece * 8)
+                    : *reinterpret_cast<const uint4*>(a + (size_t)r * H + (piece - 8) * 8);
+    *reinterpret_cast<uint4*>(X + rr * LDU + piece * 8) = v;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+  warp_tile_mma<KU>(X + warp * 16 * LDU, LDU, W, LDU, acc);
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int c = nt * 8 + tig * 2;
+    const float b0 = bias[c], b1 = bias[c + 1];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int r = r0 + warp * 16 + gid + half * 8;
+      if (r < rows) {
+        const float u0 = acc[nt][2 * half] + b0, u1 = acc[nt][2 * half + 1] + b1;
+        *reinterpret_cast<float2*>(u + (size_t)r * H + c) = make_float2(u0, u1);
+        const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162*>(h + (size_t)r * H + c);
+        __nv_bfloat162 o;
+        o.x = __float2bfloat16_rn(__bfloat162float(hv.x) + fmaxf(u0, 0.0f));
+        o.y = __float2bfloat16_rn(__bfloat162float(hv.y) + fmaxf(u1, 0.0f));
+        *reinterpret_cast<__nv_bfloat162*>(hout + (size_t)r * H + c) = o;
+      }
+    }
+  }
+}
+
+// out = Wd h + bd; with x0 given: x0 = phi1 + s_phi out (one sample per n rows).
+__global__ void decode_kernel(int rows, int n, const float* __restrict__ P, const bf16* __restrict__ h,
+                              float* __restrict__ out, const double* __restrict__ phi1,
+                              const double* __restrict__ scale, double* __restrict__ x0) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  float o = P[OFF_BD];
+  const bf16* hr = h + (size_t)r * H;
+#pragma unroll 8
+  for (int k = 0; k < H; ++k) o = fmaf(P[OFF_WD + k], __bfloat162float(hr[k]), o);
+  out[r] = o;
+  if (x0) x0[r] = phi1[r] + scale[r / n] * (double)o;
+}
+
+// ---------------------------------------------------------------------------
+// loss and backward (FP32, fixed-order sums)
+// ---------------------------------------------------------------------------
+__global__ void loss_kernel(int rows, const float* __restrict__ out, const float* __restrict__ target,
+                            float* __restrict__ dout, float* __restrict__ loss) {
+  __shared__ float red[32];
+  float s = 0.0f;
+  const float inv = 1.0f / rows;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    const float d = out[r] - target[r];
+    s = fmaf(d, d, s);
+    dout[r] = 2.0f * d * inv;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) *loss = t * inv;
+  }
+}
+
+// dh = dout * Wd  (gradient entering the last layer's output)
+__global__ void decode_bwd_kernel(int rows, const float* __restrict__ P, const float* __restrict__ dout,
+                                  float* __restrict__ dh) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * H) return;
+  dh[t] = dout[t / H] * P[OFF_WD + t % H];
+}
+
+// du = dh * [u > 0];  [dh_prev | da] = du Wu (Wu as its BF16 values); dh_prev += dh.
+__global__ void update_bwd_kernel(int rows, const float* __restrict__ dh, const float* __restrict__ u,
+                                  const bf16* __restrict__ Wb, float* __restrict__ du, float* __restrict__ dh_prev,
+                                  float* __restrict__ da) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* Wf = reinterpret_cast<float*>(smem);          // [H][KU]
+  for (int i = threadIdx.x; i < H * KU; i += blockDim.x) Wf[i] = __bfloat162float(Wb[i]);
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = t / KU, k = t % KU;
+  if (r >= rows) return;
+  float s = 0.0f;
+  const float* dhr = dh + (size_t)r * H;
+  const float* ur = u + (size_t)r * H;
+  for (int o = 0; o < H; ++o) {
+    const float g = ur[o] > 0.0f ? dhr[o] : 0.0f;
+    s = fmaf(g, Wf[o * KU + k], s);
+  }
+  if (k < H) {
+    dh_prev[(size_t)r * H + k] = dhr[k] + s;
+    du[(size_t)r * H + k] = ur[k] > 0.0f ? dhr[k] : 0.0f;
+  } else {
+    da[(size_t)r * H + (k - H)] = s;
+  }
+}
+
+// dz_e = da[dst] * [m_e > 0];  dx_e = dz_e Wm (first 2H inputs) for the node gathers.
+__global__ void message_bwd_kernel(int n, int E, int rows, const int* __restrict__ dst, const float* __restrict__ da,
+                                   const bf16* __restrict__ m, const bf16* __restrict__ Wb, float* __restrict__ dz,
+                                   float* __restrict__ dxe) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* Wf = reinterpret_cast<float*>(smem);          // [H][2H] (the h_i, h_j inputs)
+  for (int i = threadIdx.x; i < H * KU; i += blockDim.x) Wf[i] = __bfloat162float(Wb[(i / KU) * KMP + i % KU]);
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = t / KU, k = t % KU;
+  if (r >= rows) return;
+  const int s = r / E, e = r % E;
+  const float* dar = da + ((size_t)s * n + dst[e]) * H;
+  const bf16* mr = m + (size_t)r * H;
+  float acc = 0.0f;
+  for (int o = 0; o < H; ++o) {
+    const float g = __bfloat162float(mr[o]) > 0.0f ? dar[o] : 0.0f;
+    acc = fmaf(g, Wf[o * KU + k], acc);
+  }
+  dxe[(size_t)r * KU + k] = acc;
+  if (k < H) dz[(size_t)r * H + k] = __bfloat162float(mr[k]) > 0.0f ? dar[k] : 0.0f;
+}
+
+// dh_prev[i] += sum over in-edges of dx_e[:, 0:H] + sum over out-edges of dx_e[:, H:2H]
+__global__ void message_gather_kernel(int n, int E, int B, const int* __restrict__ in_ptr,
+                                      const int* __restrict__ out_ptr, const int* __restrict__ out_edge,
+                                      const float* __restrict__ dxe, float* __restrict__ dh_prev) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * n * H) return;
+  const int c = t % H, node = (t / H) % n, s = t / (H * n);
+  const size_t eb = (size_t)s * E;
+  float acc = dh_prev[t];
+  for (int e = in_ptr[node]; e < in_ptr[node + 1]; ++e) acc += dxe[(eb + e) * KU + c];
+  for (int q = out_ptr[node]; q < out_ptr[node + 1]; ++q) acc += dxe[(eb + out_edge[q]) * KU + H + c];
+  dh_prev[t] = acc;
+}
+
+__global__ void encode_bwd_kernel(int rows, const float* __restrict__ dh, const float* __restrict__ z0,
+                                  float* __restrict__ dz0) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * H) return;
+  dz0[t] = z0[t] > 0.0f ? dh[t] : 0.0f;
+}
+
+// Weight gradient partials: for a chunk of ROWS rows, G[o][k] = sum_r D[r][o] X[r][k]
+// and G[o][K] = sum_r D[r][o] (the bias); X rows come from `load_x`.
+constexpr int WG_ROWS = 128;
+
+template <int KX, int NO, typename LoadX>
+__device__ void wgrad_chunk(int rows, const float* __restrict__ D, LoadX load_x, float* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* Ds = reinterpret_cast<float*>(smem);          // [WG_ROWS][NO]
+  float* Xs = Ds + WG_ROWS * NO;                       // [WG_ROWS][KX + 1]
+  const int r0 = blockIdx.x * WG_ROWS;
+  for (int i = threadIdx.x; i < WG_ROWS * NO; i += blockDim.x) {
+    const int rr = i / NO, o = i % NO, r = r0 + rr;
+    Ds[i] = r < rows ? D[(size_t)r * NO + o] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < WG_ROWS * (KX + 1); i += blockDim.x) {
+    const int rr = i / (KX + 1), k = i % (KX + 1), r = r0 + rr;
+    Xs[i] = (r < rows) ? (k < KX ? load_x(r, k) : 1.0f) : 0.0f;
+  }
+  __syncthreads();
+  float* out = part + (size_t)blockIdx.x * NO * (KX + 1);
+  for (int j = threadIdx.x; j < NO * (KX + 1); j += blockDim.x) {
+    const int o = j / (KX + 1), k = j % (KX + 1);
+    float s = 0.0f;
+    for (int rr = 0; rr < WG_ROWS; ++rr) s = fmaf(Ds[rr * NO + o], Xs[rr * (KX + 1) + k], s);
+    out[j] = s;
+  }
+}
+
+__global__ void wgrad_message_kernel(int n, int E, int rows, const int* __restrict__ dst, const int* __restrict__ src,
+                                     const bf16* __restrict__ ef, const bf16* __restrict__ h,
+                                     const float* __restrict__ dz, float* __restrict__ part) {
+  wgrad_chunk<KM, H>(rows, dz,
+                     [&](int r, int k) -> float {
+                       const int s = r / E, e = r % E;
+                       if (k < H) return __bfloat162float(h[((size_t)s * n + dst[e]) * H + k]);
+                       if (k < 2 * H) return __bfloat162float(h[((size_t)s * n + src[e]) * H + k - H]);
+                       return __bfloat162float(ef[4 * (size_t)e + (k - 2 * H)]);
+                     },
+                     part);
+}
+
+__global__ void wgrad_update_kernel(int rows, const bf16* __restrict__ h, const bf16* __restrict__ a,
+                                    const float* __restrict__ du, float* __restrict__ part) {
+  wgrad_chunk<KU, H>(rows, du,
+                     [&](int r, int k) -> float {
+                       return k < H ? __bfloat162float(h[(size_t)r * H + k]) : __bfloat162float(a[(size_t)r * H + k - H]);
+                     },
+                     part);
+}
+
+__global__ void wgrad_encode_kernel(int rows, const float* __restrict__ f, const float* __restrict__ dz0,
+                                    float* __restrict__ part) {
+  wgrad_chunk<FIN, H>(rows, dz0, [&](int r, int k) -> float { return f[(size_t)r * FIN + k]; }, part);
+}
+
+__global__ void wgrad_decode_kernel(int rows, const bf16* __restrict__ h, const float* __restrict__ dout,
+                                    float* __restrict__ part) {
+  wgrad_chunk<H, 1>(rows, dout, [&](int r, int k) -> float { return __bfloat162float(h[(size_t)r * H + k]); },
+                    part);
+}
+
+// Sum the chunk partials in chunk order into the gradient vector: G[o][k] at
+// gw + o*KX + k for k < KX, the bias column at gb + o.
+__global__ void wgrad_reduce_kernel(int chunks, int NO, int KX, const float* __restrict__ part, float* __restrict__ G,
+                                    int gw, int gb) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = NO * (KX + 1);
+  if (j >= per) return;
+  float s = 0.0f;
+  for (int c = 0; c < chunks; ++c) s += part[(size_t)c * per + j];
+  const int o = j / (KX + 1), k = j % (KX + 1);
+  if (k < KX)
+    G[gw + o * KX + k] = s;
+  else
+    G[gb + o] = s;
+}
+
+// Adam on the FP32 master weights (bias-corrected moments).
+__global__ void adam_kernel(int count, float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
+                            float* __restrict__ V, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float g = G[i];
+  const float m = b1 * M[i] + (1.0f - b1) * g;
+  const float v = b2 * V[i] + (1.0f - b2) * g * g;
+  M[i] = m;
+  V[i] = v;
+  P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+// BF16 copies of the dense weights: Wm padded to KMP columns, Wu as is.
+__global__ void refresh_bf16_kernel(const float* __restrict__ P, bf16* __restrict__ Wm, bf16* __restrict__ Wu) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per_m = H * KMP, per_u = H * KU;
+  if (t < NL * per_m) {
+    const int l = t / per_m, o = (t % per_m) / KMP, k = t % KMP;
+    const float w = k < KM ? P[layer_off(l) + L_WM + o * KM + k] : 0.0f;
+    Wm[t] = __float2bfloat16_rn(w);
+  } else if (t < NL * (per_m + per_u)) {
+    const int q = t - NL * per_m, l = q / per_u, i = q % per_u;
+    Wu[q] = __float2bfloat16_rn(P[layer_off(l) + L_WU + i]);
+  }
+}
+
+}  // namespace gnn
+}  // namespace cgp
+
+using namespace cgp;
+using namespace cgp::gnn;
+
+struct cgp_gnn_s {
+  int device = 0;
+  cgp_mesh_impl* m = nullptr;
+  int n = 0, E = 0, max_batch = 0;
+  int step = 0;
+  void* base = nullptr;
+  size_t bytes = 0;
+  // graph
+  int *dst = nullptr, *src = nullptr, *in_ptr = nullptr, *out_ptr = nullptr, *out_edge = nullptr;
+  double* ell = nullptr;
+  bf16* ef = nullptr;
+  // parameters
+  float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
+  bf16 *Wm = nullptr, *Wu = nullptr;
+  // activations and gradients (max_batch samples)
+  float *f = nullptr, *z0 = nullptr, *u = nullptr, *out = nullptr, *target = nullptr, *dout = nullptr, *loss = nullptr;
+  double* scale = nullptr;
+  bf16 *h = nullptr, *msg = nullptr, *agg = nullptr;
+  float *dh = nullptr, *dh2 = nullptr, *du = nullptr, *da = nullptr, *dz = nullptr, *dxe = nullptr, *part = nullptr;
+  size_t part_floats = 0;
+};
+
+namespace {
+
+size_t al(size_t v) { return (v + 255) / 256 * 256; }
+
+int smem_optin(const void* fn, size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return e == cudaSuccess ? CGP_OK : cuda_fail(e, "cudaFuncSetAttribute(gnn)");
+}
+
+// forward for B samples stacked; x0 (nullable) receives phi1 + s_phi out
+int gnn_forward(cgp_gnn_s* g, int B, const double* b, const double* phi1, const double* phi2, const double* phi_t,
+                double* x0, cudaStream_t s) {
+  const int n = g->n, E = g->E, rn = B * n, re = B * E;
+  const double2* xy = reinterpret_cast<const double2*>(g->m->xy_c);
+  features_kernel<<<B, 256, 0, s>>>(n, b, phi1, phi2, phi_t, xy, g->f, g->scale, g->target);
+  encode_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, g->P, g->f, g->z0, g->h);
+  const size_t smem_m = (size_t)(H + TILE) * LDM * sizeof(bf16), smem_u = (size_t)(H + TILE) * LDU * sizeof(bf16);
+  for (int l = 0; l < NL; ++l) {
+    const bf16* hl = g->h + (size_t)l * rn * H;
+    bf16* ml = g->msg + (size_t)l * re * H;
+    bf16* al_ = g->agg + (size_t)l * rn * H;
+    message_fwd_kernel<<<(re + TILE - 1) / TILE, 256, smem_m, s>>>(n, E, re, g->dst, g->src, g->ef, hl,
+                                                                   g->Wm + (size_t)l * H * KMP,
+                                                                   g->P + layer_off(l) + L_BM, ml);
+    aggregate_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(n, E, B, g->in_ptr, ml, al_);
+    update_fwd_kernel<<<(rn + TILE - 1) / TILE, 256, smem_u, s>>>(rn, hl, al_, g->Wu + (size_t)l * H * KU,
+                                                                  g->P + layer_off(l) + L_BU,
+                                                                  g->u + (size_t)l * rn * H,
+                                                                  g->h + (size_t)(l + 1) * rn * H);
+  }
+  decode_kernel<<<(rn + 255) / 256, 256, 0, s>>>(rn, n, g->P, g->h + (size_t)NL * rn * H, g->out, phi1, g->scale, x0);
+  CGP_CUDA(cudaGetLastError());
+  return CGP_OK;
+}
+
+int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
+  const int n = g->n, E = g->E, rn = B * n, re = B * E;
+  loss_kernel<<<1, 1024, 0, s>>>(rn, g->out, g->target, g->dout, g->loss);
+  // decoder
+  {
+    const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
+    const size_t sm = (size_t)WG_ROWS * (1 + H + 1) * sizeof(float);
+    wgrad_decode_kernel<<<chunks, 256, sm, s>>>(rn, g->h + (size_t)NL * rn * H, g->dout, g->part);
+    wgrad_reduce_kernel<<<1, 128, 0, s>>>(chunks, 1, H, g->part, g->G, OFF_WD, OFF_BD);
+    decode_bwd_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, g->P, g->dout, g->dh);
+  }
+  float* dh = g->dh;
+  float* dh_prev = g->dh2;
+  for (int l = NL - 1; l >= 0; --l) {
+    const bf16* hl = g->h + (size_t)l * rn * H;
+    const bf16* al_ = g->agg + (size_t)l * rn * H;
+    const bf16* ml = g->msg + (size_t)l * re * H;
+    const float* ul = g->u + (size_t)l * rn * H;
+    const int off = layer_off(l);
+    // node update
+    update_bwd_kernel<<<(rn * KU + 255) / 256, 256, (size_t)H * KU * sizeof(float), s>>>(
+        rn, dh, ul, g->Wu + (size_t)l * H * KU, g->du, dh_prev, g->da);
+    {
+      const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
+      const size_t sm = (size_t)WG_ROWS * (H + KU + 1) * sizeof(float);
+      wgrad_update_kernel<<<chunks, 256, sm, s>>>(rn, hl, al_, g->du, g->part);
+      wgrad_reduce_kernel<<<(H * (KU + 1) + 255) / 256, 256, 0, s>>>(chunks, H, KU, g->part, g->G, off + L_WU,
+                                                                    off + L_BU);
+    }
+    // messages
+    message_bwd_kernel<<<(re * KU + 255) / 256, 256, (size_t)H * KU * sizeof(float), s>>>(
+        n, E, re, g->dst, g->da, ml, g->Wm + (size_t)l * H * KMP, g->dz, g->dxe);
+    {
+      const int chunks = (re + WG_ROWS - 1) / WG_ROWS;
+      const size_t sm = (size_t)WG_ROWS * (H + KM + 1) * sizeof(float);
+      wgrad_message_kernel<<<chunks, 256, sm, s>>>(n, E, re, g->dst, g->src, g->ef, hl, g->dz, g->part);
+      wgrad_reduce_kernel<<<(H * (KM + 1) + 255) / 256, 256, 0, s>>>(chunks, H, KM, g->part, g->G, off + L_WM,
+                                                                    off + L_BM);
+    }
+    message_gather_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(n, E, B, g->in_ptr, g->out_ptr, g->out_edge, g->dxe,
+                                                               dh_prev);
+    std::swap(dh, dh_prev);
+  }
+  // encoder
+  encode_bwd_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, dh, g->z0, g->du);
+  {
+    const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
+    const size_t sm = (size_t)WG_ROWS * (H + FIN + 1) * sizeof(float);
+    wgrad_encode_kernel<<<chunks, 256, sm, s>>>(rn, g->f, g->du, g->part);
+    wgrad_reduce_kernel<<<(H * (FIN + 1) + 255) / 256, 256, 0, s>>>(chunks, H, FIN, g->part, g->G, OFF_WE, OFF_BE);
+  }
+  CGP_CUDA(cudaGetLastError());
+  return CGP_OK;
+}
+
+int refresh(cgp_gnn_s* g, cudaStream_t s) {
+  const int total = NL * H * (KMP + KU);
+  refresh_bf16_kernel<<<(total + 255) / 256, 256, 0, s>>>(g->P, g->Wm, g->Wu);
+  CGP_CUDA(cudaGetLastError());
+  return CGP_OK;
+}
+
+int check_batch(cgp_gnn_s* g, int B) {
+  if (B < 1 || B > g->max_batch) return fail(CGP_ERR_INVALID_ARG, "gnn: batch outside [1, max_batch]");
+  return CGP_OK;
+}
+
+}  // namespace
+
+extern "C" int cgp_gnn_param_count(void) { return NPARAM; }
+
+extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params, cgp_gnn* out) {
+  if (!out) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_create: out is NULL");
+  *out = nullptr;
+  if (!mesh || !params || max_batch < 1) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_create: bad arguments");
+  cgp_mesh_impl* m = mesh;
+  const int n = m->n_c;
+  // directed edges i <- j in CSR order of i (diagonal excluded), and the out-edge lists
+  std::vector<int> dst, src, in_ptr(n + 1, 0), out_cnt(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    for (int k = m->h_rowptr[i]; k < m->h_rowptr[i + 1]; ++k)
+      if (m->h_col[k] != i) {
+        dst.push_back(i);
+        src.push_back(m->h_col[k]);
+      }
+    in_ptr[i + 1] = (int)dst.size();
+  }
+  const int E = (int)dst.size();
+  for (int e = 0; e < E; ++e) out_cnt[src[e] + 1]++;
+  std::vector<int> out_ptr(n + 1, 0), out_edge(E), fillp(n, 0);
+  for (int i = 0; i < n; ++i) out_ptr[i + 1] = out_ptr[i] + out_cnt[i + 1];
+  for (int e = 0; e < E; ++e) out_edge[out_ptr[src[e]] + fillp[src[e]]++] = e;   // ascending e per source
+  if ((long long)max_batch * E * KU > (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_create: batch too large");
+
+  cgp_gnn_s* g = new cgp_gnn_s();
+  g->m = m;
+  g->device = m->device;
+  g->n = n;
+  g->E = E;
+  g->max_batch = max_batch;
+  const size_t B = max_batch, rn = B * n, re = B * E;
+  const size_t chunks = (std::max(rn, re) + WG_ROWS - 1) / WG_ROWS;
+  g->part_floats = chunks * (size_t)H * (KM + 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = al(off + bytes); return o; };
+  const size_t o_dst = take(E * 4), o_src = take(E * 4), o_in = take((n + 1) * 4), o_op = take((n + 1) * 4),
+               o_oe = take(E * 4), o_ell = take(8), o_ef = take((size_t)E * 4 * 2), o_P = take(NPARAM * 4),
+               o_G = take(NPARAM * 4), o_M = take(NPARAM * 4), o_V = take(NPARAM * 4),
+               o_Wm = take((size_t)NL * H * KMP * 2), o_Wu = take((size_t)NL * H * KU * 2), o_f = take(rn * FIN * 4),
+               o_z0 = take(rn * H * 4), o_u = take((size_t)NL * rn * H * 4), o_out = take(rn * 4),
+               o_t = take(rn * 4), o_do = take(rn * 4), o_loss = take(8), o_sc = take(B * 8),
+               o_h = take((size_t)(NL + 1) * rn * H * 2), o_msg = take((size_t)NL * re * H * 2),
+               o_agg = take((size_t)NL * rn * H * 2), o_dh = take(rn * H * 4), o_dh2 = take(rn * H * 4),
+               o_du = take(rn * H * 4), o_da = take(rn * H * 4), o_dz = take(re * H * 4), o_dxe = take(re * KU * 4),
+               o_part = take(g->part_floats * 4);
+  g->bytes = off;
+  cudaError_t e = cudaMalloc(&g->base, g->bytes);
+  if (e != cudaSuccess) {
+    delete g;
+    return cuda_fail(e, "cudaMalloc(gnn)");
+  }
+  char* bs = static_cast<char*>(g->base);
+  g->dst = (int*)(bs + o_dst);
+  g->src = (int*)(bs + o_src);
+  g->in_ptr = (int*)(bs + o_in);
+  g->out_ptr = (int*)(bs + o_op);
+  g->out_edge = (int*)(bs + o_oe);
+  g->ell = (double*)(bs + o_ell);
+  g->ef = (bf16*)(bs + o_ef);
+  g->P = (float*)(bs + o_P);
+  g->G = (float*)(bs + o_G);
+  g->M = (float*)(bs + o_M);
+  g->V = (float*)(bs + o_V);
+  g->Wm = (bf16*)(bs + o_Wm);
+  g->Wu = (bf16*)(bs + o_Wu);
+  g->f = (float*)(bs + o_f);
+  g->z0 = (float*)(bs + o_z0);
+  g->u = (float*)(bs + o_u);
+  g->out = (float*)(bs + o_out);
+  g->target = (float*)(bs + o_t);
+  g->dout = (float*)(bs + o_do);
+  g->loss = (float*)(bs + o_loss);
+  g->scale = (double*)(bs + o_sc);
+  g->h = (bf16*)(bs + o_h);
+  g->msg = (bf16*)(bs + o_msg);
+  g->agg = (bf16*)(bs + o_agg);
+  g->dh = (float*)(bs + o_dh);
+  g->dh2 = (float*)(bs + o_dh2);
+  g->du = (float*)(bs + o_du);
+  g->da = (float*)(bs + o_da);
+  g->dz = (float*)(bs + o_dz);
+  g->dxe = (float*)(bs + o_dxe);
+  g->part = (float*)(bs + o_part);
+  auto up = [&](void* d, const void* h, size_t bytes) -> int {
+    cudaError_t ee = cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice);
+    return ee == cudaSuccess ? CGP_OK : cuda_fail(ee, "cudaMemcpy(gnn)");
+  };
+  int st = CGP_OK;
+  if ((st = up(g->dst, dst.data(), E * 4)) || (st = up(g->src, src.data(), E * 4)) ||
+      (st = up(g->in_ptr, in_ptr.data(), (n + 1) * 4)) || (st = up(g->out_ptr, out_ptr.data(), (n + 1) * 4)) ||
+      (st = up(g->out_edge, out_edge.data(), E * 4)) || (st = up(g->P, params, NPARAM * 4))) {
+    cgp_gnn_destroy(g);
+    return st;
+  }
+  cudaMemset(g->M, 0, NPARAM * 4);
+  cudaMemset(g->V, 0, NPARAM * 4);
+  cudaMemset(g->G, 0, NPARAM * 4);
+  const double2* xy = reinterpret_cast<const double2*>(m->xy_c);
+  edge_length_kernel<<<1, 1024>>>(E, g->dst, g->src, xy, g->ell);
+  edge_feature_kernel<<<(E + 255) / 256, 256>>>(E, g->dst, g->src, xy, g->ell, g->ef);
+  st = refresh(g, 0);
+  if (st == CGP_OK) st = smem_optin((const void*)message_fwd_kernel, (size_t)(H + TILE) * LDM * sizeof(bf16));
+  if (st == CGP_OK) st = smem_optin((const void*)update_fwd_kernel, (size_t)(H + TILE) * LDU * sizeof(bf16));
+  if (st == CGP_OK) st = smem_optin((const void*)wgrad_message_kernel, (size_t)WG_ROWS * (H + KM + 1) * sizeof(float));
+  if (st == CGP_OK) st = smem_optin((const void*)wgrad_update_kernel, (size_t)WG_ROWS * (H + KU + 1) * sizeof(float));
+  if (st == CGP_OK) st = smem_optin((const void*)update_bwd_kernel, (size_t)H * KU * sizeof(float));
+  if (st == CGP_OK) st = smem_optin((const void*)message_bwd_kernel, (size_t)H * KU * sizeof(float));
+  if (st == CGP_OK) {
+    cudaError_t ee = cudaDeviceSynchronize();
+    if (ee != cudaSuccess) st = cuda_fail(ee, "gnn set-up kernels");
+  }
+  if (st != CGP_OK) {
+    cgp_gnn_destroy(g);
+    return st;
+  }
+  *out = g;
+  return CGP_OK;
+}
+
+extern "C" int cgp_gnn_set_params(cgp_gnn g, const float* params) {
+  if (!g || !params) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_set_params: NULL argument");
+  CGP_CUDA(cudaMemcpy(g->P, params, NPARAM * 4, cudaMemcpyHostToDevice));
+  CGP_CUDA(cudaMemset(g->M, 0, NPARAM * 4));
+  CGP_CUDA(cudaMemset(g->V, 0, NPARAM * 4));
+  g->step = 0;
+  int st = refresh(g, 0);
+  if (st != CGP_OK) return st;
+  CGP_CUDA(cudaDeviceSynchronize());
+  return CGP_OK;
+}
+
+extern "C" int cgp_gnn_get_params(cgp_gnn g, float* params) {
+  if (!g || !params) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_get_params: NULL argument");
+  CGP_CUDA(cudaDeviceSynchronize());
+  CGP_CUDA(cudaMemcpy(params, g->P, NPARAM * 4, cudaMemcpyDeviceToHost));
+  return CGP_OK;
+}
+
+extern "C" int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, const double* phi2, double* x0,
+                               void* stream) {
+  if (!g || !b || !phi1 || !phi2 || !x0) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_predict: NULL argument");
+  return gnn_forward(g, 1, b, phi1, phi2, nullptr, x0, (cudaStream_t)stream);
+}
+
+extern "C" int cgp_gnn_gradients(cgp_gnn g, int batch, const double* b, const double* phi1, const double* phi2,
+                                 const double* phi_t, float* grads, float* out, float* loss, void* stream) {
+  if (!g || !b || !phi1 || !phi2 || !phi_t) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_gradients: NULL argument");
+  int st = check_batch(g, batch);
+  if (st != CGP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = gnn_forward(g, batch, b, phi1, phi2, phi_t, nullptr, s))) return st;
+  if ((st = gnn_backward(g, batch, s))) return st;
+  CGP_CUDA(cudaStreamSynchronize(s));
+  if (grads) CGP_CUDA(cudaMemcpy(grads, g->G, NPARAM * 4, cudaMemcpyDeviceToHost));
+  if (out) CGP_CUDA(cudaMemcpy(out, g->out, (size_t)batch * g->n * 4, cudaMemcpyDeviceToHost));
+  if (loss) CGP_CUDA(cudaMemcpy(loss, g->loss, 4, cudaMemcpyDeviceToHost));
+  return CGP_OK;
+}
+
+extern "C" int cgp_gnn_train_step(cgp_gnn g, int batch, const double* b, const double* phi1, const double* phi2,
+                                  const double* phi_t, float lr, float* loss_dev, void* stream) {
+  if (!g || !b || !phi1 || !phi2 || !phi_t) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_train_step: NULL argument");
+  if (!(lr > 0.0f)) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_train_step: lr must be positive");
+  int st = check_batch(g, batch);
+  if (st != CGP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = gnn_forward(g, batch, b, phi1, phi2, phi_t, nullptr, s))) return st;
+  if ((st = gnn_backward(g, batch, s))) return st;
+  g->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - std::pow(b1, (float)g->step), c2 = 1.0f - std::pow(b2, (float)g->step);
+  adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(NPARAM, g->P, g->G, g->M, g->V, lr, b1, b2, 1e-8f, c1, c2);
+  if ((st = refresh(g, s))) return st;
+  if (loss_dev) CGP_CUDA(cudaMemcpyAsync(loss_dev, g->loss, 4, cudaMemcpyDeviceToDevice, s));
+  CGP_CUDA(cudaGetLastError());
+  return CGP_OK;
+}
+
+extern "C" int cgp_gnn_destroy(cgp_gnn g) {
+  if (!g) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_destroy: NULL");
+  cudaDeviceSynchronize();
+  if (g->base) cudaFree(g->base);
+  delete g;
+  return CGP_OK;
+}
