@@ -211,14 +211,14 @@ def run_mine(args, rank, world, local_rank):
 
     solve_events = []
 
-    def step(uf, vf, warm, slot, timing=False):
+    def step(uf, vf, warm, slot, timing=False, tol=TOL):
         prec = precision
         cgp.cgp_restrict(mesh.handle, cgp.CGP_RHS_POTENTIAL, B_FIELD, RHO_OVER_DT, uf, vf, b)
         e0 = torch.cuda.Event(enable_timing=True) if timing else None
         e1 = torch.cuda.Event(enable_timing=True) if timing else None
         if timing:
             e0.record(stream)
-        cgp.cgp_poisson_solve_async(mesh.handle, b, phi_c, tol=TOL, use_x0=warm, precision=prec,
+        cgp.cgp_poisson_solve_async(mesh.handle, b, phi_c, tol=tol, use_x0=warm, precision=prec,
                                     info_dev=info_addr(slot))
         if timing:
             e1.record(stream)
@@ -230,7 +230,7 @@ def run_mine(args, rank, world, local_rank):
         e3 = torch.cuda.Event(enable_timing=True) if timing else None
         if timing:
             e2.record(stream)
-        cgp.cgp_poisson_solve_async(mesh.handle, b, p_c, tol=TOL, use_x0=warm, precision=prec,
+        cgp.cgp_poisson_solve_async(mesh.handle, b, p_c, tol=tol, use_x0=warm, precision=prec,
                                     info_dev=info_addr(slot + 1))
         if timing:
             e3.record(stream)
@@ -306,16 +306,25 @@ def run_mine(args, rank, world, local_rank):
     if not args.no_variants:
         phi_c.copy_(phi_keep)
         p_c.copy_(p_keep)
-        main_fields = []
-        # reference fields of the main precision for the first timed step
+        # fields of the first timed step: a tightly converged FP64 reference (tol 1e-13) and the main precision
+        saved_prec = precision
+        precision = cgp.CGP_FP64
+        phi_c.copy_(phi_keep)
+        p_c.copy_(p_keep)
+        step(Ud[W, 0], Ud[W, 1], W > 0, 2 * W, tol=1e-13)
+        torch.cuda.synchronize()
+        tight = [phi_f.clone(), force.clone(), grad_p.clone()]
+        precision = saved_prec
         phi_c.copy_(phi_keep)
         p_c.copy_(p_keep)
         step(Ud[W, 0], Ud[W, 1], W > 0, 2 * W)
         torch.cuda.synchronize()
         main_fields = [phi_f.clone(), force.clone(), grad_p.clone()]
+        rel = lambda a, r: float(torch.linalg.norm(a - r) / torch.linalg.norm(r))  # noqa: E731
+        err_main = {"phi_f": rel(main_fields[0], tight[0]), "force": rel(main_fields[1], tight[1]),
+                    "grad_p": rel(main_fields[2], tight[2])}
         phi_c.copy_(phi_keep)
         p_c.copy_(p_keep)
-        saved_prec = precision
         precision = other
         alt_events = []
         for j in range(K):
@@ -329,9 +338,11 @@ def run_mine(args, rank, world, local_rank):
             alt_events.append((e0, e1))
             if j == 0:
                 torch.cuda.synchronize()
-                rel = lambda a, r: float(torch.linalg.norm(a - r) / torch.linalg.norm(r))  # noqa: E731
                 alt["rel_err_vs_main"] = {"phi_f": rel(phi_f, main_fields[0]), "force": rel(force, main_fields[1]),
                                           "grad_p": rel(grad_p, main_fields[2])}
+                alt["rel_err_vs_tight_fp64"] = {"phi_f": rel(phi_f, tight[0]), "force": rel(force, tight[1]),
+                                                "grad_p": rel(grad_p, tight[2])}
+                alt["main_rel_err_vs_tight_fp64"] = err_main
         torch.cuda.synchronize()
         alt_ms = sum(a.elapsed_time(c) for a, c in alt_events)
         alt_recs = cgp.decode_infos(bytes(infos.cpu().numpy()), n_info)[2 * W: 2 * total_steps]
@@ -366,6 +377,7 @@ def run_mine(args, rank, world, local_rank):
     if rank == 0 and not args.no_variants:
         from paper_2003_00082_gb300 import configs
         result["batched"] = run_batched(cgp, inputs, configs, torch, dev, flush, peak)
+        result["learned_guess"] = run_learned_guess(cgp, inputs, torch)
     mesh.close()
     return result
 
@@ -430,6 +442,20 @@ def run_batched(cgp, inputs, configs, torch, dev, flush, peak, reps=5):
     for m in meshes:
         m.close()
     return out
+
+
+def run_learned_guess(cgp, inputs, torch):
+    """Learned initial guess on the 64x32 mesh: train on 4 N x 5 seeds x 200 steps, test N = 3 on seeds 100-104."""
+    from paper_2003_00082_gb300 import learned_guess as LG
+    xy, tri = inputs.ogrid(64, 32)
+    m = cgp.Mesh(xy, tri)
+    xy_f, _, _ = m.fine_geometry()
+    net, ev = LG.run_protocol(torch, m, xy_f)
+    net.close()
+    m.close()
+    ev["workload"] = ("64x32 O-grid potential solves, vortex train + noise 1e-3, tol 1e-8; train N in {0.5,1,2,5} "
+                      "x seeds 0-4 x 200 steps, test N = 3 seeds 100-104 x 200 steps")
+    return ev
 
 
 def spmv_bench(cgp, inputs, torch, dev, flush, peak, reps=15):
@@ -544,6 +570,43 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------------------
+def profile_case(case):
+    """A short run for a profiler: the kernels of one case, no timing."""
+    import torch
+
+    from paper_2003_00082_gb300 import build, cgp, configs, inputs
+
+    build.build()
+    cgp.load()
+    dev = torch.device("cuda:0")
+    if case in ("fp64", "mixed"):
+        xy, tri = inputs.ogrid(N_THETA, N_R)
+        m = cgp.Mesh(xy, tri)
+        xy_f, _, _ = m.fine_geometry()
+        u, v = inputs.velocity(xy_f, 7, SEED, vortices=True)
+        b = torch.empty(m.n_c, dtype=torch.float64, device=dev)
+        cgp.cgp_restrict(m.handle, cgp.CGP_RHS_POTENTIAL, B_FIELD, RHO_OVER_DT, torch.as_tensor(u, device=dev),
+                         torch.as_tensor(v, device=dev), b)
+        x = torch.zeros(m.n_c, dtype=torch.float64, device=dev)
+        prec = cgp.CGP_MIXED if case == "mixed" else cgp.CGP_FP64
+        what = cgp.CGP_TUNE_SOLVE_MIXED if case == "mixed" else cgp.CGP_TUNE_SOLVE_FP64
+        cgp.cgp_set_tuning(m.handle, what, 512, 1, 304, 0)    # the shape the autotuner picks on GB300
+        for _ in range(2):
+            x.zero_()
+            info = cgp.cgp_poisson_solve(m.handle, b, x, tol=TOL, precision=prec)
+        print(json.dumps({"case": case, "info": info, "launch": cgp.cgp_last_launch(m.handle, prec)}))
+        m.close()
+    elif case == "batched":
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        out = run_batched(cgp, inputs, configs, torch, dev, flush, read_peaks()[0], reps=1)
+        print(json.dumps({"case": case, "value": out["value"], "launch": out["launch"]}))
+    else:
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        out = spmv_bench(cgp, inputs, torch, dev, flush, read_peaks()[0], reps=2)
+        print(json.dumps({"case": case, "fp64_gb_s": out["fp64"]["gb_s"], "fp32_gb_s": out["fp32"]["gb_s"]}))
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -555,10 +618,16 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the other-precision and batched passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "batched", "spmv"], default=None,
+                    help="run one small case for a profiler and exit: two 512x256 potential solves, "
+                         "one batched launch of the 64-instance workload, or the SpMV sweep")
     args = ap.parse_args()
 
     if args.oracle_sample:
         print(json.dumps(oracle_sample()), flush=True)
+        return
+    if args.profile_case:
+        profile_case(args.profile_case)
         return
 
     rank = int(os.environ.get("RANK", "0"))
@@ -622,6 +691,8 @@ def main():
             line["other_precision"] = res["variant"]
         if "batched" in res:
             line["batched"] = res["batched"]
+        if "learned_guess" in res:
+            line["learned_guess"] = res["learned_guess"]
         line["tuned_launch"] = res["tuned"]
         print(json.dumps(line), flush=True)
     if world > 1:

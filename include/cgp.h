@@ -248,14 +248,15 @@ int cgp_poisson_solve_batched(const cgp_mesh* meshes, int count, const double* c
  * The paper has no learned component; this is the spec addition (4)
  * that predicts the PCG starting point of the potential solve (Eq. 12) from
  * the right-hand side b and the two previous solutions.  Per coarse node i,
- * f_i = [b/s_b, phi1/s_phi, phi2/s_phi, x/15, y/15] (s = rms over nodes);
+ * f_i = [r/s_r, (phi1 - phi2)/s_d, b/s_b, x/15, y/15] with r = b - K phi1
+ * (s = rms over nodes, each input scaled by its own size);
  * h0 = relu(We f + be); three layers of m_ij = relu(Wm [h_i; h_j; e_ij] + bm)
  * over the directed mesh edges i <- j (e_ij = (dx, dy, |d|) / mean edge
  * length), a_i = sum_j m_ij, h_i += relu(Wu [h_i; a_i] + bu); out = Wd h + bd;
- * x0 = phi1 + s_phi * out (the solver projects x0 to mean zero).  Hidden width
+ * x0 = phi1 + s_d * out (the solver projects x0 to mean zero).  Hidden width
  * 64; the dense layers run on the tensor cores in BF16 with FP32
  * accumulation; weights are kept in FP32 for Adam (lr given per step, betas
- * 0.9 / 0.999, eps 1e-8).  The training target is (phi(t) - phi1) / s_phi
+ * 0.9 / 0.999, eps 1e-8).  The training target is (phi(t) - phi1) / s_d
  * and the loss the mean squared error over all nodes of the batch.
  *
  * Parameters are one FP32 vector of cgp_gnn_param_count() values in this

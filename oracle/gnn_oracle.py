@@ -6,10 +6,13 @@ The network predicts the PCG initial guess of the potential solve from the
 right-hand side and the two previous solutions (the learned-guess addition
 on top of the method of Sect. 2.2).  Per coarse node i the inputs are
 
-    f_i = [b_i / s_b, phi1_i / s_phi, phi2_i / s_phi, x_i / L, y_i / L]
+    f_i = [r_i / s_r, (phi1 - phi2)_i / s_d, b_i / s_b, x_i / L, y_i / L]
 
-with s_b = rms(b), s_phi = rms(phi(t-1)) (tiny values floored), L = 15 the
-outer radius.  For every directed mesh edge (i <- j) the edge feature is
+with r = b - K phi(t-1) the residual of the previous solution for the new
+right-hand side (K dphi = r drives the increment), s_r, s_d, s_b the rms
+values over the nodes (floored), L = 15 the outer radius.  Each input is
+scaled by its own size because BF16 activations (8-bit mantissa) cannot
+resolve phi(t-1) against phi(t-2) when both are scaled by rms(phi).  For every directed mesh edge (i <- j) the edge feature is
 e_ij = (dx, dy, |d|) / ell, d = x_j - x_i, ell the mean edge length.
 
     h0   = relu(We f + be)                                   (encoder, FP32)
@@ -18,9 +21,11 @@ e_ij = (dx, dy, |d|) / ell, d = x_j - x_i, ell the mean edge length.
       a_i  = sum_{j in N(i)} m_ij
       h_i  = h_i + relu(Wu_l [h_i ; a_i] + bu_l)
     out_i = Wd h_i + bd
-    x0    = phi1 + s_phi * out                               (then projected to mean zero)
+    x0    = phi1 + s_d * out                                 (then projected to mean zero)
 
-Training target: t_i = (phi(t)_i - phi(t-1)_i) / s_phi, loss = mean (out - t)^2.
+Training target: t_i = (phi(t)_i - phi(t-1)_i) / s_d, loss = mean (out - t)^2:
+the network predicts the next increment in units of the last one (linear
+extrapolation is out = (phi1 - phi2) / s_d, a zero decoder gives phi1).
 Activations h, messages m, aggregates a and the dense weights Wm, Wu are
 stored in BF16 (round to nearest even) where the GPU stores them; every sum
 is exact FP64 here.  ``bf16=False`` gives the plain FP64 network used for
@@ -107,11 +112,15 @@ def floor_scale(s):
     return s if s > 1e-30 else 1.0
 
 
-def features(g: Graph, b, phi1, phi2):
+def features(g: Graph, K, b, phi1, phi2):
+    """Input features and the output scale s_d = rms(phi1 - phi2)."""
+    r = b - K @ phi1
+    d = phi1 - phi2
+    s_r = floor_scale(rms(r))
+    s_d = floor_scale(rms(d))
     s_b = floor_scale(rms(b))
-    s_p = floor_scale(rms(phi1))
-    f = np.stack([b / s_b, phi1 / s_p, phi2 / s_p, g.xy[:, 0] / R_OUT, g.xy[:, 1] / R_OUT], axis=1)
-    return f, s_p
+    f = np.stack([r / s_r, d / s_d, b / s_b, g.xy[:, 0] / R_OUT, g.xy[:, 1] / R_OUT], axis=1)
+    return f, s_d
 
 
 def forward(p, g: Graph, f, bf16_storage=True):
@@ -199,9 +208,9 @@ class Adam:
             p[k] = p[k] - self.lr * mh / (np.sqrt(vh) + self.eps)
 
 
-def guess(p, g: Graph, b, phi1, phi2, bf16_storage=True):
-    """Initial guess phi1 + s_phi * out, projected to mean zero."""
-    f, s_p = features(g, b, phi1, phi2)
+def guess(p, g: Graph, K, b, phi1, phi2, bf16_storage=True):
+    """Initial guess phi1 + s_d * out, projected to mean zero."""
+    f, s_d = features(g, K, b, phi1, phi2)
     out, _ = forward(p, g, f, bf16_storage)
-    x0 = phi1 + s_p * out
+    x0 = phi1 + s_d * out
     return x0 - x0.mean()

@@ -1,12 +1,12 @@
 // Learned PCG initial guess: a message-passing network on the coarse mesh's
 // edges (hidden width 64, three layers), with its training step.
 //
-//   f_i  = [b/s_b, phi1/s_phi, phi2/s_phi, x/15, y/15]          s = rms over nodes
+//   f_i  = [r/s_r, (phi1-phi2)/s_d, b/s_b, x/15, y/15]      r = b - K phi1, s = rms over nodes
 //   h0   = relu(We f + be)
 //   m_ij = relu(Wm_l [h_i ; h_j ; e_ij] + bm_l)     (directed edge i <- j, e_ij = (dx, dy, |d|)/ell)
 //   a_i  = sum_j m_ij
 //   h_i  = h_i + relu(Wu_l [h_i ; a_i] + bu_l)
-//   out  = Wd h + bd,   x0 = phi1 + s_phi out       (the solver projects x0 to mean zero)
+//   out  = Wd h + bd,   x0 = phi1 + s_d out         (the solver projects x0 to mean zero)
 //
 // The two dense layers of every message-passing step run on the tensor
 // cores as BF16 x BF16 -> FP32 mma.sync tiles (16 rows x 64 outputs per
@@ -117,55 +117,63 @@ __global__ void edge_feature_kernel(int E, const int* __restrict__ dst, const in
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-// One block per sample: scales, input features and (when phi_t is given) targets.
-__global__ void features_kernel(int n, const double* __restrict__ b, const double* __restrict__ phi1,
-                                const double* __restrict__ phi2, const double* __restrict__ phi_t,
-                                const double2* __restrict__ xy, float* __restrict__ f, double* __restrict__ scale,
-                                float* __restrict__ target) {
-  __shared__ double red[2][32];
-  __shared__ double sc[2];
+// One block per sample: residual r = b - K phi1, scales, input features and
+// (when phi_t is given) targets.  Each input is scaled by its own rms so the
+// BF16 activations resolve it (phi1 and phi2 differ by far less than their size).
+__device__ __forceinline__ double residual_row(int i, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                               const double* __restrict__ K, const double* __restrict__ b,
+                                               const double* __restrict__ phi1) {
+  double s = 0.0;
+  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s = fma(K[k], phi1[col[k]], s);
+  return b[i] - s;
+}
+
+__global__ void features_kernel(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                const double* __restrict__ K, const double* __restrict__ b,
+                                const double* __restrict__ phi1, const double* __restrict__ phi2,
+                                const double* __restrict__ phi_t, const double2* __restrict__ xy,
+                                float* __restrict__ f, double* __restrict__ scale, float* __restrict__ target) {
+  __shared__ double red[3][32];
+  __shared__ double sc[3];
   const int s = blockIdx.x;
   const size_t base = (size_t)s * n;
-  double sb = 0.0, sp = 0.0;
+  const double* bs = b + base;
+  const double* p1 = phi1 + base;
+  double v[3] = {0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double bi = b[base + i], pi = phi1[base + i];
-    sb += bi * bi;
-    sp += pi * pi;
+    const double r = residual_row(i, rowptr, col, K, bs, p1);
+    const double dd = p1[i] - phi2[base + i];
+    v[0] = fma(r, r, v[0]);
+    v[1] = fma(dd, dd, v[1]);
+    v[2] = fma(bs[i], bs[i], v[2]);
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    sb += __shfl_xor_sync(0xffffffffu, sb, o);
-    sp += __shfl_xor_sync(0xffffffffu, sp, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = sb;
-    red[1][threadIdx.x >> 5] = sp;
+  for (int c = 0; c < 3; ++c) {
+    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+    if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v[c];
   }
   __syncthreads();
   if (threadIdx.x < 32) {
-    double tb = threadIdx.x < (blockDim.x >> 5) ? red[0][threadIdx.x] : 0.0;
-    double tp = threadIdx.x < (blockDim.x >> 5) ? red[1][threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      tb += __shfl_xor_sync(0xffffffffu, tb, o);
-      tp += __shfl_xor_sync(0xffffffffu, tp, o);
+    for (int c = 0; c < 3; ++c) {
+      double t = threadIdx.x < (blockDim.x >> 5) ? red[c][threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (threadIdx.x == 0) {
+        const double rr = sqrt(t / n);
+        sc[c] = rr > 1e-30 ? rr : 1.0;
+      }
     }
-    if (threadIdx.x == 0) {
-      double rb = sqrt(tb / n), rp = sqrt(tp / n);
-      sc[0] = rb > 1e-30 ? rb : 1.0;
-      sc[1] = rp > 1e-30 ? rp : 1.0;
-      scale[s] = sc[1];
-    }
+    if (threadIdx.x == 0) scale[s] = sc[1];
   }
   __syncthreads();
-  const double ib = 1.0 / sc[0], ip = 1.0 / sc[1];
+  const double ir = 1.0 / sc[0], id = 1.0 / sc[1], ib = 1.0 / sc[2];
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double2 p = xy[i];
     float* fi = f + (base + i) * FIN;
-    fi[0] = (float)(b[base + i] * ib);
-    fi[1] = (float)(phi1[base + i] * ip);
-    fi[2] = (float)(phi2[base + i] * ip);
+    fi[0] = (float)(residual_row(i, rowptr, col, K, bs, p1) * ir);
+    fi[1] = (float)((p1[i] - phi2[base + i]) * id);
+    fi[2] = (float)(bs[i] * ib);
     fi[3] = (float)(p.x / 15.0);
     fi[4] = (float)(p.y / 15.0);
-    if (phi_t) target[base + i] = (float)((phi_t[base + i] - phi1[base + i]) * ip);
+    if (phi_t) target[base + i] = (float)((phi_t[base + i] - p1[i]) * id);
   }
 }
 
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(256) update_fwd_kernel(int rows, const bf16* _
   }
 }
 
-// out = Wd h + bd; with x0 given: x0 = phi1 + s_phi out (one sample per n rows).
+// out = Wd h + bd; with x0 given: x0 = phi1 + s_d out (one sample per n rows).
 __global__ void decode_kernel(int rows, int n, const float* __restrict__ P, const bf16* __restrict__ h,
                               float* __restrict__ out, const double* __restrict__ phi1,
                               const double* __restrict__ scale, double* __restrict__ x0) {
@@ -554,12 +562,13 @@ int smem_optin(const void* fn, size_t bytes) {
   return e == cudaSuccess ? CGP_OK : cuda_fail(e, "cudaFuncSetAttribute(gnn)");
 }
 
-// forward for B samples stacked; x0 (nullable) receives phi1 + s_phi out
+// forward for B samples stacked; x0 (nullable) receives phi1 + s_d out
 int gnn_forward(cgp_gnn_s* g, int B, const double* b, const double* phi1, const double* phi2, const double* phi_t,
                 double* x0, cudaStream_t s) {
   const int n = g->n, E = g->E, rn = B * n, re = B * E;
   const double2* xy = reinterpret_cast<const double2*>(g->m->xy_c);
-  features_kernel<<<B, 256, 0, s>>>(n, b, phi1, phi2, phi_t, xy, g->f, g->scale, g->target);
+  features_kernel<<<B, 256, 0, s>>>(n, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, phi_t, xy, g->f, g->scale,
+                                   g->target);
   encode_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, g->P, g->f, g->z0, g->h);
   const size_t smem_m = (size_t)(H + TILE) * LDM * sizeof(bf16), smem_u = (size_t)(H + TILE) * LDU * sizeof(bf16);
   for (int l = 0; l < NL; ++l) {

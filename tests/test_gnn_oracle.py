@@ -18,7 +18,7 @@ def tiny():
         b = rng.standard_normal(om.n_c)
         phi1 = rng.standard_normal(om.n_c)
         phi2 = rng.standard_normal(om.n_c)
-        f, s_p = G.features(g, b, phi1, phi2)
+        f, s_p = G.features(g, om.K, b, phi1, phi2)
         samples.append((f, rng.standard_normal(om.n_c) * 0.1))
     return om, g, samples
 
@@ -45,7 +45,7 @@ def test_zero_decoder_returns_previous_solution(tiny):
     p = G.init_params(3, zero_decoder=True)
     rng = np.random.default_rng(2)
     b, phi1, phi2 = rng.standard_normal((3, om.n_c))
-    x0 = G.guess(p, g, b, phi1, phi2)
+    x0 = G.guess(p, g, om.K, b, phi1, phi2)
     np.testing.assert_allclose(x0, phi1 - phi1.mean(), atol=1e-14)
 
 
@@ -111,6 +111,18 @@ def test_node_relabelling_permutes_the_output(tiny):
     gp = G.Graph(Kp, om.xy_c[perm])
     outp, _ = G.forward(p, gp, f[perm], bf16_storage=False)
     np.testing.assert_allclose(outp, out[perm], rtol=1e-12, atol=1e-12)
+
+
+def test_features_make_linear_extrapolation_learnable(tiny):
+    """Feature 1 is the last increment in units of s_d: out = f[:, 1] reproduces phi1 + (phi1 - phi2)."""
+    om, g, _ = tiny
+    rng = np.random.default_rng(9)
+    b, phi1, phi2 = rng.standard_normal((3, om.n_c))
+    f, s_d = G.features(g, om.K, b, phi1, phi2)
+    np.testing.assert_allclose(phi1 + s_d * f[:, 1], 2 * phi1 - phi2, atol=1e-12)
+    # feature 0 is the residual of phi1 for b, in its own units
+    r = b - om.K @ phi1
+    np.testing.assert_allclose(f[:, 0] * np.sqrt(np.mean(r ** 2)), r, atol=1e-12)
 
 
 def test_adam_first_step_is_lr_times_sign():

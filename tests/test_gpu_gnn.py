@@ -75,7 +75,7 @@ def test_forward_and_gradients_match_the_oracle(cgp, setting):
     grads, out, loss = net.gradients(B, stacked(data, 0), stacked(data, 1), stacked(data, 2), stacked(data, 3))
     samples = []
     for s, (b, phi1, phi2, phit) in enumerate(data):
-        f, s_p = G.features(g, b, phi1, phi2)
+        f, s_p = G.features(g, om.K, b, phi1, phi2)
         ref_out, _ = G.forward(p, g, f, bf16_storage=True)
         assert np.linalg.norm(out[s] - ref_out) <= 2e-2 * np.linalg.norm(ref_out)
         samples.append((f, (phit - phi1) / s_p))
