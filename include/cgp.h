@@ -66,7 +66,7 @@ typedef struct {
 
 typedef struct {
   int iterations;            /* PCG iterations (MIXED: inner iterations summed) */
-  int outer_sweeps;          /* MIXED: refinement sweeps; FP64: 0 */
+  int outer_sweeps;          /* MIXED: refinement sweeps; FP64: restarts from the true residual (normally 0) */
   double rel_res_recursive;  /* FP64: recursive-residual norm / ||b||; MIXED: as rel_res_true */
   double rel_res_true;       /* ||b - K x|| / ||b|| of the returned x */
   int status;                /* cgp_status of the solve */
@@ -142,7 +142,12 @@ int cgp_restrict(cgp_mesh m, int kind, const double* B, double rho_over_dt,
  *
  * b and x0 are projected to mean zero (the null space of K is the
  * constants), CG runs on the projected system, and the result is projected
- * again.  FP64 runs plain PCG in FP64.  MIXED runs FP64 iterative refinement
+ * again.  FP64 runs PCG in FP64, by default in the single-reduction form of
+ * Chronopoulos and Gear (one grid barrier per iteration; the recurrences
+ * for K p and the residual are checked against the true residual when the
+ * recursive one converges, and CG restarts from the true residual if it
+ * does not meet tol); tuning flag bit 1 selects the textbook iteration
+ * (Saad, Alg. 9.1) with two barriers.  MIXED runs FP64 iterative refinement
  * (residual b - K x, correction sum and projection in FP64) around FP32 inner
  * PCG solves to inner_tol.  The whole solve is one persistent cooperative
  * kernel launch; its grid barriers give up after about two seconds without
@@ -219,7 +224,8 @@ int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* col, const do
  *                     first non-OK status among the systems.
  * cgp_batch_set_tuning  re-plans with threads per block, lanes per CSR row,
  *                     blocks per SM (0 = as many as fit) and flags (bit 0:
- *                     rows in global memory).
+ *                     rows in global memory; bit 1: FP64 textbook iteration,
+ *                     as for cgp_set_tuning).
  * cgp_batch_autotune  times a set of launch shapes on the batch's own
  *                     systems (from x = 0) and keeps the fastest; writes the
  *                     best time in ms to best_ms (nullable).  Synchronous;
@@ -333,7 +339,8 @@ int cgp_spmv(cgp_mesh m, int precision, const void* x, void* y, void* stream);
  * blocks  solver: blocks of the persistent grid (clamped to what can be
  *         co-resident); SpMV: grid size; 0 = chosen from the size.
  * flags   solver: bit 0 keeps each block's rows in global memory instead of
- *         shared memory; other bits must be 0.
+ *         shared memory; bit 1 (FP64 only) runs the textbook two-barrier CG
+ *         iteration instead of the single-reduction form; other bits must be 0.
  * Invalid shapes are rejected with INVALID_ARG.  cgp_autotune sets these.
  */
 typedef enum {
@@ -352,8 +359,10 @@ int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks, in
  * Runs the solve (precision CGP_FP64 or CGP_MIXED, tol 1e-8, from x = 0) on
  * the caller's right-hand side b (device [n_c]) for every candidate of
  * threads per block {256, 512}, lanes per CSR row {1, 2, 4}, grid size (a
- * few counts around the SM count, and 1..16 blocks for small systems) and
- * shared-memory residency, and keeps the fastest with cgp_set_tuning.  x
+ * few counts around the SM count, and 1..16 blocks for small systems),
+ * shared-memory residency and, for FP64, the iteration form (flag bit 1),
+ * and keeps the fastest with cgp_set_tuning.  Every candidate meets the
+ * same tolerance on the true residual.  x
  * (device [n_c]) is overwritten.  cache_path (nullable) names a text file of
  * earlier results keyed by GPU name, n, nnz and target: a hit applies the
  * cached shape without timing (best_ms = -1), a miss appends the new

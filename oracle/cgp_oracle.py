@@ -315,8 +315,8 @@ def lorentz(xy_f, tri_f, phi_f, u_f, v_f, B, sigma):
 # ----------------------------------------------------------------------------
 # FP32-inner / FP64-outer iterative refinement
 # ----------------------------------------------------------------------------
-def pcg32(K32, d32, r32, tol, max_it):
-    """Jacobi PCG in float32 arithmetic from zero, stopping at ||r|| <= tol ||r0||."""
+def pcg32(K32, d32, r32, tol, max_it, floor=0.0):
+    """Jacobi PCG in float32 arithmetic from zero, stopping at ||r|| <= max(tol ||r0||, floor)."""
     n = r32.shape[0]
     x = np.zeros(n, dtype=np.float32)
     r = r32.astype(np.float32).copy()
@@ -328,7 +328,7 @@ def pcg32(K32, d32, r32, tol, max_it):
     rz = np.float32(np.dot(r, z))
     k = 0
     while k < max_it:
-        if math.sqrt(float(np.dot(r, r))) <= tol * r0:
+        if math.sqrt(float(np.dot(r, r))) <= max(tol * r0, floor):
             break
         if k > 0:
             rz_new = np.float32(np.dot(r, z))
@@ -348,7 +348,13 @@ def pcg32(K32, d32, r32, tol, max_it):
 
 
 def mixed_ir(K, d, b, x0=None, tol=1e-8, inner_tol=1e-4, max_sweeps=50, inner_max_it=20000):
-    """Iterative refinement: FP64 residual, correction sum and projection; FP32 inner PCG."""
+    """Iterative refinement: FP64 residual, correction sum and projection; FP32 inner PCG.
+
+    The inner solve of K e = r stops at the relative reduction inner_tol, or
+    as soon as its residual (the outer residual after the correction, up to
+    FP32 rounding) is below half the outer target tol ||b||: solving further
+    would only be thrown away by the next outer test.
+    """
     bp = project_mean(b)
     n = bp.shape[0]
     bnorm = math.sqrt(float(np.dot(bp, bp)))
@@ -370,7 +376,7 @@ def mixed_ir(K, d, b, x0=None, tol=1e-8, inner_tol=1e-4, max_sweeps=50, inner_ma
             break
         if sweeps >= max_sweeps:
             break
-        dx, its = pcg32(K32, d32, r.astype(np.float32), inner_tol, inner_max_it)
+        dx, its = pcg32(K32, d32, r.astype(np.float32), inner_tol, inner_max_it, floor=0.5 * tol * bnorm)
         total += its
         x = project_mean(x + dx.astype(np.float64))
         sweeps += 1

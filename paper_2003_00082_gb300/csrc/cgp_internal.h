@@ -100,6 +100,7 @@ struct cgp_mesh_impl {
   double* p = nullptr;
   double* p2 = nullptr;
   double* q = nullptr;
+  double* pub64 = nullptr;   // [6 n] single-reduction FP64: published R[2], W[2], S[2]
   float* f32pub = nullptr;   // [6 n] mixed: published R[2], W[2], S[2]
   float* f32own = nullptr;   // [6 n] mixed without shared-memory residency: own inner vectors
   float* fpart = nullptr;    // [8 * max_blocks] FP32 partial sums

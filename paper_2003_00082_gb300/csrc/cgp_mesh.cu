@@ -224,7 +224,7 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
          o_edges = take(2 * (size_t)m->n_e * 4), o_xyf = take(2 * (size_t)m->n_f * 8),
          o_xyc = take(2 * n * 8), o_incp = take((n + 1) * 4), o_inc = take(3 * (size_t)t_c * 4),
          o_bp = take(n * 8), o_r = take(n * 8), o_z = take(n * 8), o_p = take(n * 8), o_p2 = take(n * 8), o_q = take(n * 8),
-         o_f32pub = take(6 * n * 4), o_f32own = take(6 * n * 4),
+         o_pub64 = take(6 * n * 8), o_f32pub = take(6 * n * 4), o_f32own = take(6 * n * 4),
          o_fpart = take((size_t)m->max_blocks * 8 * 4), o_part = take((size_t)m->max_blocks * 32 * 8), o_bar = take(256),
          o_res = take(sizeof(SolveResult));
   m->d_bytes = off;
@@ -252,6 +252,7 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
   m->p = (double*)(base + o_p);
   m->p2 = (double*)(base + o_p2);
   m->q = (double*)(base + o_q);
+  m->pub64 = (double*)(base + o_pub64);
   m->f32pub = (float*)(base + o_f32pub);
   m->f32own = (float*)(base + o_f32own);
   m->fpart = (float*)(base + o_fpart);

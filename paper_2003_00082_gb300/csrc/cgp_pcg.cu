@@ -60,6 +60,7 @@ struct Desc {
   double* p;
   double* p2;         // second buffer of p (FP64 solver)
   double* q;
+  double* pub64;      // FP64 single-reduction: published R[2], W[2], S[2] ([6][n])
   float* f32pub;      // mixed: published R[2], W[2], S[2] ([6][n])
   float* f32own;      // mixed without RES: own r, u, w, p, s, e ([6][n])
   float* fpart;       // mixed: FP32 partial slots [2][NCOMP][part_stride]
@@ -71,6 +72,7 @@ struct Desc {
   int blk0, nblk;
   double tol, inner_tol;
   int max_it, max_sweeps, use_x0, mixed;
+  int classic;        // FP64: two barriers per iteration (Saad, Alg. 9.1) instead of the single-reduction form
   int res_nnz_cap;    // RES: capacity of the shared-memory CSR slice
   int halo_cap;       // RES: capacity of the halo gather buffer
   const int* lcol;    // RES: columns renumbered per block (halo plan)
@@ -99,9 +101,9 @@ __device__ __forceinline__ V warp_sum(V v) {
 }
 
 struct Shared {
-  unsigned long long wlo[2][32];  // per-warp fixed-point partials of one reduction
-  long long whi[2][32];
-  int wexp[2][32];
+  unsigned long long wlo[3][32];  // per-warp fixed-point partials of one reduction
+  long long whi[3][32];
+  int wexp[3][32];
   double tot[NCOMP];
   double sc[8];                 // scalars computed by one lane and broadcast
   int isc[4];
@@ -190,13 +192,14 @@ __device__ __forceinline__ unsigned long long* part_slot(const Desc& d, int red,
   return reinterpret_cast<unsigned long long*>(d.part) + 4 * ((size_t)((red & 1) * NCOMP + c) * d.part_stride + blk);
 }
 
-// Sum NC (<= 2) per-thread values over the block; thread 0 stores them as
-// this block's partials in bank (red & 1).  The sums are exact fixed-point
-// integer sums (cgp_fixed.h): they run on the integer pipe, cost no FP64
-// instructions, and do not depend on the order of the terms.
+// Sum NC (<= 3) per-thread values over the block; warp c then folds
+// component c over the warps and stores it as this block's partial in bank
+// (red & 1).  The sums are exact fixed-point integer sums (cgp_fixed.h): they
+// run on the integer pipe, cost no FP64 instructions, and do not depend on
+// the order of the terms.
 template <int NC>
 __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, double (&v)[NC], Shared& sh) {
-  static_assert(NC <= 2, "at most two components per reduction");
+  static_assert(NC >= 1 && NC <= 3, "one to three components per reduction");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -209,107 +212,92 @@ __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, dou
     }
   }
   __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      fx::I128 x = 0;
-      int e = 1;
-      if (lane < nw) {
-        x = ((fx::I128)sh.whi[c][lane] << 64) | (fx::I128)sh.wlo[c][lane];
-        e = sh.wexp[c][lane];
-      }
-      const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
-      x = warp_sum_i128(E < fx::kBadExp ? fx::sar(x, E - e) : (fx::I128)0);
-      if (lane == 0) {
-        ulonglong2* slot = reinterpret_cast<ulonglong2*>(part_slot(d, red, c, lb));
-        slot[0] = make_ulonglong2((unsigned long long)x, (unsigned long long)(x >> 64));
-        slot[1] = make_ulonglong2((unsigned long long)E, 0ull);
-      }
+  for (int c = warp; c < NC; c += nw) {
+    fx::I128 x = 0;
+    int e = 1;
+    if (lane < nw) {
+      x = ((fx::I128)sh.whi[c][lane] << 64) | (fx::I128)sh.wlo[c][lane];
+      e = sh.wexp[c][lane];
+    }
+    const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+    x = warp_sum_i128(E < fx::kBadExp ? fx::sar(x, E - e) : (fx::I128)0);
+    if (lane == 0) {
+      ulonglong2* slot = reinterpret_cast<ulonglong2*>(part_slot(d, red, c, lb));
+      slot[0] = make_ulonglong2((unsigned long long)x, (unsigned long long)(x >> 64));
+      slot[1] = make_ulonglong2((unsigned long long)E, 0ull);
     }
   }
 }
 
-// Warp 0: the totals over the group's blocks of NC components of reduction
-// `red`, as doubles on every lane.  All slot loads are issued before any is
+// One warp: the total over the group's blocks of component c of reduction
+// `red`, as a double on every lane.  All slot loads are issued before any is
 // used; each lane folds its blocks in a fixed order, so every block of the
 // group computes the same bits.
-template <int NC>
-__device__ __forceinline__ void group_totals(const Desc& d, int red, double (&out)[NC]) {
+__device__ __forceinline__ double group_total(const Desc& d, int red, int c) {
   constexpr int PRE = 8;  // slots per lane held in registers (groups of up to 256 blocks per pass)
   const int lane = threadIdx.x & 31;
-  fx::I128 acc[NC];
-  int Ea[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    acc[c] = 0;
-    Ea[c] = 1;
-  }
+  fx::I128 acc = 0;
+  int Ea = 1;
   for (int base = 0; base < d.nblk; base += 32 * PRE) {
-    ulonglong2 w0[NC][PRE], w1[NC][PRE];
+    ulonglong2 w0[PRE];
+    int ex[PRE];
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-      for (int t = 0; t < PRE; ++t) {
-        const int j = base + lane + 32 * t;
-        if (j < d.nblk) {
-          const ulonglong2* slot = reinterpret_cast<const ulonglong2*>(part_slot(d, red, c, j));
-          w0[c][t] = __ldcg(slot);
-          w1[c][t] = __ldcg(slot + 1);
-        } else {
-          w0[c][t] = make_ulonglong2(0ull, 0ull);
-          w1[c][t] = make_ulonglong2(1ull, 0ull);
-        }
+    for (int t = 0; t < PRE; ++t) {
+      const int j = base + lane + 32 * t;
+      if (j < d.nblk) {
+        const ulonglong2* slot = reinterpret_cast<const ulonglong2*>(part_slot(d, red, c, j));
+        w0[t] = __ldcg(slot);
+        ex[t] = (int)__ldcg(reinterpret_cast<const unsigned long long*>(slot + 1));
+      } else {
+        w0[t] = make_ulonglong2(0ull, 0ull);
+        ex[t] = 1;
       }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      int e = Ea[c];
-#pragma unroll
-      for (int t = 0; t < PRE; ++t) e = max(e, (int)w1[c][t].x);
-      fx::I128 a = fx::sar(acc[c], e - Ea[c]);
-#pragma unroll
-      for (int t = 0; t < PRE; ++t) {
-        const fx::I128 x = ((fx::I128)(long long)w0[c][t].y << 64) | (fx::I128)w0[c][t].x;
-        a += fx::sar(x, e - (int)w1[c][t].x);
-      }
-      acc[c] = a;
-      Ea[c] = e;
     }
-  }
+    int e = Ea;
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)Ea[c]);
-    const fx::I128 t = warp_sum_i128(E < fx::kBadExp ? fx::sar(acc[c], E - Ea[c]) : (fx::I128)0);
-    out[c] = fx::to_double(t, E);
+    for (int t = 0; t < PRE; ++t) e = max(e, ex[t]);
+    fx::I128 a = fx::sar(acc, e - Ea);
+#pragma unroll
+    for (int t = 0; t < PRE; ++t) {
+      const fx::I128 x = ((fx::I128)(long long)w0[t].y << 64) | (fx::I128)w0[t].x;
+      a += fx::sar(x, e - ex[t]);
+    }
+    acc = a;
+    Ea = e;
+  }
+  const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)Ea);
+  const fx::I128 t = warp_sum_i128(E < fx::kBadExp ? fx::sar(acc, E - Ea) : (fx::I128)0);
+  return fx::to_double(t, E);
+}
+
+// Warps 0 .. NC-1 fetch one component each into sh.tot.
+template <int NC>
+__device__ __forceinline__ void totals_to_shared(const Desc& d, int red, Shared& sh) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < NC; c += nw) {
+    const double t = group_total(d, red, c);
+    if ((threadIdx.x & 31) == 0) sh.tot[c] = t;
   }
 }
 
 // After a barrier: totals of reduction `red`, identical in every block.
 template <int NC>
 __device__ __forceinline__ void get_totals(const Desc& d, int red, Shared& sh) {
-  if (threadIdx.x < 32) {
-    double t[NC];
-    group_totals<NC>(d, red, t);
-    if (threadIdx.x == 0)
-#pragma unroll
-      for (int c = 0; c < NC; ++c) sh.tot[c] = t[c];
-  }
+  totals_to_shared<NC>(d, red, sh);
   __syncthreads();
 }
 
 // As get_totals, then `derive(sh)` runs on one thread to turn the totals
 // into the scalars of the next phase (divisions are done once per block, not
-// once per thread); all threads see them afterwards.
+// once per thread); all threads see them afterwards.  The warps that fetched
+// the components meet on a named barrier before the derivation.
 template <int NC, typename F>
 __device__ __forceinline__ void get_totals_then(const Desc& d, int red, Shared& sh, F derive) {
-  if (threadIdx.x < 32) {
-    double t[NC];
-    group_totals<NC>(d, red, t);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) sh.tot[c] = t[c];
-      derive(sh);
-    }
-  }
+  totals_to_shared<NC>(d, red, sh);
+  const int nw = blockDim.x >> 5;
+  const int wk = NC < nw ? NC : nw;
+  if (wk > 1 && (int)(threadIdx.x >> 5) < wk) asm volatile("bar.sync 1, %0;" ::"r"(wk * 32) : "memory");
+  if (threadIdx.x == 0) derive(sh);
   __syncthreads();
 }
 
@@ -682,6 +670,310 @@ __device__ void solve_fp64(const Desc& d, int lb, Shared& sh) {
   finish(d, lb, status, k, 0, sqrt(sh.sc[0]) / bnorm, sqrt(sh.tot[0]) / bnorm, bnorm);
 }
 
+// FP64 Jacobi-PCG in the single-reduction form of Chronopoulos and Gear:
+// one group barrier per iteration.
+//
+// With u = D^-1 r and w = K u, the recurrences p = u + beta p and
+// s = w + beta s (so that s = K p) replace the product K p, and (r,u),
+// (w,u), (r,r) of an iteration share one reduction:
+//   gamma = (r,u), delta = (w,u), beta = gamma / gamma_old,
+//   alpha = gamma / (delta - beta gamma / alpha_old),
+//   x += alpha p, r -= alpha s, u = D^-1 r, w = K u.
+// The product w = K u needs u_j of rows owned by other blocks; each block
+// rebuilds them from the owner's published r_j, w_j and s_j (two buffers of
+// each, by iteration parity) with the owner's own operations, so both hold
+// the same bits.
+//
+// The recurrences let the recursive residual drift from b - K x by
+// rounding.  When the recursive residual meets the tolerance the solver
+// projects x, forms the true residual, and restarts from it if that one
+// does not meet the tolerance as well (at most kMaxRestarts times).
+constexpr int kMaxRestarts = 16;
+
+template <int T, bool RES>
+__device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int chunk = (d.n + d.nblk - 1) / d.nblk;
+  const int r0 = min(d.n, lb * chunk), r1 = min(d.n, r0 + chunk), nloc = r1 - r0;
+  const size_t n = d.n;
+  Group grp{d.bar, &d.res->timeout, (unsigned)d.nblk, 0u, d.spin_ns};
+  int red = 0;
+
+  // published buffers (global): R0/R1, W0/W1, S0/S1 by iteration parity
+  double* const R0 = d.pub64;
+  double* const R1 = d.pub64 + n;
+  double* const W0 = d.pub64 + 2 * n;
+  double* const W1 = d.pub64 + 3 * n;
+  double* const S0 = d.pub64 + 4 * n;
+  double* const S1 = d.pub64 + 5 * n;
+
+  double *x, *r, *u, *w, *p, *s, *bp, *ext = nullptr;
+  const double* di;
+  const double* dih = nullptr;  // RES: D^-1 of the halo rows
+  const int* hid = nullptr;     // RES: global index of each halo slot
+  int nh = 0;
+  Local L;  // row structure of the own rows
+  if constexpr (RES) {
+    double* base = reinterpret_cast<double*>(dsm);
+    x = base;
+    r = base + chunk;
+    u = base + 2 * chunk;
+    w = base + 3 * chunk;
+    p = base + 4 * chunk;
+    s = base + 5 * chunk;
+    double* dil = base + 6 * chunk;
+    bp = base + 7 * chunk;
+    ext = base + 8 * chunk;                  // [chunk + halo_cap]: own u, then gathered halo u
+    double* dh = ext + chunk + d.halo_cap;   // [halo_cap]
+    double* val = dh + d.halo_cap;           // [nnz_cap]
+    int* row = reinterpret_cast<int*>(val + d.res_nnz_cap);
+    int* col = row + chunk + 1;
+    int* hd = col + d.res_nnz_cap;
+    const int k0 = nloc > 0 ? d.rowptr[r0] : 0;
+    const int nnzl = nloc > 0 ? d.rowptr[r1] - k0 : 0;
+    const int h0 = d.hptr[lb];
+    nh = d.hptr[lb + 1] - h0;
+    for (int i = tid; i <= nloc; i += bd) row[i] = d.rowptr[r0 + i] - k0;
+    for (int k = tid; k < nnzl; k += bd) {
+      col[k] = d.lcol[k0 + k];
+      val[k] = d.val[k0 + k];
+    }
+    for (int h = tid; h < nh; h += bd) {
+      const int j = d.hidx[h0 + h];
+      hd[h] = j;
+      dh[h] = d.dinv[j];
+    }
+    for (int i = tid; i < nloc; i += bd) dil[i] = d.dinv[r0 + i];
+    di = dil;
+    dih = dh;
+    hid = hd;
+    L.row = row;
+    L.col = col;
+    L.val = val;
+  } else {
+    x = d.x + r0;
+    r = d.r + r0;
+    u = d.z + r0;
+    w = d.q + r0;
+    p = d.p + r0;
+    s = d.p2 + r0;
+    bp = d.bp + r0;
+    di = d.dinv + r0;
+    L.row = d.rowptr + r0;
+    L.col = d.col;
+    L.val = d.val;
+  }
+
+  // ---- means of b and x0 ----
+  {
+    double v2[2] = {0.0, 0.0};
+    for (int i = tid; i < nloc; i += bd) {
+      v2[0] += d.b[r0 + i];
+      if (d.use_x0) v2[1] += d.x[r0 + i];
+    }
+    put_partials<2>(d, lb, red, v2, sh);
+    if (!grp.sync(sh)) return;
+    get_totals<2>(d, red, sh);
+    ++red;
+  }
+  // ---- projected b and x0; x0 published for the first product ----
+  {
+    const double mb = sh.tot[0] / d.n, mx = sh.tot[1] / d.n;
+    double v1[1] = {0.0};
+    for (int i = tid; i < nloc; i += bd) {
+      const double bi = d.b[r0 + i] - mb;
+      bp[i] = bi;
+      v1[0] += bi * bi;
+      const double xi = d.use_x0 ? d.x[r0 + i] - mx : 0.0;
+      x[i] = xi;
+      if (RES) d.x[r0 + i] = xi;
+    }
+    put_partials<1>(d, lb, red, v1, sh);
+    if (!grp.sync(sh)) return;
+    get_totals<1>(d, red, sh);
+    ++red;
+  }
+  const double bnorm = sqrt(sh.tot[0]);
+  if (!isfinite(bnorm)) { finish(d, lb, CGP_ERR_NONFINITE, 0, 0, 0.0, 0.0, bnorm); return; }
+  if (bnorm == 0.0) {
+    for (int i = tid; i < nloc; i += bd) d.x[r0 + i] = 0.0;
+    finish(d, lb, CGP_OK, 0, 0, 0.0, 0.0, 0.0);
+    return;
+  }
+  const double stop = d.tol * bnorm, stop2 = stop * stop;
+  if (tid == 0) sh.sc[4] = stop2;   // the test ||r||^2 <= (tol ||b||)^2 needs no square root
+
+  int its = 0, restarts = 0, status = CGP_ERR_NOT_CONVERGED, pending = -1;
+  double rr_rec = 0.0, rr_true = 0.0;
+  bool first = true;
+  while (true) {
+    // ---- true residual of the projected, published x: r = bp - K x, u = D^-1 r; r published ----
+    {
+      double v1[1] = {0.0};
+      auto op = [&](int il, double sum) {
+        const double t = bp[il] - sum;
+        r[il] = t;
+        u[il] = di[il] * t;
+        R0[r0 + il] = t;
+        v1[0] += t * t;
+      };
+      if constexpr (RES) {
+        for (int i = tid; i < nloc; i += bd) ext[i] = x[i];
+        for (int h = tid; h < nh; h += bd) ext[nloc + h] = __ldcg(d.x + hid[h]);
+        __syncthreads();
+        spmv_ext<T>(L.row, L.col, L.val, ext, nloc, op);
+      } else {
+        spmv_local<T, double>(
+            L, r0, nloc, [&](int jl) { return x[jl]; }, [&](int j) { return __ldcg(d.x + j); }, op);
+      }
+      put_partials<1>(d, lb, red, v1, sh);
+      if (!grp.sync(sh)) return;   // also publishes r for the first product
+      get_totals<1>(d, red, sh);
+      ++red;
+    }
+    rr_true = sh.tot[0];
+    if (first) rr_rec = rr_true;
+    if (!isfinite(rr_true)) { status = CGP_ERR_NONFINITE; break; }
+    if (rr_true <= stop2) { status = CGP_OK; break; }
+    if (pending >= 0) { status = pending; break; }
+    if (its >= d.max_it || restarts >= kMaxRestarts) { status = CGP_ERR_NOT_CONVERGED; break; }
+    if (!first) ++restarts;
+    first = false;
+
+    // ---- w = K u (halo u_j = D^-1_j r_j from the published r) and the first reduction ----
+    {
+      double v3[3] = {0.0, 0.0, 0.0};
+      auto op = [&](int il, double sum) {
+        w[il] = sum;
+        W0[r0 + il] = sum;
+        const double ui = u[il], ri = r[il];
+        v3[0] += ri * ui;
+        v3[1] += sum * ui;
+        v3[2] += ri * ri;
+      };
+      if constexpr (RES) {
+        for (int i = tid; i < nloc; i += bd) ext[i] = u[i];
+        for (int h = tid; h < nh; h += bd) ext[nloc + h] = dih[h] * __ldcg(R0 + hid[h]);
+        __syncthreads();
+        spmv_ext<T>(L.row, L.col, L.val, ext, nloc, op);
+      } else {
+        __syncthreads();
+        spmv_local<T, double>(
+            L, r0, nloc, [&](int jl) { return u[jl]; }, [&](int j) { return d.dinv[j] * __ldcg(R0 + j); }, op);
+      }
+      put_partials<3>(d, lb, red, v3, sh);
+      if (!grp.sync(sh)) return;
+    }
+    // scalars (thread 0): sc[0] alpha, sc[1] beta, sc[2] gamma, sc[5] (r,r), isc[0] stop flag;
+    // sc[3] = 1 / gamma_old and sc[6] = 1 / alpha_old are prepared off the critical path
+    int k = 0;
+    auto derive = [&](Shared& S) {
+      const double g = S.tot[0], dl = S.tot[1], rr = S.tot[2];
+      int st = -1;
+      if (!isfinite(g) || !isfinite(dl) || !isfinite(rr)) st = CGP_ERR_NONFINITE;
+      else if (rr <= S.sc[4]) st = CGP_OK;
+      else if (its + k >= d.max_it) st = CGP_ERR_NOT_CONVERGED;
+      double beta = 0.0, alpha;
+      if (k == 0) {
+        alpha = g / dl;
+      } else {
+        beta = g * S.sc[3];
+        alpha = g / (dl - beta * g * S.sc[6]);
+      }
+      if (st < 0 && !(g > 0.0 && alpha > 0.0 && isfinite(alpha))) st = CGP_ERR_BREAKDOWN;
+      S.isc[0] = st;
+      S.sc[0] = alpha;
+      S.sc[1] = beta;
+      S.sc[2] = g;
+      S.sc[5] = rr;
+    };
+    get_totals_then<3>(d, red, sh, derive);
+    ++red;
+    while (true) {
+      const int st = sh.isc[0];
+      if (st >= 0) {
+        if (st != CGP_OK) pending = st;
+        break;
+      }
+      if (tid == 32 || (bd == 32 && tid == 0)) {
+        sh.sc[3] = 1.0 / sh.sc[2];
+        sh.sc[6] = 1.0 / sh.sc[0];
+      }
+      const double alpha = sh.sc[0], beta = sh.sc[1];
+      const double* Rc = (k & 1) ? R1 : R0;
+      const double* Wc = (k & 1) ? W1 : W0;
+      const double* Sc = (k & 1) ? S1 : S0;
+      double* Rn = (k & 1) ? R0 : R1;
+      double* Wn = (k & 1) ? W0 : W1;
+      double* Sn = (k & 1) ? S0 : S1;
+      // own rows: p, s, x, r, u; r and s published
+      for (int i = tid; i < nloc; i += bd) {
+        const double pi = k == 0 ? u[i] : fma(beta, p[i], u[i]);
+        const double si = k == 0 ? w[i] : fma(beta, s[i], w[i]);
+        p[i] = pi;
+        s[i] = si;
+        x[i] = fma(alpha, pi, x[i]);
+        const double ri = fma(-alpha, si, r[i]);
+        r[i] = ri;
+        const double ui = di[i] * ri;
+        u[i] = ui;
+        Rn[r0 + i] = ri;
+        Sn[r0 + i] = si;
+        if (RES) ext[i] = ui;
+      }
+      // halo: u_j = D^-1_j (r_j - alpha (w_j + beta s_j)) from the owner's published values
+      auto halo_u = [&](int j, double dj) {
+        const double sj = k == 0 ? __ldcg(Wc + j) : fma(beta, __ldcg(Sc + j), __ldcg(Wc + j));
+        return dj * fma(-alpha, sj, __ldcg(Rc + j));
+      };
+      if constexpr (RES) {
+        for (int h = tid; h < nh; h += bd) ext[nloc + h] = halo_u(hid[h], dih[h]);
+      }
+      __syncthreads();
+      double v3[3] = {0.0, 0.0, 0.0};
+      auto op = [&](int il, double sum) {
+        w[il] = sum;
+        Wn[r0 + il] = sum;
+        const double ui = u[il], ri = r[il];
+        v3[0] += ri * ui;
+        v3[1] += sum * ui;
+        v3[2] += ri * ri;
+      };
+      if constexpr (RES) {
+        spmv_ext<T>(L.row, L.col, L.val, ext, nloc, op);
+      } else {
+        spmv_local<T, double>(
+            L, r0, nloc, [&](int jl) { return u[jl]; }, [&](int j) { return halo_u(j, d.dinv[j]); }, op);
+      }
+      put_partials<3>(d, lb, red, v3, sh);
+      if (!grp.sync(sh)) return;
+      ++k;
+      get_totals_then<3>(d, red, sh, derive);
+      ++red;
+    }
+    its += k;
+    rr_rec = sh.sc[5];
+    // ---- x -= mean(x), published for the true residual ----
+    {
+      double v1[1] = {0.0};
+      for (int i = tid; i < nloc; i += bd) v1[0] += x[i];
+      put_partials<1>(d, lb, red, v1, sh);
+      if (!grp.sync(sh)) return;
+      get_totals<1>(d, red, sh);
+      ++red;
+    }
+    const double mxf = sh.tot[0] / d.n;
+    for (int i = tid; i < nloc; i += bd) {
+      const double xi = x[i] - mxf;
+      x[i] = xi;
+      if (RES) d.x[r0 + i] = xi;
+    }
+    if (!grp.sync(sh)) return;
+  }
+  finish(d, lb, status, its, restarts, sqrt(rr_rec) / bnorm, sqrt(rr_true) / bnorm, bnorm);
+}
+
 // ---------------------------------------------------------------------------
 // FP32 reductions of the inner solve: warp trees on the FP32 pipe, one slot
 // per block, every block sums the slots in the same order (deterministic).
@@ -776,7 +1068,7 @@ __device__ __forceinline__ void spmv_ext32(const int* __restrict__ row, const in
 // Inner (FP32): Jacobi-preconditioned CG in the single-reduction form of
 // Chronopoulos and Gear (the recurrence s = w + beta s replaces the product
 // A p, and (r,u), (w,u), (r,r) share one reduction), solving K e = r from
-// e = 0 to ||r_inner|| <= inner_tol ||r||.  One barrier per inner
+// e = 0 to ||r_inner|| <= max(inner_tol ||r||, tol ||b|| / 2).  One barrier per inner
 // iteration: the product w = A u needs u_j of rows owned elsewhere, which
 // each block rebuilds from the owner's published r_j, w_j, s_j (kept in two
 // buffers by iteration parity) with the owner's own FMAs.
@@ -968,7 +1260,7 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
       int st = -1;
       if (k == 0) S.fsc[3] = rr;                                       // ||r_0||^2 of this sweep
       if (!isfinite(rr) || !isfinite(g) || !isfinite(dl)) st = 1;     // non-finite
-      else if (rr <= S.fsc[4] * S.fsc[3]) st = 0;                     // inner tolerance reached
+      else if (rr <= fmaxf(S.fsc[4] * S.fsc[3], S.fsc[5])) st = 0;   // inner tolerance reached
       else if (total + k >= d.max_it) st = 0;
       float beta = 0.0f, alpha;
       if (k == 0) {
@@ -983,7 +1275,12 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
       S.fsc[1] = beta;
       S.fsc[2] = g;
     };
-    if (tid == 0) sh.fsc[4] = (float)(d.inner_tol * d.inner_tol);
+    if (tid == 0) {
+      sh.fsc[4] = (float)(d.inner_tol * d.inner_tol);
+      // below half the outer target the correction would already pass the outer test
+      const double floor = 0.5 * d.tol * bnorm;
+      sh.fsc[5] = (float)(floor * floor);
+    }
     get_totals_f_then<3>(d, red, sh, derive);
     ++red;
     bool bad = false;
@@ -1074,8 +1371,10 @@ __global__ void __launch_bounds__(MAX_BLOCK) pcg_persistent_kernel(Desc d) {
   mark_pending(d, blockIdx.x);
   if (d.mixed)
     solve_mixed<T, RES>(d, blockIdx.x, sh);
-  else
+  else if (d.classic)
     solve_fp64<T, RES>(d, blockIdx.x, sh);
+  else
+    solve_fp64_sr<T, RES>(d, blockIdx.x, sh);
 }
 
 // Many independent systems in one launch: block b runs instance
@@ -1091,8 +1390,10 @@ __global__ void __launch_bounds__(MAX_BLOCK)
   mark_pending(d, lb);
   if (d.mixed)
     solve_mixed<T, RES>(d, lb, sh);
-  else
+  else if (d.classic)
     solve_fp64<T, RES>(d, lb, sh);
+  else
+    solve_fp64_sr<T, RES>(d, lb, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -1236,14 +1537,33 @@ int get_halo_plan(cgp_mesh_impl* m, int nblk, HaloPlan& out) {
   return CGP_OK;
 }
 
-// Dynamic shared memory of a block that keeps its rows resident: FP64 needs
-// seven vectors, the halo buffer and an FP64 CSR slice; the mixed solver six
-// FP32 vectors, D^-1, the halo buffer and D^-1 of the halo, and an FP32 slice.
-size_t res_smem_bytes(bool mixed, int chunk, const HaloPlan& hp) {
-  const size_t s = mixed ? 4 * ((size_t)9 * chunk + 3 * (size_t)hp.max_halo + 2 * (size_t)hp.max_nnz + 1)
-                         : 8 * ((size_t)7 * chunk + hp.max_halo + hp.max_nnz) +
-                               4 * ((size_t)chunk + 1 + hp.max_nnz + hp.max_halo);
+// Solver variants of one launch.
+enum SolverKind { KIND_FP64_CLASSIC = 0, KIND_MIXED = 1, KIND_FP64_SR = 2 };
+
+SolverKind solver_kind(bool mixed, int flags) {
+  return mixed ? KIND_MIXED : ((flags & 2) ? KIND_FP64_CLASSIC : KIND_FP64_SR);
+}
+
+// Dynamic shared memory of a block that keeps its rows resident: the classic
+// FP64 solver needs seven vectors, the halo buffer and an FP64 CSR slice; the
+// single-reduction FP64 solver eight vectors, the halo buffer, D^-1 of the
+// halo and the slice; the mixed solver six FP32 vectors, D^-1, the halo
+// buffer and D^-1 of the halo, and an FP32 slice.
+size_t res_smem_bytes(SolverKind kind, int chunk, const HaloPlan& hp) {
+  const size_t ints = 4 * ((size_t)chunk + 1 + hp.max_nnz + hp.max_halo);
+  size_t s = 0;
+  if (kind == KIND_MIXED)
+    s = 4 * ((size_t)9 * chunk + 3 * (size_t)hp.max_halo + 2 * (size_t)hp.max_nnz + 1);
+  else if (kind == KIND_FP64_CLASSIC)
+    s = 8 * ((size_t)7 * chunk + hp.max_halo + hp.max_nnz) + ints;
+  else
+    s = 8 * ((size_t)9 * chunk + 2 * (size_t)hp.max_halo + hp.max_nnz) + ints;
   return (s + 15) / 16 * 16;
+}
+
+// Bound on the barrier epochs of one solve (the counter must stay below 2^31).
+long long max_epochs(const cgp_solve_opts& o) {
+  return 16LL + 4LL * (long long)std::max(o.max_it, 1) + 8LL * std::max(o.max_sweeps, 1) + 8LL * 16;
 }
 
 // Shape of a persistent launch for an n-row system.  For FP64 on a mesh the
@@ -1261,7 +1581,15 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
   if (cap0 <= 0) return fail(CGP_ERR_CUDA, "solver: kernel cannot be resident on this device");
   const int sms = std::max(1, dev_info(device).sms);
   int nblk = tu.blocks;
-  if (nblk <= 0) nblk = n <= 4096 ? 1 : std::min(sms, (n + 767) / 768);
+  if (nblk <= 0) {
+    // FP64 work per row is slow on this GPU's narrow FP64 pipe: spread small
+    // systems over several SMs; the FP32 inner solve of MIXED is cheap per row
+    // and small systems are best kept in one block (no grid barriers).
+    if (mixed)
+      nblk = n <= 4096 ? 1 : std::min(sms, (n + 767) / 768);
+    else
+      nblk = std::min(sms, std::max(1, (n + 255) / 256));
+  }
   nblk = std::max(1, std::min(nblk, std::min(cap0, n)));
   out = LaunchPlan{};
   out.fn = fn0;
@@ -1278,11 +1606,12 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
     return CGP_OK;
   }
   const size_t limit = (size_t)std::max(0, optin_smem(device) - (int)fa.sharedSizeBytes - 1024);
-  if ((size_t)chunk * 56 + (size_t)rough_nnz * 12 > limit) return CGP_OK;
+  const SolverKind kind = solver_kind(mixed, tu.flags);
+  if ((size_t)chunk * (kind == KIND_FP64_SR ? 72 : 56) + (size_t)rough_nnz * 12 > limit) return CGP_OK;
   HaloPlan hp;
   int st = get_halo_plan(m, nblk, hp);
   if (st != CGP_OK) return st;
-  const size_t smem = res_smem_bytes(mixed, chunk, hp);
+  const size_t smem = res_smem_bytes(kind, chunk, hp);
   if (smem > limit) return CGP_OK;
   if (cudaFuncSetAttribute((const void*)fnr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
@@ -1311,7 +1640,7 @@ namespace {
 
 // Descriptor of one system solved by `nblk` blocks (blk0 set by the caller).
 Desc make_desc(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opts& o, int nblk,
-               const LaunchPlan& plan, unsigned* bar, SolveResult* res) {
+               const LaunchPlan& plan, unsigned* bar, SolveResult* res, int flags) {
   Desc d{};
   d.n = m->n_c;
   d.rowptr = m->rowptr;
@@ -1328,6 +1657,7 @@ Desc make_desc(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opt
   d.p = m->p;
   d.p2 = m->p2;
   d.q = m->q;
+  d.pub64 = m->pub64;
   d.f32pub = m->f32pub;
   d.f32own = m->f32own;
   d.fpart = m->fpart;
@@ -1344,6 +1674,7 @@ Desc make_desc(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opt
   d.max_sweeps = o.max_sweeps;
   d.use_x0 = o.use_x0;
   d.mixed = o.precision == CGP_MIXED ? 1 : 0;
+  d.classic = (flags & 2) ? 1 : 0;
   d.res_nnz_cap = plan.nnz_cap;
   d.halo_cap = plan.halo_cap;
   d.lcol = plan.halo.lcol;
@@ -1364,10 +1695,9 @@ int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_o
   if (st != CGP_OK) return st;
   const int nblk = plan.nblk;
   // barrier epochs stay far below 2^32 / nblk
-  const long long max_epochs = 8LL + 4LL * (long long)std::max(o.max_it, 1) + 8LL * std::max(o.max_sweeps, 1);
-  if (max_epochs * nblk >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "solver: max_it too large");
+  if (max_epochs(o) * nblk >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "solver: max_it too large");
 
-  Desc d = make_desc(m, b, x, o, nblk, plan, m->bar, m->res);
+  Desc d = make_desc(m, b, x, o, nblk, plan, m->bar, m->res, tu.flags);
   d.out = info_dev;
 
   CGP_CUDA(cudaMemsetAsync(m->bar, 0, 256, s));
@@ -1396,12 +1726,11 @@ void (*spmv_for(int lanes))(int, const int*, const int*, const V*, const V*, V*)
 int launch_solve_fp64_raw(int device, const RawSystem& sys, const RawScratch& scr, const double* b, double* x,
                           const cgp_solve_opts& o, cudaStream_t s) {
   LaunchPlan plan;
-  const SolverTuning tu{0, 1, 0, 1};   // default shape, vectors in global scratch
+  const SolverTuning tu{0, 1, 0, 3};   // default shape, vectors in global scratch, classic FP64 iteration
   int st = plan_solve(nullptr, device, sys.n, scr.max_blocks, tu, false, plan);
   if (st != CGP_OK) return st;
   const int nblk = plan.nblk;
-  const long long max_epochs = 8LL + 4LL * (long long)std::max(o.max_it, 1);
-  if (max_epochs * nblk >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "solver: max_it too large");
+  if (max_epochs(o) * nblk >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "solver: max_it too large");
   Desc d{};
   d.n = sys.n;
   d.rowptr = sys.rowptr;
@@ -1429,6 +1758,7 @@ int launch_solve_fp64_raw(int device, const RawSystem& sys, const RawScratch& sc
   d.max_sweeps = 1;
   d.use_x0 = o.use_x0;
   d.mixed = 0;
+  d.classic = 1;
   d.res_nnz_cap = 0;
   d.spin_ns = 2000000000LL;
   void* args[] = {&d};
@@ -1478,7 +1808,7 @@ struct BatchShape {
   int block = 512;
   int lanes = 1;
   int per_sm = 0;   // blocks per SM (0: as many as can be co-resident)
-  int flags = 0;    // bit 0: rows in global memory
+  int flags = 0;    // bit 0: rows in global memory; bit 1: classic FP64 iteration
 };
 
 }  // namespace cgp
@@ -1560,6 +1890,7 @@ int batch_plan(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
   }
   // shared-memory residency when every instance's chunk fits
   std::vector<HaloPlan> hp(count);
+  const SolverKind kind = solver_kind(mixed, sh.flags);
   bool res = !(sh.flags & 1);
   size_t smem = 0;
   BatchFn fnr = batched_kernel_for(lanes, true);
@@ -1573,13 +1904,13 @@ int batch_plan(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
     cgp_mesh_impl* m = B->meshes[i];
     const int chunk = (m->n_c + nb[i] - 1) / nb[i];
     const int rough_nnz = m->h_rowptr[std::min(m->n_c, chunk)] - m->h_rowptr[0];
-    if ((size_t)chunk * 56 + (size_t)rough_nnz * 12 > limit) {
+    if ((size_t)chunk * (kind == KIND_FP64_SR ? 72 : 56) + (size_t)rough_nnz * 12 > limit) {
       res = false;
       break;
     }
     int st = get_halo_plan(m, nb[i], hp[i]);
     if (st != CGP_OK) return st;
-    smem = std::max(smem, res_smem_bytes(mixed, chunk, hp[i]));
+    smem = std::max(smem, res_smem_bytes(kind, chunk, hp[i]));
     if (smem > limit) res = false;
   }
   if (res) {
@@ -1614,10 +1945,9 @@ int batch_plan(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
     }
     unsigned char* ctrl = B->d_ctrl + kCtrlPerInstance * i;
     desc[i] = make_desc(m, B->b[i], B->x[i], o, nb[i], lp, reinterpret_cast<unsigned*>(ctrl),
-                        reinterpret_cast<SolveResult*>(ctrl + 256));
+                        reinterpret_cast<SolveResult*>(ctrl + 256), sh.flags);
     desc[i].blk0 = blk0;
-    const long long max_epochs = 8LL + 4LL * (long long)std::max(o.max_it, 1) + 8LL * std::max(o.max_sweeps, 1);
-    if (max_epochs * nb[i] >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "batch: max_it too large");
+    if (max_epochs(o) * nb[i] >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "batch: max_it too large");
     for (int k = 0; k < nb[i]; ++k) blk_inst[blk0 + k] = i;
     blk0 += nb[i];
   }
@@ -1707,10 +2037,10 @@ static bool valid_shape(int what, int block, int lanes) {
 extern "C" int cgp_set_tuning(cgp_mesh m, int what, int block, int lanes, int blocks, int flags) {
   if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: NULL mesh");
   if (what < 0 || what > 3) return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: unknown target");
-  if (!valid_shape(what, block, lanes) || blocks < 0 || (flags & ~1))
+  if (!valid_shape(what, block, lanes) || blocks < 0 || (flags & ~3))
     return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: block must be 0 or a multiple of 32 in [64, 512] "
                                      "(solver) or [64, 256] (SpMV), "
-                                     "lanes 0, 1, 2, 4, 8 or 32, blocks >= 0, flags 0 or 1");
+                                     "lanes 0, 1, 2, 4, 8 or 32, blocks >= 0, flags 0 to 3");
   m->tune[what] = SolverTuning{block, lanes, blocks, flags};
   return CGP_OK;
 }
@@ -1827,7 +2157,7 @@ extern "C" int cgp_batch_create(const cgp_mesh* meshes, int count, const double*
 
 extern "C" int cgp_batch_set_tuning(cgp_batch batch, int block, int lanes, int blocks_per_sm, int flags) {
   if (!batch) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_set_tuning: NULL batch");
-  if (!valid_shape(CGP_TUNE_SOLVE_FP64, block, lanes) || blocks_per_sm < 0 || (flags & ~1))
+  if (!valid_shape(CGP_TUNE_SOLVE_FP64, block, lanes) || blocks_per_sm < 0 || (flags & ~3))
     return fail(CGP_ERR_INVALID_ARG, "cgp_batch_set_tuning: bad shape");
   return batch_plan(batch, BatchShape{block, lanes, blocks_per_sm, flags}, batch->opts);
 }
@@ -1887,7 +2217,8 @@ extern "C" int cgp_batch_autotune(cgp_batch batch, void* stream, double* best_ms
   const int blocks[2] = {256, 512};
   const int lanes[2] = {1, 2};
   const int per_sm[2] = {1, 2};
-  for (int fl = 0; fl < 2; ++fl)
+  const int nflags = batch->opts.precision == CGP_MIXED ? 2 : 4;
+  for (int fl = 0; fl < nflags; ++fl)
     for (int bk : blocks)
       for (int ln : lanes)
         for (int ps : per_sm) {
@@ -2018,7 +2349,8 @@ extern "C" int cgp_autotune(cgp_mesh m, int precision, const double* b, double* 
   const SolverTuning saved = m->tune[what];
   SolverTuning best{};
   float best_t = 1e30f;
-  for (int fl = 0; fl < 2; ++fl)
+  const int nflags = precision == CGP_MIXED ? 2 : 4;   // bit 1 (classic FP64 iteration) only for FP64
+  for (int fl = 0; fl < nflags; ++fl)
     for (int bk : {256, 512})
       for (int ln : {1, 2, 4})
         for (int c : counts) {

@@ -147,12 +147,29 @@ def oracle_rhs(om, u, v, kind=0, B=(0.0, 1.0, 1.0)):
     return O.rhs(om.Gx, om.Gy, Fx, Fy)
 
 
+def assert_iterations_match(info, ref_its, textbook):
+    """The textbook iteration follows the oracle to +-2 steps; the single-reduction form
+    rounds differently and may restart from the true residual (counted in outer_sweeps)."""
+    if textbook:
+        assert info["outer_sweeps"] == 0
+        assert abs(info["iterations"] - ref_its) <= 2, (info, ref_its)
+    else:
+        assert info["outer_sweeps"] <= 2, info
+        slack = 3 + info["outer_sweeps"] * max(10, ref_its // 5)
+        assert abs(info["iterations"] - ref_its) <= slack, (info, ref_its)
+
+
 SHAPES = [(128, 1, 1), (128, 2, 5), (128, 4, 3), (256, 8, 7), (64, 32, 2), (64, 1, 13), (512, 1, 0)]
 
 
-@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3])
 @pytest.mark.parametrize("block,lanes,blocks", SHAPES)
 def test_fp64_solve_matches_oracle(pair, cgp, block, lanes, blocks, flags):
+    """Both FP64 iterations (bit 1: textbook, else single-reduction) in both storage modes (bit 0).
+
+    The single-reduction form takes the same steps in exact arithmetic; its
+    recurrences round differently, so its count may differ by a little more,
+    and a restart from the true residual (outer_sweeps) adds a few iterations."""
     m, om = pair
     u, v = velocity_for(om)
     b = oracle_rhs(om, u, v)
@@ -162,12 +179,12 @@ def test_fp64_solve_matches_oracle(pair, cgp, block, lanes, blocks, flags):
     info = cgp.cgp_poisson_solve(m.handle, T(b), x, tol=1e-12)
     launch = cgp.cgp_last_launch(m.handle)
     cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64, 0, 0, 0, 0)
-    if flags == 1:
+    if flags & 1:
         assert launch["resident"] == 0
     elif m.n_c <= 600:
         assert launch["resident"] == 1, launch     # these systems always fit in shared memory
     assert info["status"] == cgp.CGP_OK, info
-    assert abs(info["iterations"] - ref["iterations"]) <= 2
+    assert_iterations_match(info, ref["iterations"], textbook=bool(flags & 2))
     xs = x.cpu().numpy()
     assert rel(xs, ref["x"]) <= 1e-10
     assert abs(xs.mean()) <= 1e-14 * max(1.0, np.max(np.abs(xs)))
@@ -183,7 +200,7 @@ def test_fp64_solve_with_initial_guess(pair, cgp):
     x = T(x0)
     info = cgp.cgp_poisson_solve(m.handle, T(b), x, tol=1e-10, use_x0=True)
     assert info["status"] == cgp.CGP_OK
-    assert abs(info["iterations"] - ref["iterations"]) <= 2
+    assert_iterations_match(info, ref["iterations"], textbook=False)
     assert rel(x.cpu().numpy(), ref["x"]) <= 1e-9
 
 
@@ -219,15 +236,21 @@ def test_solver_status_codes(cgp):
     u, v = velocity_for(om)
     b = oracle_rhs(om, u, v)
     x = torch.zeros(m.n_c, dtype=torch.float64, device=DEV)
-    info = cgp.cgp_poisson_solve(m.handle, T(b), x, tol=1e-12, max_it=3)
-    assert info["status"] == cgp.CGP_ERR_NOT_CONVERGED and info["iterations"] == 3
-    bn = b.copy()
-    bn[5] = np.nan
-    info = cgp.cgp_poisson_solve(m.handle, T(bn), x, tol=1e-8)
-    assert info["status"] == cgp.CGP_ERR_NONFINITE
-    info = cgp.cgp_poisson_solve(m.handle, T(np.zeros(m.n_c)), x, tol=1e-8)
-    assert info["status"] == cgp.CGP_OK and info["iterations"] == 0
-    assert float(torch.max(torch.abs(x))) == 0.0
+    for flags in (0, 2):     # single-reduction and textbook FP64 iterations
+        cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64, 0, 0, 0, flags)
+        x.zero_()
+        info = cgp.cgp_poisson_solve(m.handle, T(b), x, tol=1e-12, max_it=3)
+        assert info["status"] == cgp.CGP_ERR_NOT_CONVERGED and info["iterations"] == 3
+        info = cgp.cgp_poisson_solve(m.handle, T(b), x, tol=1e-12, max_it=0)
+        assert info["status"] == cgp.CGP_ERR_NOT_CONVERGED and info["iterations"] == 0
+        bn = b.copy()
+        bn[5] = np.nan
+        info = cgp.cgp_poisson_solve(m.handle, T(bn), x, tol=1e-8)
+        assert info["status"] == cgp.CGP_ERR_NONFINITE
+        info = cgp.cgp_poisson_solve(m.handle, T(np.zeros(m.n_c)), x, tol=1e-8)
+        assert info["status"] == cgp.CGP_OK and info["iterations"] == 0
+        assert float(torch.max(torch.abs(x))) == 0.0
+    cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64, 0, 0, 0, 0)
     with pytest.raises(cgp.CgpError) as e:
         cgp.cgp_poisson_solve(m.handle, T(b), x, tol=1e-8, max_it=3, raise_on_status=True)
     assert e.value.status == cgp.CGP_ERR_NOT_CONVERGED
