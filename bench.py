@@ -50,6 +50,27 @@ def workload_config(precision="fp64"):
             "l2": "flushed between timed steps (512 MiB write)", "seed": SEED}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent
+# solver launch, from one ncu capture of `bench.py --profile-case <precision>`
+# (the bench's launch shape).  They hold only for the kernel sources they were
+# taken on: when the sources' hash differs the traffic is reported as null.
+SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_sync.h", "cgp_fixed.h", "cgp_internal.h")
+SOLVER_TRAFFIC = {
+    "sha256": "228da2b8365f977c7e6df9b2117738beec735534842ca332a3b8186155765069",
+    "fp64": 14491904 + 246528,
+    "mixed": 21242880 + 246016,
+}
+
+
+def solver_traffic(precision):
+    import hashlib
+    h = hashlib.sha256()
+    for f in SOLVER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2003_00082_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return SOLVER_TRAFFIC[precision] if h.hexdigest() == SOLVER_TRAFFIC["sha256"] else None
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -376,6 +397,7 @@ def run_mine(args, rank, world, local_rank):
         result["spmv"] = spmv_bench(cgp, inputs, torch, dev, peak)
     if rank == 0 and not args.no_variants:
         from paper_2003_00082_gb300 import configs
+        result["mixed_64x32"] = run_mixed_small(cgp, inputs, torch, dev)
         result["batched"] = run_batched(cgp, inputs, configs, torch, dev, flush, peak)
         result["learned_guess"] = run_learned_guess(cgp, inputs, torch)
     mesh.close()
@@ -441,6 +463,80 @@ def run_batched(cgp, inputs, configs, torch, dev, flush, peak, reps=5):
     batch.close()
     for m in meshes:
         m.close()
+    return out
+
+
+def run_mixed_small(cgp, inputs, torch, dev, steps=200, check_every=10):
+    """Mixed precision on the 64x32 vortex-train sequence with noise (B = k, tol 1e-8, inner 1e-4,
+    previous-step x0): solves/s of FP64 and mixed over the same potential steps, and the relative
+    L2 errors of phi_f, grad phi and J x B of both against tightly converged FP64 (tol 1e-13)."""
+    from paper_2003_00082_gb300 import configs
+    wl = configs.C3_MIXED
+    xy, tri = inputs.ogrid(wl.n_theta, wl.n_r)
+    m = cgp.Mesh(xy, tri)
+    xy_f, _, _ = m.fine_geometry()
+    f64 = dict(dtype=torch.float64, device=dev)
+    n, nf, tf = m.n_c, m.n_f, m.t_f
+    U = torch.empty((steps, 2, nf), **f64)
+    for t in range(steps):
+        u, v = inputs.velocity(xy_f, t, wl.seed, vortices=True, noise_std=wl.noise_std)
+        U[t, 0].copy_(torch.as_tensor(u))
+        U[t, 1].copy_(torch.as_tensor(v))
+    b = torch.empty((steps, n), **f64)
+    for t in range(steps):
+        cgp.cgp_restrict(m.handle, cgp.CGP_RHS_POTENTIAL, wl.B, wl.rho_over_dt, U[t, 0], U[t, 1], b[t])
+    stream = torch.cuda.current_stream()
+    infos = torch.zeros(steps * cgp.INFO_BYTES, dtype=torch.uint8, device=dev)
+
+    def fields(phi_c, t):
+        phi_f = torch.empty(nf, **f64)
+        grad = torch.empty(2 * tf, **f64)
+        force = torch.empty(2 * tf, **f64)
+        cgp.cgp_prolong(m.handle, phi_c, phi_f)
+        cgp.cgp_lorentz(m.handle, phi_f, U[t, 0], U[t, 1], wl.B, wl.sigma, grad, force)
+        return phi_f, grad, force
+
+    out = {"workload": "64x32 O-grid potential steps, vortex train + noise 1e-3, B = k, tol 1e-8, previous-step x0",
+           "steps": steps}
+    sols = {}
+    for name, prec in (("fp64", cgp.CGP_FP64), ("mixed", cgp.CGP_MIXED)):
+        x = torch.zeros(n, **f64)
+        phis = torch.empty((steps, n), **f64)
+        for t in range(3):   # warm-up on the first steps
+            cgp.cgp_poisson_solve(m.handle, b[t], x, tol=wl.tol, precision=prec, inner_tol=wl.inner_tol,
+                                  use_x0=t > 0, info=False)
+        x.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(steps):
+            cgp.cgp_poisson_solve_async(m.handle, b[t], x, tol=wl.tol, precision=prec, inner_tol=wl.inner_tol,
+                                        use_x0=t > 0, info_dev=infos.data_ptr() + t * cgp.INFO_BYTES)
+            phis[t].copy_(x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        recs = cgp.decode_infos(bytes(infos.cpu().numpy()), steps)
+        ms = e0.elapsed_time(e1)
+        out[name] = {"solves_per_s": steps / (ms * 1e-3), "ms_per_solve": ms / steps,
+                     "iterations_mean": statistics.mean(r["iterations"] for r in recs),
+                     "all_converged": all(r["status"] == cgp.CGP_OK for r in recs),
+                     "rel_res_true_max": max(r["rel_res_true"] for r in recs)}
+        sols[name] = phis
+    rel = lambda a, c: float(torch.linalg.norm(a - c) / torch.linalg.norm(c))  # noqa: E731
+    worst = {k: {"phi_f": 0.0, "grad_phi": 0.0, "force": 0.0} for k in ("fp64", "mixed")}
+    xt = torch.zeros(n, **f64)
+    for t in range(0, steps, check_every):
+        xt.zero_()
+        cgp.cgp_poisson_solve(m.handle, b[t], xt, tol=1e-13, max_it=100000)
+        ref = fields(xt, t)
+        for k in ("fp64", "mixed"):
+            got = fields(sols[k][t], t)
+            for name, g, r in zip(("phi_f", "grad_phi", "force"), got, ref):
+                worst[k][name] = max(worst[k][name], rel(g, r))
+    out["rel_err_vs_tight_fp64"] = worst
+    out["speedup_mixed_over_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    m.close()
     return out
 
 
@@ -596,7 +692,7 @@ def profile_case(case):
         x = torch.zeros(m.n_c, dtype=torch.float64, device=dev)
         prec = cgp.CGP_MIXED if case == "mixed" else cgp.CGP_FP64
         what = cgp.CGP_TUNE_SOLVE_MIXED if case == "mixed" else cgp.CGP_TUNE_SOLVE_FP64
-        cgp.cgp_set_tuning(m.handle, what, 512, 1, 304, 0)    # the shape the autotuner picks on GB300
+        cgp.cgp_set_tuning(m.handle, what, 512, 1, 152, 0)    # the shape the autotuner picks on GB300
         for _ in range(2):
             x.zero_()
             info = cgp.cgp_poisson_solve(m.handle, b, x, tol=TOL, precision=prec)
@@ -674,7 +770,7 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic", "config": workload_config(args.precision),
             "roofline": {"bound": "hbm", "achieved": res["achieved"], "peak": peak, "unit": "GB/s",
-                         "frac": res["achieved"] / peak, "traffic": None,
+                         "frac": res["achieved"] / peak, "traffic": solver_traffic(args.precision),
                          "kernel": "pcg_persistent_kernel",
                          "alg_bytes_per_launch": res["alg_bytes_per_launch"],
                          "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({res['peak_kind']})",
@@ -694,6 +790,8 @@ def main():
             line["spmv"] = res["spmv"]
         if res.get("variant"):
             line["other_precision"] = res["variant"]
+        if "mixed_64x32" in res:
+            line["mixed_64x32"] = res["mixed_64x32"]
         if "batched" in res:
             line["batched"] = res["batched"]
         if "learned_guess" in res:

@@ -273,6 +273,11 @@ int cgp_poisson_solve_batched(const cgp_mesh* meshes, int count, const double* c
  *                  samples; params host [param_count].  Allocates its device
  *                  memory; synchronous.
  * cgp_gnn_predict  x0 (device [n_c]) from b, phi1, phi2 (device [n_c]); async.
+ *                  One cooperative launch runs the whole forward (the same
+ *                  arithmetic as the batched training forward, so the same
+ *                  bits); its grid barriers give up after about two seconds
+ *                  and then leave NaN in x0, which the solve reports as
+ *                  CGP_ERR_NONFINITE.
  * cgp_gnn_train_step  forward, loss, backward and one Adam step on `batch`
  *                  samples stacked sample-major (device [batch][n_c] each,
  *                  phi_t the solutions to learn); loss_dev (device float,

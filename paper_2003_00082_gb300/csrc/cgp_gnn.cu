@@ -14,7 +14,9 @@
 // rounding in the epilogue.  Activations h, messages m, aggregates a and
 // the dense weights are stored in BF16; master weights, Adam moments,
 // gradients and every sum are FP32.  Aggregations and all gradient sums run
-// in a fixed order (no atomics), so training is deterministic.
+// in a fixed order (no atomics), so training is deterministic.  Inference of
+// one sample (cgp_gnn_predict) is a single cooperative kernel with four grid
+// barriers instead of the dozen launches of the batched forward.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -24,6 +26,7 @@
 #include <vector>
 
 #include "cgp_internal.h"
+#include "cgp_sync.h"
 
 namespace cgp {
 namespace gnn {
@@ -79,6 +82,25 @@ __device__ __forceinline__ void warp_tile_mma(const bf16* X, int ldx, const bf16
   }
 }
 
+// One warp: acc[16 x 8] += X[16 rows x K] * W[nt*8 .. nt*8+7]^T, the n-tile nt of
+// warp_tile_mma with the same k order (the same bits for those 8 outputs).
+template <int K>
+__device__ __forceinline__ void warp_tile_mma_nt(const bf16* X, int ldx, const bf16* W, int ldw, int nt,
+                                                 float (&acc)[4]) {
+  const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const unsigned a0 = *reinterpret_cast<const unsigned*>(X + gid * ldx + k0 + tig * 2);
+    const unsigned a1 = *reinterpret_cast<const unsigned*>(X + (gid + 8) * ldx + k0 + tig * 2);
+    const unsigned a2 = *reinterpret_cast<const unsigned*>(X + gid * ldx + k0 + 8 + tig * 2);
+    const unsigned a3 = *reinterpret_cast<const unsigned*>(X + (gid + 8) * ldx + k0 + 8 + tig * 2);
+    const bf16* w = W + (nt * 8 + gid) * ldw + k0 + tig * 2;
+    const unsigned b0 = *reinterpret_cast<const unsigned*>(w);
+    const unsigned b1 = *reinterpret_cast<const unsigned*>(w + 8);
+    mma_bf16(acc, a0, a1, a2, a3, b0, b1);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // set-up: mean edge length and edge features
 // ---------------------------------------------------------------------------
@@ -117,9 +139,10 @@ __global__ void edge_feature_kernel(int E, const int* __restrict__ dst, const in
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
-// One block per sample: residual r = b - K phi1, scales, input features and
-// (when phi_t is given) targets.  Each input is scaled by its own rms so the
-// BF16 activations resolve it (phi1 and phi2 differ by far less than their size).
+// Input features: residual r = b - K phi1, increment phi1 - phi2, b and the
+// coordinates, and (when phi_t is given) the target.  Each input is scaled
+// by its own rms so the BF16 activations resolve it (phi1 and phi2 differ by
+// far less than their size).
 __device__ __forceinline__ double residual_row(int i, const int* __restrict__ rowptr, const int* __restrict__ col,
                                                const double* __restrict__ K, const double* __restrict__ b,
                                                const double* __restrict__ phi1) {
@@ -128,53 +151,111 @@ __device__ __forceinline__ double residual_row(int i, const int* __restrict__ ro
   return b[i] - s;
 }
 
-__global__ void features_kernel(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
-                                const double* __restrict__ K, const double* __restrict__ b,
-                                const double* __restrict__ phi1, const double* __restrict__ phi2,
-                                const double* __restrict__ phi_t, const double2* __restrict__ xy,
-                                float* __restrict__ f, double* __restrict__ scale, float* __restrict__ target) {
-  __shared__ double red[3][32];
-  __shared__ double sc[3];
-  const int s = blockIdx.x;
-  const size_t base = (size_t)s * n;
-  const double* bs = b + base;
-  const double* p1 = phi1 + base;
+// Input scales in one fixed reduction order, shared by the batched forward
+// and the fused inference kernel so both produce the same bits.  Chunk c of a
+// sample holds rows [c TILE, (c+1) TILE); thread t < TILE takes row
+// c TILE + t.  A chunk's partial sums of r^2, d^2 and b^2 are warp
+// butterflies added over the warps in order; a sample's totals add the chunk
+// partials per lane (chunks lane, lane + 32, ...) and finish with a butterfly.
+__device__ __forceinline__ void chunk_partials(int n, int c, const int* __restrict__ rowptr,
+                                               const int* __restrict__ col, const double* __restrict__ K,
+                                               const double* __restrict__ bs, const double* __restrict__ p1,
+                                               const double* __restrict__ p2, double* red, double* out,
+                                               double* __restrict__ r_out) {
+  const int t = threadIdx.x, i = c * TILE + t, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
   double v[3] = {0.0, 0.0, 0.0};
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  if (t < TILE && i < n) {
     const double r = residual_row(i, rowptr, col, K, bs, p1);
-    const double dd = p1[i] - phi2[base + i];
-    v[0] = fma(r, r, v[0]);
-    v[1] = fma(dd, dd, v[1]);
-    v[2] = fma(bs[i], bs[i], v[2]);
+    if (r_out) r_out[i] = r;
+    const double dd = p1[i] - p2[i];
+    v[0] = r * r;
+    v[1] = dd * dd;
+    v[2] = bs[i] * bs[i];
   }
-  for (int c = 0; c < 3; ++c) {
-    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
-    if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v[c];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0) red[q * 32 + warp] = v[q];
   }
   __syncthreads();
+  if (t < 3) {   // one thread per component, warps in order
+    double a = 0.0;
+    for (int w = 0; w < nw; ++w) a += red[t * 32 + w];
+    out[t] = a;
+  }
+  __syncthreads();
+}
+
+// Warp 0: the sample's scales sc[q] = sqrt(total_q / n) (1 when zero) from its
+// C chunk partials, and their inverses isc[q] = 1 / sc[q].
+__device__ __forceinline__ void sample_scales(int n, int C, const double* __restrict__ part, double* sc, double* isc) {
   if (threadIdx.x < 32) {
-    for (int c = 0; c < 3; ++c) {
-      double t = threadIdx.x < (blockDim.x >> 5) ? red[c][threadIdx.x] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (threadIdx.x == 0) {
-        const double rr = sqrt(t / n);
-        sc[c] = rr > 1e-30 ? rr : 1.0;
+    const int lane = threadIdx.x;
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int ch = lane; ch < C; ch += 32) {
+      const double v0 = __ldcg(part + ch * 3), v1 = __ldcg(part + ch * 3 + 1), v2 = __ldcg(part + ch * 3 + 2);
+      a[0] += v0;
+      a[1] += v1;
+      a[2] += v2;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
+      if (lane == q) {   // three lanes, one scale each
+        const double rr = sqrt(a[q] / n);
+        sc[q] = rr > 1e-30 ? rr : 1.0;
+        isc[q] = 1.0 / sc[q];
       }
     }
-    if (threadIdx.x == 0) scale[s] = sc[1];
   }
   __syncthreads();
-  const double ir = 1.0 / sc[0], id = 1.0 / sc[1], ib = 1.0 / sc[2];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double2 p = xy[i];
-    float* fi = f + (base + i) * FIN;
-    fi[0] = (float)(residual_row(i, rowptr, col, K, bs, p1) * ir);
-    fi[1] = (float)((p1[i] - phi2[base + i]) * id);
-    fi[2] = (float)(bs[i] * ib);
-    fi[3] = (float)(p.x / 15.0);
-    fi[4] = (float)(p.y / 15.0);
-    if (phi_t) target[base + i] = (float)((phi_t[base + i] - p1[i]) * id);
-  }
+}
+
+// Features of row i with residual r (and its target when phi_t is given), scales inverted by the caller.
+__device__ __forceinline__ void features_row(int i, double r, const double* __restrict__ bs,
+                                             const double* __restrict__ p1, const double* __restrict__ p2,
+                                             const double* __restrict__ pt, const double2* __restrict__ xy,
+                                             double ir, double id, double ib, float* __restrict__ fi,
+                                             float* __restrict__ ti) {
+  const double2 p = xy[i];
+  fi[0] = (float)(r * ir);
+  fi[1] = (float)((p1[i] - p2[i]) * id);
+  fi[2] = (float)(bs[i] * ib);
+  fi[3] = (float)(p.x / 15.0);
+  fi[4] = (float)(p.y / 15.0);
+  if (pt) *ti = (float)((pt[i] - p1[i]) * id);
+}
+
+// Batched forward, first pass: partial sums of every (sample, chunk).
+__global__ void features_partial_kernel(int n, int C, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                        const double* __restrict__ K, const double* __restrict__ b,
+                                        const double* __restrict__ phi1, const double* __restrict__ phi2,
+                                        double* __restrict__ part) {
+  __shared__ double red[3 * 32];
+  const int s = blockIdx.x / C, c = blockIdx.x % C;
+  const size_t base = (size_t)s * n;
+  __shared__ double out[3];
+  chunk_partials(n, c, rowptr, col, K, b + base, phi1 + base, phi2 + base, red, out, nullptr);
+  if (threadIdx.x < 3) part[((size_t)s * C + c) * 3 + threadIdx.x] = out[threadIdx.x];
+}
+
+// Batched forward, second pass: scales, input features and (when phi_t is given) targets.
+__global__ void features_rows_kernel(int n, int C, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                     const double* __restrict__ K, const double* __restrict__ b,
+                                     const double* __restrict__ phi1, const double* __restrict__ phi2,
+                                     const double* __restrict__ phi_t, const double2* __restrict__ xy,
+                                     const double* __restrict__ part, float* __restrict__ f,
+                                     double* __restrict__ scale, float* __restrict__ target) {
+  __shared__ double sc[3], isc[3];
+  const int s = blockIdx.x / C, c = blockIdx.x % C;
+  const size_t base = (size_t)s * n;
+  sample_scales(n, C, part + (size_t)s * C * 3, sc, isc);
+  if (c == 0 && threadIdx.x == 0) scale[s] = sc[1];
+  const double ir = isc[0], id = isc[1], ib = isc[2];
+  const int i = c * TILE + threadIdx.x;
+  if (threadIdx.x < TILE && i < n)
+    features_row(i, residual_row(i, rowptr, col, K, b + base, phi1 + base), b + base, phi1 + base, phi2 + base,
+                 phi_t ? phi_t + base : nullptr, xy, ir, id, ib, f + (base + i) * FIN, target + base + i);
 }
 
 __global__ void encode_kernel(int rows, const float* __restrict__ P, const float* __restrict__ f,
@@ -318,6 +399,292 @@ __global__ void decode_kernel(int rows, int n, const float* __restrict__ P, cons
   for (int k = 0; k < H; ++k) o = fmaf(P[OFF_WD + k], __bfloat162float(hr[k]), o);
   out[r] = o;
   if (x0) x0[r] = phi1[r] + scale[r / n] * (double)o;
+}
+
+// ---------------------------------------------------------------------------
+// fused inference: the whole forward of one sample in one cooperative launch
+// ---------------------------------------------------------------------------
+struct InferArgs {
+  int n, C;
+  const int* rowptr;
+  const int* col;
+  const double* K;
+  const double* b;
+  const double* phi1;
+  const double* phi2;
+  const double2* xy;
+  const int* dst;
+  const int* src;
+  const int* in_ptr;
+  const bf16* ef;
+  const float* P;
+  const bf16* Wm;
+  const bf16* Wu;
+  bf16* h;        // [NL + 1][n][H]
+  bf16* msg;      // [E][H]
+  float* f;       // [n][FIN]
+  double* part;   // [C][3]
+  double* res;    // [n] residual b - K phi1 of the first phase
+  double* scale;  // [1]
+  float* out;     // [n]
+  double* x0;     // [n]
+  unsigned* bar;
+  int* timeout;
+  long long spin_ns;
+};
+
+// Layers and decoder work on node chunks of NT nodes (block b takes chunks b,
+// b + grid, ...); a chunk's in-edges are contiguous in CSR order and run
+// through the message tile 128 at a time, each message tile's rows added in
+// edge order into FP32 aggregates in shared memory.  The input scales use
+// the 128-row chunks of the shared reduction order.  Four grid barriers:
+// after the scale partials, after the encoder and after each of the first
+// two layers (a layer reads the previous layer's h of neighbouring chunks;
+// the decoder only its own).  Every step runs the same arithmetic in the
+// same order as the batched kernels (features, encode, message_fwd,
+// aggregate, update_fwd, decode), so the result is the same bits.  A
+// barrier that gives up writes NaN to the block's x0 rows.
+constexpr int NT = 16;    // nodes per inference chunk (one 16-row update tile)
+constexpr int EIC = 256;  // in-edge indices of a chunk kept in shared memory (more are read from global)
+constexpr size_t kInferSmem = (size_t)NL * H * (LDM + LDU) * sizeof(bf16)   // all dense weights
+                              + (size_t)TILE * LDM * sizeof(bf16)         // message / update tile
+                              + (size_t)NT * H * sizeof(bf16)             // the chunk's own h
+                              + (size_t)NT * H * sizeof(float)            // FP32 aggregates
+                              + (size_t)2 * EIC * sizeof(int);            // dst, src of the chunk's in-edges
+
+__global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bf16* Wms = reinterpret_cast<bf16*>(smem);               // [NL][H][LDM]
+  bf16* Wus = Wms + NL * H * LDM;                          // [NL][H][LDU]
+  bf16* X = Wus + NL * H * LDU;                            // [TILE][LDM] or [NT][LDU]
+  bf16* Hs = X + TILE * LDM;                               // [NT][H]
+  float* agg = reinterpret_cast<float*>(Hs + NT * H);      // [NT][H]
+  int* dsts = reinterpret_cast<int*>(agg + NT * H);        // [EIC]
+  int* srcs = dsts + EIC;                                  // [EIC]
+  __shared__ double red[3 * 32];
+  __shared__ double sc[3], isc[3];
+  __shared__ float bias[NL][2][H];   // bm, bu of every layer
+  __shared__ int iptr[NT + 1];       // in-edge offsets of the (single) chunk
+  __shared__ int ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
+  const int n = a.n, C = a.C, CN = (n + NT - 1) / NT;
+  unsigned epoch = 0;
+  auto gsync = [&]() -> bool {
+    __syncthreads();
+    ++epoch;
+    if (tid == 0) ok = barrier_arrive_wait(a.bar, a.timeout, gridDim.x, epoch, a.spin_ns) ? 1 : 0;
+    __syncthreads();
+    return ok != 0;
+  };
+  auto give_up = [&]() {
+    for (int c = blockIdx.x; c < CN; c += gridDim.x) {
+      const int i = c * NT + tid;
+      if (tid < NT && i < n) a.x0[i] = __longlong_as_double(0x7FF8000000000000LL);
+    }
+  };
+  // all dense weights to shared memory once, by asynchronous 16-byte copies
+  // that complete while the first two phases run (waited for before layer 0)
+  {
+    constexpr int NM = NL * H * KMP / 8, NU = NL * H * KU / 8;
+    for (int i = tid; i < NM + NU; i += blockDim.x) {
+      const bf16* src;
+      bf16* dstp;
+      if (i < NM) {
+        const int lo = i / (KMP / 8), k8 = i % (KMP / 8);   // lo = layer * H + output
+        src = a.Wm + (size_t)i * 8;
+        dstp = Wms + lo * LDM + k8 * 8;
+      } else {
+        const int j = i - NM, lo = j / (KU / 8), k8 = j % (KU / 8);
+        src = a.Wu + (size_t)j * 8;
+        dstp = Wus + lo * LDU + k8 * 8;
+      }
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(dstp);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int i = tid; i < NL * 2 * H; i += blockDim.x) {
+      const int l = i / (2 * H), w = (i / H) % 2, ch = i % H;
+      bias[l][w][ch] = a.P[layer_off(l) + (w == 0 ? L_BM : L_BU) + ch];
+    }
+  }
+  // ---- scale partials (128-row chunks) ----
+  for (int c = blockIdx.x; c < C; c += gridDim.x) {
+    chunk_partials(n, c, a.rowptr, a.col, a.K, a.b, a.phi1, a.phi2, red, sc, a.res);
+    if (tid < 3) a.part[c * 3 + tid] = sc[tid];
+    __syncthreads();
+  }
+  // a block with a single node chunk keeps its in-edge indices for all layers
+  const bool one_chunk = CN <= (int)gridDim.x;
+  auto load_edges = [&](int c) {
+    const int n0 = c * NT, cnt = min(NT, n - n0);
+    if (tid <= cnt) iptr[tid] = a.in_ptr[n0 + tid];
+    const int e0 = a.in_ptr[n0], e1 = a.in_ptr[n0 + cnt];
+    for (int e = e0 + tid; e < min(e1, e0 + EIC); e += blockDim.x) {
+      dsts[e - e0] = a.dst[e];
+      srcs[e - e0] = a.src[e];
+    }
+  };
+  if (one_chunk && (int)blockIdx.x < CN) load_edges(blockIdx.x);
+  if (!gsync()) { give_up(); return; }
+  sample_scales(n, C, a.part, sc, isc);
+  if (blockIdx.x == 0 && tid == 0) a.scale[0] = sc[1];
+  // ---- features and encoder of the block's node chunks ----
+  {
+    const double ir = isc[0], id = isc[1], ib = isc[2];
+    __shared__ float fs[NT * FIN];
+    for (int c = blockIdx.x; c < CN; c += gridDim.x) {
+      const int i = c * NT + tid;
+      if (tid < NT && i < n)
+        features_row(i, __ldcg(a.res + i), a.b, a.phi1, a.phi2, nullptr, a.xy, ir, id, ib, fs + tid * FIN, nullptr);
+      __syncthreads();
+      const int cnt = min(NT, n - c * NT);
+      for (int t = tid; t < cnt * H; t += blockDim.x) {
+        const int rr = t / H, ch = t % H;
+        const float* w = a.P + OFF_WE + ch * FIN;
+        float z = a.P[OFF_BE + ch];
+#pragma unroll
+        for (int k = 0; k < FIN; ++k) z = fmaf(w[k], fs[rr * FIN + k], z);
+        a.h[(size_t)(c * NT + rr) * H + ch] = __float2bfloat16_rn(fmaxf(z, 0.0f));
+      }
+      __syncthreads();
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's weight copies; gsync makes all visible
+  if (!gsync()) { give_up(); return; }
+  // ---- message-passing layers ----
+  for (int l = 0; l < NL; ++l) {
+    const bf16* hin = a.h + (size_t)l * n * H;
+    bf16* hout = a.h + (size_t)(l + 1) * n * H;
+    const float* bm = bias[l][0];
+    const float* bu = bias[l][1];
+    const bf16* W = Wms + l * H * LDM;
+    const bf16* Wu = Wus + l * H * LDU;
+    for (int c = blockIdx.x; c < CN; c += gridDim.x) {
+      const int n0 = c * NT, n1 = min(n, n0 + NT);
+      if (!one_chunk) {
+        load_edges(c);
+        __syncthreads();
+      }
+      const int e0 = iptr[0], e1 = iptr[n1 - n0];
+      for (int i = tid; i < NT * H; i += blockDim.x) agg[i] = 0.0f;
+      // the chunk's own h rows, for the update: loaded now, stored with the first message tile
+      static_assert(NT * 8 <= 256, "one 16-byte piece of the chunk's rows per thread");
+      uint4 hsv = make_uint4(0u, 0u, 0u, 0u);
+      if (tid < NT * 8 && n0 + tid / 8 < n1) hsv = *reinterpret_cast<const uint4*>(hin + (size_t)(n0 + tid / 8) * H + (tid % 8) * 8);
+      bool hs_done = false;
+      // messages of the chunk's in-edges, TILE at a time, summed in edge order
+      for (int t0 = e0; t0 < e1; t0 += TILE) {
+        const int rows = min(TILE, e1 - t0);
+        {
+          constexpr int PER = TILE * 18 / 256;   // 16-byte pieces per thread, all loads in flight at once
+          uint4 v[PER];
+#pragma unroll
+          for (int q = 0; q < PER; ++q) {
+            const int i = q * 256 + tid, rr = i / 18, piece = i % 18, e = t0 + rr;
+            v[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (rr < rows) {
+              const int el = e - e0;
+              if (piece < 8) {
+                const int j = el < EIC ? dsts[el] : a.dst[e];
+                v[q] = *reinterpret_cast<const uint4*>(hin + (size_t)j * H + piece * 8);
+              } else if (piece < 16) {
+                const int j = el < EIC ? srcs[el] : a.src[e];
+                v[q] = *reinterpret_cast<const uint4*>(hin + (size_t)j * H + (piece - 8) * 8);
+              } else if (piece == 16) {
+                const uint2 w2 = *reinterpret_cast<const uint2*>(a.ef + 4 * (size_t)e);
+                v[q] = make_uint4(w2.x, w2.y & 0xffffu, 0u, 0u);
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < PER; ++q) {
+            const int i = q * 256 + tid, rr = i / 18, piece = i % 18;
+            *reinterpret_cast<uint4*>(X + rr * LDM + piece * 8) = v[q];
+          }
+          if (!hs_done && tid < NT * 8) *reinterpret_cast<uint4*>(Hs + (tid / 8) * H + (tid % 8) * 8) = hsv;
+          hs_done = true;
+        }
+        __syncthreads();
+        if (warp * 16 < rows) {   // each warp reads and then overwrites only its own 16 rows
+          float acc[8][4];
+#pragma unroll
+          for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+          warp_tile_mma<KMP>(X + warp * 16 * LDM, LDM, W, LDM, acc);
+          __syncwarp();
+#pragma unroll
+          for (int nt = 0; nt < 8; ++nt) {
+            const int ch = nt * 8 + tig * 2;
+            const float b0 = bm[ch], b1 = bm[ch + 1];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              const int rr = warp * 16 + gid + half * 8;
+              __nv_bfloat162 v;
+              v.x = __float2bfloat16_rn(fmaxf(acc[nt][2 * half] + b0, 0.0f));
+              v.y = __float2bfloat16_rn(fmaxf(acc[nt][2 * half + 1] + b1, 0.0f));
+              *reinterpret_cast<__nv_bfloat162*>(X + rr * LDM + ch) = v;
+            }
+          }
+        }
+        __syncthreads();
+        // add this tile's messages into the aggregates of their destinations, in edge order
+        for (int i = tid; i < NT * H; i += blockDim.x) {
+          const int rr = i / H, ch = i % H, node = n0 + rr;
+          if (node < n1) {
+            const int lo = max(iptr[rr], t0), hi = min(iptr[rr + 1], t0 + rows);
+            float s = agg[i];
+            for (int e = lo; e < hi; ++e) s += __bfloat162float(X[(e - t0) * LDM + ch]);
+            agg[i] = s;
+          }
+        }
+        __syncthreads();
+      }
+      // update of the chunk's nodes: [h | bf16(a)] x Wu, warp w computing outputs 8w .. 8w+7
+      if (!hs_done && tid < NT * 8) *reinterpret_cast<uint4*>(Hs + (tid / 8) * H + (tid % 8) * 8) = hsv;
+      __syncthreads();   // Hs and agg complete (also when the chunk has no in-edges)
+      for (int i = tid; i < NT * 8; i += blockDim.x) {
+        const int rr = i / 8, piece = i % 8;
+        *reinterpret_cast<uint4*>(X + rr * LDU + piece * 8) = *reinterpret_cast<const uint4*>(Hs + rr * H + piece * 8);
+      }
+      for (int i = tid; i < NT * H; i += blockDim.x) X[(i / H) * LDU + H + (i % H)] = __float2bfloat16_rn(agg[i]);
+      __syncthreads();
+      {
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        warp_tile_mma_nt<KU>(X, LDU, Wu, LDU, warp, acc);
+        const int ch = warp * 8 + tig * 2;
+        const float b0 = bu[ch], b1 = bu[ch + 1];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int rr = gid + half * 8, node = n0 + rr;
+          if (node < n1) {
+            const float u0 = acc[2 * half] + b0, u1 = acc[2 * half + 1] + b1;
+            const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162*>(Hs + rr * H + ch);
+            __nv_bfloat162 o;
+            o.x = __float2bfloat16_rn(__bfloat162float(hv.x) + fmaxf(u0, 0.0f));
+            o.y = __float2bfloat16_rn(__bfloat162float(hv.y) + fmaxf(u1, 0.0f));
+            *reinterpret_cast<__nv_bfloat162*>(hout + (size_t)node * H + ch) = o;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (l + 1 < NL && !gsync()) { give_up(); return; }
+  }
+  // ---- decoder of the block's own nodes ----
+  const bf16* hl = a.h + (size_t)NL * n * H;
+  for (int c = blockIdx.x; c < CN; c += gridDim.x) {
+    const int i = c * NT + tid;
+    if (tid < NT && i < n) {
+      uint4 hv[H / 8];
+#pragma unroll
+      for (int q = 0; q < H / 8; ++q) hv[q] = *reinterpret_cast<const uint4*>(hl + (size_t)i * H + q * 8);
+      const bf16* hr = reinterpret_cast<const bf16*>(hv);
+      float o = a.P[OFF_BD];
+#pragma unroll
+      for (int k = 0; k < H; ++k) o = fmaf(a.P[OFF_WD + k], __bfloat162float(hr[k]), o);
+      a.out[i] = o;
+      a.x0[i] = a.phi1[i] + sc[1] * (double)o;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -551,6 +918,10 @@ struct cgp_gnn_s {
   bf16 *h = nullptr, *msg = nullptr, *agg = nullptr;
   float *dh = nullptr, *dh2 = nullptr, *du = nullptr, *da = nullptr, *dz = nullptr, *dxe = nullptr, *part = nullptr;
   size_t part_floats = 0;
+  double* fpart = nullptr;        // [max_batch][C][3] partial sums of the input scales
+  double* rres = nullptr;         // [n] fused inference: residual b - K phi1
+  unsigned char* ictrl = nullptr; // fused inference: barrier counter and timeout word
+  int infer_grid = 0;             // co-resident blocks of the fused inference kernel (capped by the chunk count)
 };
 
 namespace {
@@ -567,8 +938,10 @@ int gnn_forward(cgp_gnn_s* g, int B, const double* b, const double* phi1, const 
                 double* x0, cudaStream_t s) {
   const int n = g->n, E = g->E, rn = B * n, re = B * E;
   const double2* xy = reinterpret_cast<const double2*>(g->m->xy_c);
-  features_kernel<<<B, 256, 0, s>>>(n, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, phi_t, xy, g->f, g->scale,
-                                   g->target);
+  const int C = (n + TILE - 1) / TILE;
+  features_partial_kernel<<<B * C, 256, 0, s>>>(n, C, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, g->fpart);
+  features_rows_kernel<<<B * C, 256, 0, s>>>(n, C, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, phi_t, xy,
+                                             g->fpart, g->f, g->scale, g->target);
   encode_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, g->P, g->f, g->z0, g->h);
   const size_t smem_m = (size_t)(H + TILE) * LDM * sizeof(bf16), smem_u = (size_t)(H + TILE) * LDU * sizeof(bf16);
   for (int l = 0; l < NL; ++l) {
@@ -703,7 +1076,8 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
                o_h = take((size_t)(NL + 1) * rn * H * 2), o_msg = take((size_t)NL * re * H * 2),
                o_agg = take((size_t)NL * rn * H * 2), o_dh = take(rn * H * 4), o_dh2 = take(rn * H * 4),
                o_du = take(rn * H * 4), o_da = take(rn * H * 4), o_dz = take(re * H * 4), o_dxe = take(re * KU * 4),
-               o_part = take(g->part_floats * 4);
+               o_part = take(g->part_floats * 4), o_fpart = take(B * (size_t)((n + TILE - 1) / TILE) * 3 * 8),
+               o_ictrl = take(256), o_rres = take((size_t)n * 8);
   g->bytes = off;
   cudaError_t e = cudaMalloc(&g->base, g->bytes);
   if (e != cudaSuccess) {
@@ -742,6 +1116,9 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   g->dz = (float*)(bs + o_dz);
   g->dxe = (float*)(bs + o_dxe);
   g->part = (float*)(bs + o_part);
+  g->fpart = (double*)(bs + o_fpart);
+  g->ictrl = (unsigned char*)(bs + o_ictrl);
+  g->rres = (double*)(bs + o_rres);
   auto up = [&](void* d, const void* h, size_t bytes) -> int {
     cudaError_t ee = cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice);
     return ee == cudaSuccess ? CGP_OK : cuda_fail(ee, "cudaMemcpy(gnn)");
@@ -766,6 +1143,18 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   if (st == CGP_OK) st = smem_optin((const void*)wgrad_update_kernel, (size_t)WG_ROWS * (H + KU + 1) * sizeof(float));
   if (st == CGP_OK) st = smem_optin((const void*)update_bwd_kernel, (size_t)H * KU * sizeof(float));
   if (st == CGP_OK) st = smem_optin((const void*)message_bwd_kernel, (size_t)H * KU * sizeof(float));
+  if (st == CGP_OK) st = smem_optin((const void*)infer_kernel, kInferSmem);
+  if (st == CGP_OK) {
+    int per_sm = 0, sms = 0;
+    cudaError_t ee = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)infer_kernel, 256, kInferSmem);
+    if (ee == cudaSuccess) ee = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (ee != cudaSuccess || per_sm < 1) {
+      st = ee != cudaSuccess ? cuda_fail(ee, "gnn: occupancy of the inference kernel")
+                             : fail(CGP_ERR_CUDA, "gnn: inference kernel cannot be resident");
+    } else {
+      g->infer_grid = std::min(per_sm * sms, (n + NT - 1) / NT);
+    }
+  }
   if (st == CGP_OK) {
     cudaError_t ee = cudaDeviceSynchronize();
     if (ee != cudaSuccess) st = cuda_fail(ee, "gnn set-up kernels");
@@ -800,7 +1189,39 @@ extern "C" int cgp_gnn_get_params(cgp_gnn g, float* params) {
 extern "C" int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, const double* phi2, double* x0,
                                void* stream) {
   if (!g || !b || !phi1 || !phi2 || !x0) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_predict: NULL argument");
-  return gnn_forward(g, 1, b, phi1, phi2, nullptr, x0, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  InferArgs a{};
+  a.n = g->n;
+  a.C = (g->n + TILE - 1) / TILE;
+  a.rowptr = g->m->rowptr;
+  a.col = g->m->col;
+  a.K = g->m->K;
+  a.b = b;
+  a.phi1 = phi1;
+  a.phi2 = phi2;
+  a.xy = reinterpret_cast<const double2*>(g->m->xy_c);
+  a.dst = g->dst;
+  a.src = g->src;
+  a.in_ptr = g->in_ptr;
+  a.ef = g->ef;
+  a.P = g->P;
+  a.Wm = g->Wm;
+  a.Wu = g->Wu;
+  a.h = g->h;
+  a.msg = g->msg;
+  a.f = g->f;
+  a.part = g->fpart;
+  a.res = g->rres;
+  a.scale = g->scale;
+  a.out = g->out;
+  a.x0 = x0;
+  a.bar = reinterpret_cast<unsigned*>(g->ictrl);
+  a.timeout = reinterpret_cast<int*>(g->ictrl + 128);
+  a.spin_ns = 2000000000LL;
+  CGP_CUDA(cudaMemsetAsync(g->ictrl, 0, 256, s));
+  void* args[] = {&a};
+  CGP_CUDA(cudaLaunchCooperativeKernel((const void*)infer_kernel, dim3(g->infer_grid), dim3(256), args, kInferSmem, s));
+  return CGP_OK;
 }
 
 extern "C" int cgp_gnn_gradients(cgp_gnn g, int batch, const double* b, const double* phi1, const double* phi2,

@@ -37,6 +37,7 @@
 
 #include "cgp_fixed.h"
 #include "cgp_internal.h"
+#include "cgp_sync.h"
 
 namespace cgp {
 namespace {
@@ -81,18 +82,6 @@ struct Desc {
   long long spin_ns;
 };
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 template <typename V>
 __device__ __forceinline__ V warp_sum(V v) {
 #pragma unroll
@@ -113,21 +102,8 @@ struct Shared {
   int flag;
 };
 
-// Barrier over the blocks of one instance: arrival is a release-add on a
-// counter that only grows; a block waits until the counter reaches
-// epoch * nblk, polling with relaxed loads and finishing with an acquire.
-// The wait gives up after spin_ns of wall-clock time, or as soon as another
-// block has given up, and then reports failure.
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
+// Barrier over the blocks of one instance (cgp_sync.h): a block that gives
+// up makes every other block leave at its next barrier.
 struct Group {
   unsigned* bar;
   int* timeout;
@@ -139,28 +115,7 @@ struct Group {
     __syncthreads();
     if (nblk == 1) return true;
     ++epoch;
-    if (threadIdx.x == 0) {
-      int ok = 1;
-      red_release_add(bar, 1u);
-      const unsigned target = epoch * nblk;
-      unsigned long long t0 = 0;
-      unsigned spins = 0;
-      while (ld_relaxed(bar) < target) {
-        if ((++spins & 127u) == 0) {
-          if (*(volatile int*)timeout) { ok = 0; break; }
-          const unsigned long long now = global_ns();
-          if (t0 == 0) {
-            t0 = now;
-          } else if ((long long)(now - t0) > spin_ns) {
-            atomicExch(timeout, 1);
-            ok = 0;
-            break;
-          }
-        }
-      }
-      if (ok) (void)ld_acquire(bar);
-      sh.flag = ok;
-    }
+    if (threadIdx.x == 0) sh.flag = barrier_arrive_wait(bar, timeout, nblk, epoch, spin_ns) ? 1 : 0;
     __syncthreads();
     return sh.flag != 0;
   }
@@ -709,6 +664,7 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
   double* const S1 = d.pub64 + 5 * n;
 
   double *x, *r, *u, *w, *p, *s, *bp, *ext = nullptr;
+  double *stR = nullptr, *stW = nullptr, *stS = nullptr;  // RES: staged halo r, w, s of the next iteration
   const double* di;
   const double* dih = nullptr;  // RES: D^-1 of the halo rows
   const int* hid = nullptr;     // RES: global index of each halo slot
@@ -727,7 +683,10 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
     ext = base + 8 * chunk;                  // [chunk + halo_cap]: own u, then gathered halo u
     double* dh = ext + chunk + d.halo_cap;   // [halo_cap]
     double* val = dh + d.halo_cap;           // [nnz_cap]
-    int* row = reinterpret_cast<int*>(val + d.res_nnz_cap);
+    stR = val + d.res_nnz_cap;               // [halo_cap] each
+    stW = stR + d.halo_cap;
+    stS = stW + d.halo_cap;
+    int* row = reinterpret_cast<int*>(stS + d.halo_cap);
     int* col = row + chunk + 1;
     int* hd = col + d.res_nnz_cap;
     const int k0 = nloc > 0 ? d.rowptr[r0] : 0;
@@ -865,6 +824,23 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       put_partials<3>(d, lb, red, v3, sh);
       if (!grp.sync(sh)) return;
     }
+    // RES: while warps 0-2 fetch the reduction's totals, the other warps stage the
+    // halo inputs r_j, w_j, s_j of the coming iteration (they do not depend on the
+    // scalars), so the two global round trips overlap
+    constexpr int TW = 3 * 32;
+    const bool staged = RES && bd > TW;
+    auto stage = [&](int kk) {
+      if (!staged || tid < TW) return;
+      const double* Rc = (kk & 1) ? R1 : R0;
+      const double* Wc = (kk & 1) ? W1 : W0;
+      const double* Sc = (kk & 1) ? S1 : S0;
+      for (int h = tid - TW; h < nh; h += bd - TW) {
+        const int j = hid[h];
+        stR[h] = __ldcg(Rc + j);
+        stW[h] = __ldcg(Wc + j);
+        if (kk > 0) stS[h] = __ldcg(Sc + j);
+      }
+    };
     // scalars (thread 0): sc[0] alpha, sc[1] beta, sc[2] gamma, sc[5] (r,r), isc[0] stop flag;
     // sc[3] = 1 / gamma_old and sc[6] = 1 / alpha_old are prepared off the critical path
     int k = 0;
@@ -888,6 +864,7 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       S.sc[2] = g;
       S.sc[5] = rr;
     };
+    stage(0);
     get_totals_then<3>(d, red, sh, derive);
     ++red;
     while (true) {
@@ -928,7 +905,14 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
         return dj * fma(-alpha, sj, __ldcg(Rc + j));
       };
       if constexpr (RES) {
-        for (int h = tid; h < nh; h += bd) ext[nloc + h] = halo_u(hid[h], dih[h]);
+        if (staged) {
+          for (int h = tid; h < nh; h += bd) {
+            const double sj = k == 0 ? stW[h] : fma(beta, stS[h], stW[h]);
+            ext[nloc + h] = dih[h] * fma(-alpha, sj, stR[h]);
+          }
+        } else {
+          for (int h = tid; h < nh; h += bd) ext[nloc + h] = halo_u(hid[h], dih[h]);
+        }
       }
       __syncthreads();
       double v3[3] = {0.0, 0.0, 0.0};
@@ -949,6 +933,7 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       put_partials<3>(d, lb, red, v3, sh);
       if (!grp.sync(sh)) return;
       ++k;
+      stage(k);
       get_totals_then<3>(d, red, sh, derive);
       ++red;
     }
@@ -1091,6 +1076,7 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
   float* const S1 = d.f32pub + 5 * n;
   // own inner vectors and the local system
   float *ir, *iu, *iw, *ip, *is, *ie, *ext = nullptr, *dih = nullptr;
+  float *stR = nullptr, *stW = nullptr, *stS = nullptr;   // RES: staged halo r, w, s of the next iteration
   const float* di;
   const int *row, *col, *hid = nullptr;
   const float* val;
@@ -1107,7 +1093,10 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
     ext = f + 7 * chunk;                   // [chunk + halo_cap]
     dih = ext + chunk + d.halo_cap;        // [halo_cap]
     float* vl = dih + d.halo_cap;          // [nnz_cap]
-    int* rw = reinterpret_cast<int*>(vl + d.res_nnz_cap);
+    stR = vl + d.res_nnz_cap;              // [halo_cap] each
+    stW = stR + d.halo_cap;
+    stS = stW + d.halo_cap;
+    int* rw = reinterpret_cast<int*>(stS + d.halo_cap);
     int* cl = rw + chunk + 1;
     int* hd = cl + d.res_nnz_cap;
     const int k0 = nloc > 0 ? d.rowptr[r0] : 0;
@@ -1281,6 +1270,23 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
       const double floor = 0.5 * d.tol * bnorm;
       sh.fsc[5] = (float)(floor * floor);
     }
+    // RES: while warp 0 fetches the reduction's totals, the other warps stage
+    // the halo inputs r_j, w_j, s_j of the coming iteration, so the two global
+    // round trips overlap
+    const bool staged = RES && bd > 32;
+    auto stage = [&](int kk) {
+      if (!staged || tid < 32) return;
+      const float* Rc = (kk & 1) ? R1 : R0;
+      const float* Wc = (kk & 1) ? W1 : W0;
+      const float* Sc = (kk & 1) ? S1 : S0;
+      for (int h = tid - 32; h < nh; h += bd - 32) {
+        const int j = hid[h];
+        stR[h] = __ldcg(Rc + j);
+        stW[h] = __ldcg(Wc + j);
+        if (kk > 0) stS[h] = __ldcg(Sc + j);
+      }
+    };
+    stage(0);
     get_totals_f_then<3>(d, red, sh, derive);
     ++red;
     bool bad = false;
@@ -1317,7 +1323,14 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
         return dj * fmaf(-alpha, sj, __ldcg(Rc + j));
       };
       if constexpr (RES) {
-        for (int h = tid; h < nh; h += bd) ext[nloc + h] = halo_u(hid[h], dih[h]);
+        if (staged) {
+          for (int h = tid; h < nh; h += bd) {
+            const float sj = k == 0 ? stW[h] : fmaf(beta, stS[h], stW[h]);
+            ext[nloc + h] = dih[h] * fmaf(-alpha, sj, stR[h]);
+          }
+        } else {
+          for (int h = tid; h < nh; h += bd) ext[nloc + h] = halo_u(hid[h], dih[h]);
+        }
       }
       __syncthreads();
       float v3[3] = {0.0f, 0.0f, 0.0f};
@@ -1338,6 +1351,7 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
       put_partials_f<3>(d, lb, red, v3, sh);
       if (!grp.sync(sh)) return;
       ++k;
+      stage(k);
       get_totals_f_then<3>(d, red, sh, derive);
       ++red;
     }
@@ -1547,17 +1561,18 @@ SolverKind solver_kind(bool mixed, int flags) {
 // Dynamic shared memory of a block that keeps its rows resident: the classic
 // FP64 solver needs seven vectors, the halo buffer and an FP64 CSR slice; the
 // single-reduction FP64 solver eight vectors, the halo buffer, D^-1 of the
-// halo and the slice; the mixed solver six FP32 vectors, D^-1, the halo
-// buffer and D^-1 of the halo, and an FP32 slice.
+// halo, three staging buffers of the halo and the slice; the mixed solver six
+// FP32 vectors, D^-1, the halo buffer, D^-1 of the halo, three staging
+// buffers and an FP32 slice.
 size_t res_smem_bytes(SolverKind kind, int chunk, const HaloPlan& hp) {
   const size_t ints = 4 * ((size_t)chunk + 1 + hp.max_nnz + hp.max_halo);
   size_t s = 0;
   if (kind == KIND_MIXED)
-    s = 4 * ((size_t)9 * chunk + 3 * (size_t)hp.max_halo + 2 * (size_t)hp.max_nnz + 1);
+    s = 4 * ((size_t)9 * chunk + 6 * (size_t)hp.max_halo + 2 * (size_t)hp.max_nnz + 1);
   else if (kind == KIND_FP64_CLASSIC)
     s = 8 * ((size_t)7 * chunk + hp.max_halo + hp.max_nnz) + ints;
   else
-    s = 8 * ((size_t)9 * chunk + 2 * (size_t)hp.max_halo + hp.max_nnz) + ints;
+    s = 8 * ((size_t)9 * chunk + 5 * (size_t)hp.max_halo + hp.max_nnz) + ints;
   return (s + 15) / 16 * 16;
 }
 
@@ -1582,13 +1597,10 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
   const int sms = std::max(1, dev_info(device).sms);
   int nblk = tu.blocks;
   if (nblk <= 0) {
-    // FP64 work per row is slow on this GPU's narrow FP64 pipe: spread small
-    // systems over several SMs; the FP32 inner solve of MIXED is cheap per row
-    // and small systems are best kept in one block (no grid barriers).
-    if (mixed)
-      nblk = n <= 4096 ? 1 : std::min(sms, (n + 767) / 768);
-    else
-      nblk = std::min(sms, std::max(1, (n + 255) / 256));
+    // about 256 rows per block: the FP64 work of a row is slow on this GPU's
+    // narrow FP64 pipe, and even the FP32 inner solve of MIXED runs faster
+    // from shared memory on several SMs than from global memory on one
+    nblk = std::min(sms, std::max(1, (n + 255) / 256));
   }
   nblk = std::max(1, std::min(nblk, std::min(cap0, n)));
   out = LaunchPlan{};

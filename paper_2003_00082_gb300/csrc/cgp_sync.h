@@ -1,0 +1,58 @@
+// Grid-wide barrier of a cooperative launch, with a wall-clock limit.
+//
+// Arrival is a release-add on a counter that only grows; a block waits until
+// the counter reaches epoch * nblk, polling with relaxed loads and finishing
+// with an acquire.  The wait gives up after spin_ns of wall-clock time, or as
+// soon as another block has given up (the shared timeout word), and then
+// reports failure instead of hanging.
+#pragma once
+
+namespace cgp {
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Thread 0 of the block: arrive and wait for the `epoch`-th completion of the
+// barrier over nblk blocks; returns false when the wait gave up.
+__device__ __forceinline__ bool barrier_arrive_wait(unsigned* bar, int* timeout, unsigned nblk, unsigned epoch,
+                                                    long long spin_ns) {
+  red_release_add(bar, 1u);
+  const unsigned target = epoch * nblk;
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+  while (ld_relaxed(bar) < target) {
+    if ((++spins & 127u) == 0) {
+      if (*(volatile int*)timeout) return false;
+      const unsigned long long now = global_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if ((long long)(now - t0) > spin_ns) {
+        atomicExch(timeout, 1);
+        return false;
+      }
+    }
+  }
+  (void)ld_acquire(bar);
+  return true;
+}
+
+}  // namespace cgp

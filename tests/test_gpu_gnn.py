@@ -133,3 +133,34 @@ def test_one_adam_step_matches_the_oracle(cgp, setting):
     for k in p:
         np.testing.assert_allclose(after[k], p[k], rtol=0, atol=2e-6)
     net.close()
+
+
+@pytest.mark.parametrize("shape", [(16, 8), (33, 17), (64, 32)])
+def test_fused_inference_matches_the_batched_forward(cgp, shape):
+    """cgp_gnn_predict (one cooperative launch over node chunks of 128, ragged last chunk)
+    runs the batched kernels' arithmetic in the same order: the same FP32 outputs."""
+    xy, tri = inputs.ogrid(*shape)
+    m = cgp.Mesh(xy, tri)
+    om = O.OracleMesh(xy, tri)
+    u, v = inputs.velocity(om.xy_f, 4, 2, vortices=True, noise_std=1e-3)
+    Fx, Fy = O.source_field(O.POTENTIAL, om.restrict(u), om.restrict(v), (0.0, 0.0, 1.0))
+    b = O.rhs(om.Gx, om.Gy, Fx, Fy)
+    phi2 = O.pcg(om.K, om.d, b * 0.97, tol=1e-10)["x"]
+    phi1 = O.pcg(om.K, om.d, b * 0.99, tol=1e-10)["x"]
+    net = cgp.GNN(m, 1, pack(G.init_params(9, zero_decoder=False)))
+    T = lambda a: torch.as_tensor(a, dtype=torch.float64, device=DEV)  # noqa: E731
+    x0 = torch.empty(om.n_c, dtype=torch.float64, device=DEV)
+    net.predict(T(b), T(phi1), T(phi2), x0)
+    torch.cuda.synchronize()
+    _, out, _ = net.gradients(1, T(b), T(phi1), T(phi2), T(phi1))
+    s_d = float(np.sqrt(np.mean((phi1 - phi2) ** 2)))
+    got = x0.cpu().numpy() - phi1
+    want = s_d * out[0].astype(np.float64)
+    # identical FP32 outputs leave only the rounding of the scale and of x0 (far below one BF16 step)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    f, _ = G.features(G.Graph(om.K, om.xy_c), om.K, b, phi1, phi2)
+    p = unpack(pack(G.init_params(9, zero_decoder=False)))
+    ref_out, _ = G.forward(p, G.Graph(om.K, om.xy_c), f, bf16_storage=True)
+    assert np.linalg.norm(got / s_d - ref_out) <= 2e-2 * np.linalg.norm(ref_out)
+    net.close()
+    m.close()
