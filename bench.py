@@ -398,6 +398,7 @@ def run_mine(args, rank, world, local_rank):
     if rank == 0 and not args.no_variants:
         from paper_2003_00082_gb300 import configs
         result["mixed_64x32"] = run_mixed_small(cgp, inputs, torch, dev)
+        result["levels"] = run_levels(cgp, inputs, torch, dev, flush)
         result["batched"] = run_batched(cgp, inputs, configs, torch, dev, flush, peak)
         result["learned_guess"] = run_learned_guess(cgp, inputs, torch)
     mesh.close()
@@ -462,6 +463,66 @@ def run_batched(cgp, inputs, configs, torch, dev, flush, peak, reps=5):
            "autotune_best_ms": tune_ms}
     batch.close()
     for m in meshes:
+        m.close()
+    return out
+
+
+def run_levels(cgp, inputs, torch, dev, flush, steps=10, warm=3):
+    """The c2 step (potential + pressure, vortex train, B = k, N = 1, tol 1e-8, previous-step x0)
+    on the same 525,312-node fine mesh size reached with k = 2 and k = 3 coarsening levels
+    (coarse 256x128 and 128x64 O-grids): CGP solves/s as the coarse system shrinks (Eq. 18)."""
+    out = {"workload": "c2 potential+pressure steps, fine mesh 525,312 nodes from a 512/2^(k-1) x 256/2^(k-1) "
+                       "coarse O-grid split k times; FP64, autotuned launch; L2 flushed between steps"}
+    f64 = dict(dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    for k in (2, 3):
+        nt, nr = N_THETA >> (k - 1), N_R >> (k - 1)
+        xy, tri = inputs.ogrid(nt, nr)
+        m = cgp.Mesh(xy, tri, k)
+        xy_f, _, _ = m.fine_geometry()
+        n = m.n_c
+        b = torch.empty(n, **f64)
+        phi_c, p_c = torch.zeros(n, **f64), torch.zeros(n, **f64)
+        phi_f, p_f = torch.empty(m.n_f, **f64), torch.empty(m.n_f, **f64)
+        grad_phi, force, grad_p = (torch.empty(2 * m.t_f, **f64) for _ in range(3))
+        U = []
+        for t in range(warm + steps):
+            u, v = inputs.velocity(xy_f, t, SEED, vortices=True)
+            U.append((torch.as_tensor(u, device=dev), torch.as_tensor(v, device=dev)))
+        cgp.cgp_restrict(m.handle, cgp.CGP_RHS_POTENTIAL, B_FIELD, RHO_OVER_DT, U[0][0], U[0][1], b)
+        tune_x = torch.zeros(n, **f64)
+        cgp.cgp_autotune(m.handle, cgp.CGP_FP64, b, tune_x)
+        infos = torch.zeros(2 * (warm + steps) * cgp.INFO_BYTES, dtype=torch.uint8, device=dev)
+        ev = []
+        for t in range(warm + steps):
+            uf, vf = U[t]
+            if t >= warm:
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            cgp.cgp_restrict(m.handle, cgp.CGP_RHS_POTENTIAL, B_FIELD, RHO_OVER_DT, uf, vf, b)
+            cgp.cgp_poisson_solve_async(m.handle, b, phi_c, tol=TOL, use_x0=t > 0,
+                                        info_dev=infos.data_ptr() + 2 * t * cgp.INFO_BYTES)
+            cgp.cgp_prolong(m.handle, phi_c, phi_f)
+            cgp.cgp_lorentz(m.handle, phi_f, uf, vf, B_FIELD, STUART, grad_phi, force)
+            cgp.cgp_restrict(m.handle, cgp.CGP_RHS_PRESSURE, B_FIELD, RHO_OVER_DT, uf, vf, b)
+            cgp.cgp_poisson_solve_async(m.handle, b, p_c, tol=TOL, use_x0=t > 0,
+                                        info_dev=infos.data_ptr() + (2 * t + 1) * cgp.INFO_BYTES)
+            cgp.cgp_prolong(m.handle, p_c, p_f)
+            cgp.cgp_lorentz(m.handle, p_f, None, None, B_FIELD, STUART, grad_p, None)
+            if t >= warm:
+                e1.record(stream)
+                ev.append((e0, e1))
+        torch.cuda.synchronize()
+        recs = cgp.decode_infos(bytes(infos.cpu().numpy()), 2 * (warm + steps))[2 * warm:]
+        ms = sum(a.elapsed_time(c) for a, c in ev)
+        out[f"k{k}"] = {"coarse_mesh": f"{nt}x{nr}", "coarse_nodes": n, "fine_nodes": m.n_f,
+                        "solves_per_s": 2 * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                        "iterations_mean": statistics.mean(r["iterations"] for r in recs),
+                        "all_converged": all(r["status"] == cgp.CGP_OK for r in recs),
+                        "rel_res_true_max": max(r["rel_res_true"] for r in recs),
+                        "launch": cgp.cgp_last_launch(m.handle)}
         m.close()
     return out
 
@@ -792,6 +853,8 @@ def main():
             line["other_precision"] = res["variant"]
         if "mixed_64x32" in res:
             line["mixed_64x32"] = res["mixed_64x32"]
+        if "levels" in res:
+            line["levels"] = res["levels"]
         if "batched" in res:
             line["batched"] = res["batched"]
         if "learned_guess" in res:

@@ -25,12 +25,17 @@
  *   - Vectors are contiguous FP64 arrays; index i of a coarse vector is
  *     coarse node i.
  *
- * Fine-mesh numbering (the 4-way split of Sect. 2.3, Eq. 18 with k = 1)
- *   - fine nodes [0, n_c) are the coarse nodes; fine node n_c + e is the
- *     midpoint of coarse edge e, edges sorted by (min vertex, max vertex);
- *   - fine triangle 4T + c of coarse triangle T = (a, b, c) is child c of
- *     (a, m_ab, m_ca), (m_ab, b, m_bc), (m_ca, m_bc, c), (m_ab, m_bc, m_ca).
- *   Injection (Eq. 19) is therefore the prefix q_f[0, n_c).
+ * Fine-mesh numbering (the nested 4-way splits of Sect. 2.3, Eq. 18; k = levels)
+ *   - level l + 1 splits every triangle of level l (level 0 is the coarse
+ *     mesh, level k the fine mesh): its nodes [0, n_l) are level l's nodes,
+ *     node n_l + e is the midpoint of level-l edge e, edges sorted by
+ *     (min vertex, max vertex);
+ *   - triangle 4T + c of level l + 1 is child c of level-l triangle
+ *     T = (a, b, c): (a, m_ab, m_ca), (m_ab, b, m_bc), (m_ca, m_bc, c),
+ *     (m_ab, m_bc, m_ca); the fine children of coarse triangle T are the
+ *     4^k consecutive triangles from 4^k T.
+ *   The coarse nodes are the prefix of every level, so injection (Eq. 19) is
+ *   the prefix q_f[0, n_c).
  */
 #ifndef CGP_H
 #define CGP_H
@@ -77,8 +82,8 @@ typedef struct {
  *
  * xy_c   host, [n_c][2] coarse node coordinates (FP64, interleaved x, y).
  * tri_c  host, [t_c][3] coarse triangles, counter-clockwise, 0-based.
- * levels coarsening levels between the fine and the coarse mesh; only k = 1
- *        (one uniform 4-way split) is supported.
+ * levels coarsening levels k between the fine and the coarse mesh (Eq. 18):
+ *        1, 2 or 3 nested uniform 4-way splits (t_f = 4^k t_c).
  * out    receives the handle.
  *
  * Builds the fine mesh by the numbering above, the CSR pattern of the coarse
@@ -87,17 +92,24 @@ typedef struct {
  * D^-1 = 1/K_ii (FP64 and FP32 copies) and the fine node coordinates.
  * Blocks until the device data is ready.  Inputs are copied; the caller may
  * free them afterwards.  Errors: INVALID_ARG for sizes <= 0, indices out of
- * range, clockwise or degenerate triangles, or levels != 1; OOM; CUDA.
+ * range, clockwise or degenerate triangles, levels outside [1, 3], or a fine
+ * mesh beyond 32-bit indexing; OOM; CUDA.
  */
 int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t_c, int levels,
                  cgp_mesh* out);
 
-/* Sizes of a mesh pair; any output pointer may be NULL.  nnz counts K's pattern. */
+/* Sizes of a mesh pair; any output pointer may be NULL.  n_e counts the coarse
+ * edges, n_f and t_f the finest level, nnz K's pattern. */
 int cgp_mesh_query(cgp_mesh m, int* n_c, int* t_c, int* n_e, int* n_f, int* t_f, int* nnz);
+
+/* Coarsening levels k and the node count of every level, nodes host [k + 1]
+ * (nodes[0] = n_c, nodes[k] = n_f); either pointer may be NULL. */
+int cgp_mesh_levels(cgp_mesh m, int* levels, int* nodes);
 
 /*
  * cgp_mesh_fine_geometry - host copies of the fine mesh (synchronous).
- * xy_f  host [n_f][2] or NULL;  tri_f host [t_f][3] or NULL;  edges host [n_e][2] or NULL.
+ * xy_f  host [n_f][2] or NULL;  tri_f host [t_f][3] or NULL;  edges host [n_e][2]
+ * (the coarse edges) or NULL.
  */
 int cgp_mesh_fine_geometry(cgp_mesh m, double* xy_f, int* tri_f, int* edges);
 
@@ -273,11 +285,13 @@ int cgp_poisson_solve_batched(const cgp_mesh* meshes, int count, const double* c
  *                  samples; params host [param_count].  Allocates its device
  *                  memory; synchronous.
  * cgp_gnn_predict  x0 (device [n_c]) from b, phi1, phi2 (device [n_c]); async.
- *                  One cooperative launch runs the whole forward (the same
- *                  arithmetic as the batched training forward, so the same
- *                  bits); its grid barriers give up after about two seconds
- *                  and then leave NaN in x0, which the solve reports as
- *                  CGP_ERR_NONFINITE.
+ *                  When every 16-node chunk gets its own block (n_c up to
+ *                  16 x co-resident blocks) one cooperative launch runs the
+ *                  whole forward, else the batched training forward does;
+ *                  both take the same arithmetic steps in the same order,
+ *                  so the same bits.  The cooperative launch's grid barriers
+ *                  give up after about two seconds and then leave NaN in x0,
+ *                  which the solve reports as CGP_ERR_NONFINITE.
  * cgp_gnn_train_step  forward, loss, backward and one Adam step on `batch`
  *                  samples stacked sample-major (device [batch][n_c] each,
  *                  phi_t the solutions to learn); loss_dev (device float,
@@ -302,9 +316,11 @@ int cgp_gnn_set_params(cgp_gnn g, const float* params);
 int cgp_gnn_destroy(cgp_gnn g);
 
 /*
- * cgp_prolong - prolongation by the P1 shape functions (Eq. 20) for one level:
- * x_f[i] = x_c[i] for coarse nodes, x_f[n_c + e] = (x_c[a_e] + x_c[b_e]) / 2 at
- * the midpoint of edge e (shape functions 1/2, 1/2, 0 there).
+ * cgp_prolong - prolongation by the P1 shape functions (Eq. 20), one level
+ * at a time from the coarse to the fine mesh as the paper prescribes:
+ * x_f[i] = x_c[i] for coarse nodes; then for l = 0 .. k-1,
+ * x_f[n_l + e] = (x_f[a_e] + x_f[b_e]) / 2 at the midpoint of level-l edge e
+ * (shape functions 1/2, 1/2, 0 there).  One launch per level.
  * x_c device [n_c]; x_f device [n_f].
  */
 int cgp_prolong(cgp_mesh m, const double* x_c, double* x_f, void* stream);
@@ -324,6 +340,20 @@ int cgp_prolong(cgp_mesh m, const double* x_c, double* x_f, void* stream);
  */
 int cgp_lorentz(cgp_mesh m, const double* phi_f, const double* u_f, const double* v_f,
                 const double* B, double sigma, double* grad, double* force, void* stream);
+
+/*
+ * cgp_velocity_correct - the velocity update of the pressure correction on the
+ * fine mesh (Eqs. 16-17): u = u~ - (dt/rho) dp/dx, v = v~ - (dt/rho) dp/dy at
+ * every fine node, with the P1 gradient of p_f (constant per fine triangle)
+ * brought to the nodes by the lumped P1 mass: the area-weighted mean of the
+ * gradients of the fine triangles around the node.
+ * p_f, u_t, v_t, u, v  device [n_f]; u, v may alias u_t, v_t.
+ * dt_over_rho          dt / rho.
+ * The first call on a mesh builds the fine node -> triangle incidence
+ * (synchronous, one allocation of about 24 t_f bytes, freed with the mesh).
+ */
+int cgp_velocity_correct(cgp_mesh m, const double* p_f, const double* u_t, const double* v_t,
+                         double dt_over_rho, double* u, double* v, void* stream);
 
 /*
  * cgp_spmv - y = K x with the coarse stiffness matrix (the product inside

@@ -92,6 +92,19 @@ def split4(xy_c: np.ndarray, tri_c: np.ndarray):
     return xy_f, tri_f.astype(np.int32), edges.astype(np.int32), parent
 
 
+def split_levels(xy_c, tri_c, k: int):
+    """k nested uniform 4-way splits (Eq. 18, P = 4^-k M): the list of levels
+    [(xy_0, tri_0, None, None), (xy_1, tri_1, edges_0, parent_0), ...] where
+    level l + 1 = split4(level l), edges_l are level l's edges and parent_l[t]
+    the level-l triangle of level-(l+1) triangle t."""
+    levels = [(np.asarray(xy_c, dtype=np.float64), np.asarray(tri_c, dtype=np.int32), None, None)]
+    for _ in range(k):
+        xy, tri = levels[-1][0], levels[-1][1]
+        xy_n, tri_n, edges, parent = split4(xy, tri)
+        levels.append((xy_n, tri_n, edges, parent))
+    return levels
+
+
 # ----------------------------------------------------------------------------
 # 2. Galerkin P1 assembly (Sect. 2.3)
 # ----------------------------------------------------------------------------
@@ -385,16 +398,38 @@ def mixed_ir(K, d, b, x0=None, tol=1e-8, inner_tol=1e-4, max_sweeps=50, inner_ma
 
 
 # ----------------------------------------------------------------------------
+# 8. velocity correction (Eqs. 16-17), lumped P1 mass
+# ----------------------------------------------------------------------------
+def velocity_correct(xy_f, tri_f, p_f, u_t, v_t, dt_over_rho):
+    """u = u~ - (dt/rho) (M_L^-1 int psi_i grad p), the Galerkin form of Eqs. 16-17 with the
+    lumped mass M_L,ii = sum_{T ni i} |T| / 3 and int_T psi_i grad p = (|T| / 3) grad p|_T."""
+    xy_f = np.asarray(xy_f, dtype=np.float64)
+    tri = np.asarray(tri_f, dtype=np.int64)
+    area2, _, _ = p1_gradients(xy_f, tri)
+    gx, gy = gradient(xy_f, tri, p_f)
+    w = np.repeat((0.5 * area2 / 3.0)[:, None], 3, axis=1).ravel()
+    n = xy_f.shape[0]
+    mass = np.bincount(tri.ravel(), weights=w, minlength=n)
+    fx = np.bincount(tri.ravel(), weights=w * np.repeat(gx, 3), minlength=n)
+    fy = np.bincount(tri.ravel(), weights=w * np.repeat(gy, 3), minlength=n)
+    return np.asarray(u_t) - dt_over_rho * fx / mass, np.asarray(v_t) - dt_over_rho * fy / mass
+
+
+# ----------------------------------------------------------------------------
 # the whole CGP solve on one mesh pair
 # ----------------------------------------------------------------------------
 class OracleMesh:
-    """Coarse mesh, its 4-way split and the assembled coarse operators."""
+    """Coarse mesh, its k nested 4-way splits (Eq. 18) and the assembled coarse operators."""
 
-    def __init__(self, xy_c, tri_c):
+    def __init__(self, xy_c, tri_c, levels: int = 1):
         self.xy_c = np.asarray(xy_c, dtype=np.float64)
         self.tri_c = np.asarray(tri_c, dtype=np.int32)
         self.n_c = self.xy_c.shape[0]
-        self.xy_f, self.tri_f, self.edges, self.parent = split4(self.xy_c, self.tri_c)
+        self.k = levels
+        self.levels = split_levels(self.xy_c, self.tri_c, levels)
+        self.xy_f, self.tri_f = self.levels[-1][0], self.levels[-1][1]
+        self.edges = self.levels[1][2]              # the coarse edges
+        self.parent = self.levels[1][3] if levels == 1 else None
         self.n_f = self.xy_f.shape[0]
         self.K, self.Gx, self.Gy, self.d = assemble(self.xy_c, self.tri_c)
         self._restrict_idx = None
@@ -405,7 +440,13 @@ class OracleMesh:
         return np.asarray(q_f)[self._restrict_idx]
 
     def prolong(self, q_c):
-        return prolong(self.xy_c, self.tri_c, self.xy_f, self.tri_f, self.parent, q_c)
+        """Eq. 20 one level at a time, k times (Sect. 2.3: prolongation only reaches the next nested space)."""
+        q = np.asarray(q_c, dtype=np.float64)
+        for l in range(self.k):
+            xy, tri = self.levels[l][0], self.levels[l][1]
+            xy_n, tri_n, _, parent = self.levels[l + 1]
+            q = prolong(xy, tri, xy_n, tri_n, parent, q)
+        return q
 
     def solve(self, u_f, v_f, kind=POTENTIAL, B=(0.0, 0.0, 1.0), sigma=1.0, rho_over_dt=20.0,
               tol=1e-8, x0=None, max_it=20000, mixed=False, inner_tol=1e-4):

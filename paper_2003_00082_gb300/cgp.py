@@ -32,9 +32,9 @@ CGP_FP64 = 0
 CGP_MIXED = 1
 CGP_FP32 = 1          # precision argument of cgp_spmv for the FP32 copy of K
 
-EXPORTS = ("cgp_assemble", "cgp_mesh_query", "cgp_mesh_fine_geometry", "cgp_mesh_matrices",
+EXPORTS = ("cgp_assemble", "cgp_mesh_query", "cgp_mesh_levels", "cgp_mesh_fine_geometry", "cgp_mesh_matrices",
            "cgp_restrict", "cgp_poisson_solve", "cgp_poisson_solve_async",
-           "cgp_poisson_solve_noalloc", "cgp_prolong", "cgp_lorentz", "cgp_spmv",
+           "cgp_poisson_solve_noalloc", "cgp_prolong", "cgp_lorentz", "cgp_velocity_correct", "cgp_spmv",
            "cgp_set_tuning", "cgp_get_tuning", "cgp_autotune", "cgp_last_launch", "cgp_barrier_selftest",
            "cgp_batch_create", "cgp_batch_solve", "cgp_batch_info", "cgp_batch_set_tuning",
            "cgp_batch_autotune", "cgp_batch_query", "cgp_batch_destroy", "cgp_poisson_solve_batched",
@@ -97,6 +97,8 @@ def load(path: str | None = None):
         "cgp_poisson_solve_noalloc": [i, vp, vp, vp, vp, vp, vp, ctypes.POINTER(SolveOpts),
                                       ctypes.POINTER(SolveInfo), vp],
         "cgp_prolong": [vp, vp, vp, vp],
+        "cgp_mesh_levels": [vp, ip, ip],
+        "cgp_velocity_correct": [vp, vp, vp, vp, d, vp, vp, vp],
         "cgp_lorentz": [vp, vp, vp, vp, dp, d, vp, vp, vp],
         "cgp_spmv": [vp, i, vp, vp, vp],
         "cgp_set_tuning": [vp, i, i, i, i, i],
@@ -191,6 +193,15 @@ def cgp_mesh_query(mesh):
     return dict(zip(("n_c", "t_c", "n_e", "n_f", "t_f", "nnz"), [v.value for v in vals]))
 
 
+def cgp_mesh_levels(mesh):
+    """(levels k, node counts of levels 0 .. k)."""
+    k = ctypes.c_int()
+    _check(load().cgp_mesh_levels(mesh, ctypes.byref(k), None))
+    nodes = (ctypes.c_int * (k.value + 1))()
+    _check(load().cgp_mesh_levels(mesh, None, nodes))
+    return k.value, list(nodes)
+
+
 def cgp_mesh_fine_geometry(mesh):
     s = cgp_mesh_query(mesh)
     xy = np.empty((s["n_f"], 2), dtype=np.float64)
@@ -272,6 +283,11 @@ def cgp_prolong(mesh, x_c, x_f, stream=None):
 def cgp_lorentz(mesh, phi_f, u_f, v_f, B, sigma, grad, force=None, stream=None):
     _check(load().cgp_lorentz(mesh, _dev(phi_f), _dev(u_f), _dev(v_f), _dvec3(B), float(sigma), _dev(grad),
                               _dev(force), _stream(stream)))
+
+
+def cgp_velocity_correct(mesh, p_f, u_t, v_t, dt_over_rho, u, v, stream=None):
+    _check(load().cgp_velocity_correct(mesh, _dev(p_f), _dev(u_t), _dev(v_t), float(dt_over_rho), _dev(u), _dev(v),
+                                       _stream(stream)))
 
 
 def cgp_spmv(mesh, precision, x, y, stream=None):
@@ -502,6 +518,7 @@ class Mesh:
     def __init__(self, xy_c, tri_c, levels: int = 1):
         self.handle = cgp_assemble(xy_c, tri_c, levels)
         self.__dict__.update(cgp_mesh_query(self.handle))
+        self.levels, self.level_nodes = cgp_mesh_levels(self.handle)
 
     def fine_geometry(self):
         return cgp_mesh_fine_geometry(self.handle)

@@ -1190,6 +1190,10 @@ extern "C" int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, c
                                void* stream) {
   if (!g || !b || !phi1 || !phi2 || !x0) return fail(CGP_ERR_INVALID_ARG, "cgp_gnn_predict: NULL argument");
   cudaStream_t s = (cudaStream_t)stream;
+  // the fused kernel keeps one node chunk per block; a mesh with more chunks
+  // than co-resident blocks runs the batched forward (the same bits), whose
+  // many independent blocks hide latency better than a chunk loop would
+  if ((g->n + NT - 1) / NT > g->infer_grid) return gnn_forward(g, 1, b, phi1, phi2, nullptr, x0, s);
   InferArgs a{};
   a.n = g->n;
   a.C = (g->n + TILE - 1) / TILE;

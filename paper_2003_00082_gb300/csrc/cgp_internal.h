@@ -69,6 +69,11 @@ struct HaloPlan {
 struct cgp_mesh_impl {
   int device = 0;
   int n_c = 0, t_c = 0, n_e = 0, n_f = 0, t_f = 0, nnz = 0;
+  int levels = 1;                      // 4-way splits between the coarse and the fine mesh (Eq. 18)
+  std::vector<int> h_lvl_nodes;        // [levels + 1] nodes of level 0 (coarse) .. levels (fine)
+  std::vector<int> h_lvl_eoff;         // [levels + 1] offsets of each level's edges in `edges`
+  int t_par = 0;                       // triangles of level levels - 1 (the fine triangles' parents)
+  std::vector<int> h_tri_par, h_mid_par;  // levels >= 2: their vertices and edge midpoints (else tri_c, tri_mid)
 
   // host copies of the integer structure
   std::vector<int> h_rowptr, h_col, h_tri_c, h_edges, h_tri_mid;
@@ -87,7 +92,9 @@ struct cgp_mesh_impl {
   float* dinv32 = nullptr;   // [n_c]
   int* tri_c = nullptr;      // [t_c * 3]
   int* tri_mid = nullptr;    // [t_c * 3]: fine indices of m_ab, m_bc, m_ca
-  int* edges = nullptr;      // [n_e * 2]
+  int* edges = nullptr;      // [2 * all levels' edges]: level 0 (the coarse edges, n_e of them) first
+  int* tri_par = nullptr;    // [3 t_par] parents of the fine triangles (tri_c when levels == 1)
+  int* mid_par = nullptr;    // [3 t_par] their midpoints m_ab, m_bc, m_ca (tri_mid when levels == 1)
   double* xy_f = nullptr;    // [n_f * 2] interleaved
   double* xy_c = nullptr;    // [n_c * 2]
   int* inc_ptr = nullptr;    // [n_c + 1] node -> incident triangles
@@ -110,6 +117,12 @@ struct cgp_mesh_impl {
   SolveResult* h_res = nullptr;  // pinned host mirror
   int max_blocks = 0;
 
+  // fine node -> incident fine triangles, each entry the other two vertices in
+  // counter-clockwise order (built on the first velocity correction)
+  int* vinc_ptr = nullptr;   // [n_f + 1]
+  int* vinc = nullptr;       // [3 t_f][2]
+  void* vinc_base = nullptr;
+
   std::vector<HaloPlan> plans;   // cached per block count
   SolverTuning tune[4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};  // by cgp_tune_target
   PlanRecord last_plan[2] = {{0, 0, 0, 0}, {0, 0, 0, 0}};                          // FP64, MIXED
@@ -121,6 +134,8 @@ int launch_restrict_rhs(cgp_mesh_impl* m, int kind, double bz, double rho_over_d
                         const double* u_f, const double* v_f, double* u_c, double* v_c,
                         double* b, cudaStream_t s);
 int launch_prolong(cgp_mesh_impl* m, const double* xc, double* xf, cudaStream_t s);
+int launch_velocity_correct(cgp_mesh_impl* m, const double* p_f, const double* u_t, const double* v_t,
+                            double dt_over_rho, double* u, double* v, cudaStream_t s);
 int launch_lorentz(cgp_mesh_impl* m, const double* phi, const double* u, const double* v,
                    const double B[3], double sigma, double* grad, double* force, cudaStream_t s);
 int launch_spmv(cgp_mesh_impl* m, int precision, const void* x, void* y, cudaStream_t s);

@@ -43,7 +43,7 @@ __global__ void restrict_rhs_kernel(int n, const int* __restrict__ rowptr, const
   if (v_c) v_c[i] = v_f[i];
 }
 
-// Two fine nodes per thread: coarse prefix copy, then midpoints.
+// One level-1 node per thread: the coarse prefix copied, then the midpoints of the coarse edges.
 __global__ void prolong_kernel(int n_c, int n_f, const int2* __restrict__ edges,
                                const double* __restrict__ xc, double* __restrict__ xf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -54,6 +54,16 @@ __global__ void prolong_kernel(int n_c, int n_f, const int2* __restrict__ edges,
     const int2 e = edges[i - n_c];
     xf[i] = (xc[e.x] + xc[e.y]) * 0.5;
   }
+}
+
+// One further level (Eq. 20 from level l to l + 1, in place): node n_l + e
+// is the midpoint of level-l edge e, where the parent's shape functions are
+// (1/2, 1/2, 0); level l's nodes are the prefix and already hold their values.
+__global__ void prolong_level_kernel(int n_l, int e_l, const int2* __restrict__ edges, double* __restrict__ xf) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= e_l) return;
+  const int2 ed = edges[e];
+  xf[n_l + e] = (xf[ed.x] + xf[ed.y]) * 0.5;
 }
 
 struct Node {
@@ -116,6 +126,35 @@ __global__ void lorentz_kernel(int t_c, int t_f, const int* __restrict__ tri,
   }
 }
 
+// Velocity correction (Eqs. 16-17) at fine node i with the lumped P1 mass:
+// u_i = u~_i - (dt/rho) sum_T |T| dp/dx|_T / sum_T |T| over the fine
+// triangles T around i.  For T = (i, j, k) counter-clockwise,
+// 2|T| grad p = (p_i (y_j - y_k) + p_j (y_k - y_i) + p_k (y_i - y_j),
+//                p_i (x_k - x_j) + p_j (x_i - x_k) + p_k (x_j - x_i)),
+// so the weights 2|T| cancel the division by the area.  Triangles are taken
+// in increasing index order (deterministic).
+__global__ void velocity_correct_kernel(int n_f, const int* __restrict__ ptr, const int2* __restrict__ inc,
+                                        const double2* __restrict__ xy, const double* __restrict__ p,
+                                        const double* __restrict__ ut, const double* __restrict__ vt,
+                                        double c, double* __restrict__ u, double* __restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_f) return;
+  const double2 xi = xy[i];
+  const double pi = p[i];
+  double sx = 0.0, sy = 0.0, sa = 0.0;
+  for (int q = ptr[i]; q < ptr[i + 1]; ++q) {
+    const int2 jk = inc[q];
+    const double2 xj = xy[jk.x], xk = xy[jk.y];
+    const double pj = p[jk.x], pk = p[jk.y];
+    sx += pi * (xj.y - xk.y) + pj * (xk.y - xi.y) + pk * (xi.y - xj.y);
+    sy += pi * (xk.x - xj.x) + pj * (xi.x - xk.x) + pk * (xj.x - xi.x);
+    sa += (xj.x - xi.x) * (xk.y - xi.y) - (xk.x - xi.x) * (xj.y - xi.y);
+  }
+  const double ia = 1.0 / sa;
+  u[i] = ut[i] - c * (sx * ia);
+  v[i] = vt[i] - c * (sy * ia);
+}
+
 }  // namespace
 
 int launch_restrict_rhs(cgp_mesh_impl* m, int kind, double bz, double rho_over_dt, const double* u_f,
@@ -133,22 +172,85 @@ int launch_restrict_rhs(cgp_mesh_impl* m, int kind, double bz, double rho_over_d
 
 int launch_prolong(cgp_mesh_impl* m, const double* xc, double* xf, cudaStream_t s) {
   const int bs = 256;
-  prolong_kernel<<<(m->n_f + bs - 1) / bs, bs, 0, s>>>(m->n_c, m->n_f, reinterpret_cast<const int2*>(m->edges),
-                                                       xc, xf);
+  const int n1 = m->h_lvl_nodes[1];
+  prolong_kernel<<<(n1 + bs - 1) / bs, bs, 0, s>>>(m->n_c, n1, reinterpret_cast<const int2*>(m->edges), xc, xf);
   CGP_CUDA(cudaGetLastError());
+  for (int l = 1; l < m->levels; ++l) {   // one launch per further level, as Eq. 20 prolongs one level at a time
+    const int e_l = m->h_lvl_eoff[l + 1] - m->h_lvl_eoff[l];
+    prolong_level_kernel<<<(e_l + bs - 1) / bs, bs, 0, s>>>(
+        m->h_lvl_nodes[l], e_l, reinterpret_cast<const int2*>(m->edges) + m->h_lvl_eoff[l], xf);
+    CGP_CUDA(cudaGetLastError());
+  }
   return CGP_OK;
 }
 
 int launch_lorentz(cgp_mesh_impl* m, const double* phi, const double* u, const double* v, const double B[3],
                    double sigma, double* grad, double* force, cudaStream_t s) {
-  const int bs = 128, gs = (m->t_c + bs - 1) / bs;
+  // one thread per parent (level levels - 1) triangle and its four fine children
+  const int bs = 128, gs = (m->t_par + bs - 1) / bs;
   const double2* xy = reinterpret_cast<const double2*>(m->xy_f);
   if (force)
-    lorentz_kernel<true><<<gs, bs, 0, s>>>(m->t_c, m->t_f, m->tri_c, m->tri_mid, xy, phi, u, v, B[0], B[1],
+    lorentz_kernel<true><<<gs, bs, 0, s>>>(m->t_par, m->t_f, m->tri_par, m->mid_par, xy, phi, u, v, B[0], B[1],
                                            B[2], sigma, grad, force);
   else
-    lorentz_kernel<false><<<gs, bs, 0, s>>>(m->t_c, m->t_f, m->tri_c, m->tri_mid, xy, phi, u, v, B[0], B[1],
+    lorentz_kernel<false><<<gs, bs, 0, s>>>(m->t_par, m->t_f, m->tri_par, m->mid_par, xy, phi, u, v, B[0], B[1],
                                             B[2], sigma, grad, force);
+  CGP_CUDA(cudaGetLastError());
+  return CGP_OK;
+}
+
+// Fine-node incidence for the velocity correction, built once per mesh on the host.
+static int build_vinc(cgp_mesh_impl* m) {
+  if (m->vinc) return CGP_OK;
+  const std::vector<int>& tp = m->levels >= 2 ? m->h_tri_par : m->h_tri_c;
+  const std::vector<int>& mp = m->levels >= 2 ? m->h_mid_par : m->h_tri_mid;
+  const size_t nf = m->n_f, tf = m->t_f;
+  std::vector<int> ptr(nf + 1, 0), ent(6 * tf);
+  auto fine_tri = [&](size_t t, int (&v)[3]) {
+    const size_t T = t / 4;
+    const int a = tp[3 * T], b = tp[3 * T + 1], c = tp[3 * T + 2];
+    const int mab = mp[3 * T], mbc = mp[3 * T + 1], mca = mp[3 * T + 2];
+    const int ch[4][3] = {{a, mab, mca}, {mab, b, mbc}, {mca, mbc, c}, {mab, mbc, mca}};
+    for (int l = 0; l < 3; ++l) v[l] = ch[t % 4][l];
+  };
+  int v[3];
+  for (size_t t = 0; t < tf; ++t) {
+    fine_tri(t, v);
+    for (int l = 0; l < 3; ++l) ptr[v[l] + 1]++;
+  }
+  for (size_t i = 0; i < nf; ++i) ptr[i + 1] += ptr[i];
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (size_t t = 0; t < tf; ++t) {
+    fine_tri(t, v);
+    for (int l = 0; l < 3; ++l) {
+      const int q = fill[v[l]]++;
+      ent[2 * (size_t)q] = v[(l + 1) % 3];
+      ent[2 * (size_t)q + 1] = v[(l + 2) % 3];
+    }
+  }
+  const size_t b_ptr = (nf + 1) * 4, o_inc = (b_ptr + 255) / 256 * 256;
+  void* base = nullptr;
+  CGP_CUDA(cudaMalloc(&base, o_inc + ent.size() * 4));
+  cudaError_t e = cudaMemcpy(base, ptr.data(), b_ptr, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(static_cast<char*>(base) + o_inc, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(base);
+    return cuda_fail(e, "cudaMemcpy(fine incidence)");
+  }
+  m->vinc_base = base;
+  m->vinc_ptr = static_cast<int*>(base);
+  m->vinc = reinterpret_cast<int*>(static_cast<char*>(base) + o_inc);
+  return CGP_OK;
+}
+
+int launch_velocity_correct(cgp_mesh_impl* m, const double* p_f, const double* u_t, const double* v_t,
+                            double dt_over_rho, double* u, double* v, cudaStream_t s) {
+  int st = build_vinc(m);
+  if (st != CGP_OK) return st;
+  const int bs = 256;
+  velocity_correct_kernel<<<(m->n_f + bs - 1) / bs, bs, 0, s>>>(
+      m->n_f, m->vinc_ptr, reinterpret_cast<const int2*>(m->vinc), reinterpret_cast<const double2*>(m->xy_f), p_f,
+      u_t, v_t, dt_over_rho, u, v);
   CGP_CUDA(cudaGetLastError());
   return CGP_OK;
 }
@@ -156,6 +258,14 @@ int launch_lorentz(cgp_mesh_impl* m, const double* phi, const double* u, const d
 }  // namespace cgp
 
 using namespace cgp;
+
+extern "C" int cgp_velocity_correct(cgp_mesh m, const double* p_f, const double* u_t, const double* v_t,
+                                    double dt_over_rho, double* u, double* v, void* stream) {
+  if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_velocity_correct: NULL mesh");
+  if (!p_f || !u_t || !v_t || !u || !v) return fail(CGP_ERR_INVALID_ARG, "cgp_velocity_correct: NULL vector");
+  if (!(dt_over_rho == dt_over_rho)) return fail(CGP_ERR_INVALID_ARG, "cgp_velocity_correct: dt_over_rho is NaN");
+  return launch_velocity_correct(m, p_f, u_t, v_t, dt_over_rho, u, v, (cudaStream_t)stream);
+}
 
 static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 

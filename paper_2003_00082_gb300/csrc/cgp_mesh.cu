@@ -101,7 +101,43 @@ __global__ void fine_coords_kernel(int n_c, int n_e, const double2* __restrict__
   }
 }
 
+// midpoints of level-l edges: node n_l + e of level l + 1 sits at (x_a + x_b) / 2
+__global__ void fine_coords_level_kernel(int n_l, int e_l, const int2* __restrict__ edges, double2* __restrict__ xy_f) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= e_l) return;
+  const int2 ed = edges[e];
+  const double2 a = xy_f[ed.x], b = xy_f[ed.y];
+  xy_f[n_l + e] = make_double2(__dmul_rn(__dadd_rn(a.x, b.x), 0.5), __dmul_rn(__dadd_rn(a.y, b.y), 0.5));
+}
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Edges of one level: (min, max) vertex pairs sorted lexicographically; side k
+// of triangle t (vertices k, k+1) gets edge id tri_edge[3 t + k].
+void level_edges(const std::vector<int>& tri, int n_l, std::vector<int>& edges, std::vector<int>& tri_edge) {
+  const size_t t_l = tri.size() / 3;
+  std::vector<std::pair<long long, int>> keys(3 * t_l);
+  for (size_t t = 0; t < t_l; ++t)
+    for (int k = 0; k < 3; ++k) {
+      const int a = tri[3 * t + k], b = tri[3 * t + (k + 1) % 3];
+      const int lo = std::min(a, b), hi = std::max(a, b);
+      keys[3 * t + k] = {(long long)lo * n_l + hi, (int)(3 * t + k)};
+    }
+  std::sort(keys.begin(), keys.end());
+  tri_edge.assign(3 * t_l, 0);
+  edges.clear();
+  int ne = -1;
+  long long prev = -1;
+  for (auto& kv : keys) {
+    if (kv.first != prev) {
+      ++ne;
+      prev = kv.first;
+      edges.push_back((int)(kv.first / n_l));
+      edges.push_back((int)(kv.first % n_l));
+    }
+    tri_edge[kv.second] = ne;
+  }
+}
 
 }  // namespace
 
@@ -111,11 +147,18 @@ int launch_assemble_values(cgp_mesh_impl* m, cudaStream_t s) {
       m->n_c, m->rowptr, m->col, m->inc_ptr, m->inc_tri, m->tri_c,
       reinterpret_cast<const double2*>(m->xy_c), m->K, m->Gx, m->Gy, m->dinv, m->K32, m->dinv32);
   CGP_CUDA(cudaGetLastError());
-  const int nf = m->n_c + m->n_e;
-  fine_coords_kernel<<<(nf + 255) / 256, 256, 0, s>>>(
+  const int n1 = m->n_c + m->n_e;
+  fine_coords_kernel<<<(n1 + 255) / 256, 256, 0, s>>>(
       m->n_c, m->n_e, reinterpret_cast<const double2*>(m->xy_c),
       reinterpret_cast<const int2*>(m->edges), reinterpret_cast<double2*>(m->xy_f));
   CGP_CUDA(cudaGetLastError());
+  for (int l = 1; l < m->levels; ++l) {
+    const int e_l = m->h_lvl_eoff[l + 1] - m->h_lvl_eoff[l];
+    fine_coords_level_kernel<<<(e_l + 255) / 256, 256, 0, s>>>(
+        m->h_lvl_nodes[l], e_l, reinterpret_cast<const int2*>(m->edges) + m->h_lvl_eoff[l],
+        reinterpret_cast<double2*>(m->xy_f));
+    CGP_CUDA(cudaGetLastError());
+  }
   return CGP_OK;
 }
 
@@ -131,9 +174,17 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
   *out = nullptr;
   if (!xy_c || !tri_c) return fail(CGP_ERR_INVALID_ARG, "cgp_assemble: NULL input");
   if (n_c < 3 || t_c < 1) return fail(CGP_ERR_INVALID_ARG, "cgp_assemble: need n_c >= 3 and t_c >= 1");
-  if (levels != 1) return fail(CGP_ERR_INVALID_ARG, "cgp_assemble: only levels == 1 is supported");
-  if ((long long)t_c * 4 > (1LL << 30) || (long long)n_c + 3LL * t_c > (1LL << 30))
-    return fail(CGP_ERR_INVALID_ARG, "cgp_assemble: mesh too large for 32-bit indexing");
+  if (levels < 1 || levels > 3) return fail(CGP_ERR_INVALID_ARG, "cgp_assemble: levels must be 1, 2 or 3");
+  {
+    // every level: t_(l+1) = 4 t_l and n_(l+1) <= n_l + 3 t_l
+    long long t = t_c, nn = n_c;
+    for (int l = 0; l < levels; ++l) {
+      nn += 3 * t;
+      t *= 4;
+    }
+    if (3 * t > (1LL << 30) || nn > (1LL << 30))
+      return fail(CGP_ERR_INVALID_ARG, "cgp_assemble: mesh too large for 32-bit indexing");
+  }
 
   // ---- validate triangles ----
   std::vector<int> used(n_c, 0);
@@ -160,34 +211,51 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
   m->t_c = t_c;
   m->device = device;
 
-  // ---- edges: (min, max) keys sorted lexicographically ----
-  std::vector<std::pair<long long, int>> keys(3 * (size_t)t_c);
-  for (int t = 0; t < t_c; ++t)
-    for (int k = 0; k < 3; ++k) {
-      int a = tri_c[3 * t + k], b = tri_c[3 * t + (k + 1) % 3];
-      int lo = std::min(a, b), hi = std::max(a, b);
-      keys[3 * (size_t)t + k] = {(long long)lo * n_c + hi, 3 * t + k};
-    }
-  std::sort(keys.begin(), keys.end());
-  std::vector<int> tri_edge(3 * (size_t)t_c);
-  m->h_edges.clear();
-  int ne = -1;
-  long long prev = -1;
-  for (auto& kv : keys) {
-    if (kv.first != prev) {
-      ++ne;
-      prev = kv.first;
-      m->h_edges.push_back((int)(kv.first / n_c));
-      m->h_edges.push_back((int)(kv.first % n_c));
-    }
-    tri_edge[kv.second] = ne;
-  }
-  m->n_e = ne + 1;
-  m->n_f = n_c + m->n_e;
-  m->t_f = 4 * t_c;
+  // ---- the nested levels (Eq. 18): each a 4-way split of the previous ----
+  // Level l + 1 numbers level l's nodes first, then the midpoints of level l's
+  // edges in edge order; child 4 t + c of triangle (a, b, c) with midpoints
+  // m_ab, m_bc, m_ca is (a, m_ab, m_ca), (m_ab, b, m_bc), (m_ca, m_bc, c),
+  // (m_ab, m_bc, m_ca).  The coarse nodes stay the prefix of every level.
+  m->levels = levels;
   m->h_tri_c.assign(tri_c, tri_c + 3 * (size_t)t_c);
-  m->h_tri_mid.resize(3 * (size_t)t_c);
-  for (size_t s = 0; s < 3 * (size_t)t_c; ++s) m->h_tri_mid[s] = n_c + tri_edge[s];
+  std::vector<int> all_edges, tri_edge, lvl_edges;
+  std::vector<int> lvl_tri(m->h_tri_c);
+  m->h_lvl_nodes.assign(1, n_c);
+  m->h_lvl_eoff.assign(1, 0);
+  for (int l = 0; l < levels; ++l) {
+    const int n_l = m->h_lvl_nodes[l];
+    level_edges(lvl_tri, n_l, lvl_edges, tri_edge);
+    const int e_l = (int)(lvl_edges.size() / 2);
+    if (l == 0) {
+      m->h_edges = lvl_edges;
+      m->n_e = e_l;
+      m->h_tri_mid.resize(3 * (size_t)t_c);
+      for (size_t q = 0; q < 3 * (size_t)t_c; ++q) m->h_tri_mid[q] = n_c + tri_edge[q];
+    }
+    all_edges.insert(all_edges.end(), lvl_edges.begin(), lvl_edges.end());
+    m->h_lvl_eoff.push_back(m->h_lvl_eoff.back() + e_l);
+    m->h_lvl_nodes.push_back(n_l + e_l);
+    const size_t t_l = lvl_tri.size() / 3;
+    if (l + 1 < levels) {   // the next level's triangles
+      std::vector<int> next(12 * t_l);
+      for (size_t t = 0; t < t_l; ++t) {
+        const int a = lvl_tri[3 * t], b = lvl_tri[3 * t + 1], c = lvl_tri[3 * t + 2];
+        const int mab = n_l + tri_edge[3 * t], mbc = n_l + tri_edge[3 * t + 1], mca = n_l + tri_edge[3 * t + 2];
+        const int ch[12] = {a, mab, mca, mab, b, mbc, mca, mbc, c, mab, mbc, mca};
+        std::memcpy(&next[12 * t], ch, sizeof(ch));
+      }
+      lvl_tri.swap(next);
+    } else {                // the fine triangles' parents and their midpoints
+      m->t_par = (int)t_l;
+      if (levels >= 2) {
+        m->h_tri_par = lvl_tri;
+        m->h_mid_par.resize(3 * t_l);
+        for (size_t q = 0; q < 3 * t_l; ++q) m->h_mid_par[q] = n_l + tri_edge[q];
+      }
+    }
+  }
+  m->n_f = m->h_lvl_nodes[levels];
+  m->t_f = 4 * m->t_par;
 
   // ---- CSR pattern of the node graph plus the diagonal ----
   std::vector<int> deg(n_c, 1);
@@ -221,7 +289,8 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
   size_t o_rowptr = take((n + 1) * 4), o_col = take(nz * 4), o_K = take(nz * 8), o_Gx = take(nz * 8),
          o_Gy = take(nz * 8), o_dinv = take(n * 8), o_K32 = take(nz * 4), o_d32i = take(n * 4),
          o_tri = take(3 * (size_t)t_c * 4), o_mid = take(3 * (size_t)t_c * 4),
-         o_edges = take(2 * (size_t)m->n_e * 4), o_xyf = take(2 * (size_t)m->n_f * 8),
+         o_edges = take(2 * (size_t)m->h_lvl_eoff[levels] * 4), o_tpar = take(m->h_tri_par.size() * 4),
+         o_mpar = take(m->h_mid_par.size() * 4), o_xyf = take(2 * (size_t)m->n_f * 8),
          o_xyc = take(2 * n * 8), o_incp = take((n + 1) * 4), o_inc = take(3 * (size_t)t_c * 4),
          o_bp = take(n * 8), o_r = take(n * 8), o_z = take(n * 8), o_p = take(n * 8), o_p2 = take(n * 8), o_q = take(n * 8),
          o_pub64 = take(6 * n * 8), o_f32pub = take(6 * n * 4), o_f32own = take(6 * n * 4),
@@ -242,6 +311,8 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
   m->tri_c = (int*)(base + o_tri);
   m->tri_mid = (int*)(base + o_mid);
   m->edges = (int*)(base + o_edges);
+  m->tri_par = levels >= 2 ? (int*)(base + o_tpar) : m->tri_c;
+  m->mid_par = levels >= 2 ? (int*)(base + o_mpar) : m->tri_mid;
   m->xy_f = (double*)(base + o_xyf);
   m->xy_c = (double*)(base + o_xyc);
   m->inc_ptr = (int*)(base + o_incp);
@@ -272,7 +343,9 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
       (st = up(m->col, m->h_col.data(), nz * 4)) ||
       (st = up(m->tri_c, m->h_tri_c.data(), 3 * (size_t)t_c * 4)) ||
       (st = up(m->tri_mid, m->h_tri_mid.data(), 3 * (size_t)t_c * 4)) ||
-      (st = up(m->edges, m->h_edges.data(), 2 * (size_t)m->n_e * 4)) ||
+      (st = up(m->edges, all_edges.data(), all_edges.size() * 4)) ||
+      (levels >= 2 && (st = up(m->tri_par, m->h_tri_par.data(), m->h_tri_par.size() * 4))) ||
+      (levels >= 2 && (st = up(m->mid_par, m->h_mid_par.data(), m->h_mid_par.size() * 4))) ||
       (st = up(m->xy_c, xy_c, 2 * n * 8)) || (st = up(m->inc_ptr, inc_ptr.data(), (n + 1) * 4)) ||
       (st = up(m->inc_tri, inc.data(), 3 * (size_t)t_c * 4)))
     return cleanup_fail(st);
@@ -294,14 +367,23 @@ extern "C" int cgp_mesh_query(cgp_mesh m, int* n_c, int* t_c, int* n_e, int* n_f
   return CGP_OK;
 }
 
+extern "C" int cgp_mesh_levels(cgp_mesh m, int* levels, int* nodes) {
+  if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_mesh_levels: NULL mesh");
+  if (levels) *levels = m->levels;
+  if (nodes) std::memcpy(nodes, m->h_lvl_nodes.data(), m->h_lvl_nodes.size() * 4);
+  return CGP_OK;
+}
+
 extern "C" int cgp_mesh_fine_geometry(cgp_mesh m, double* xy_f, int* tri_f, int* edges) {
   if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_mesh_fine_geometry: NULL mesh");
   if (xy_f) CGP_CUDA(cudaMemcpy(xy_f, m->xy_f, 2 * (size_t)m->n_f * 8, cudaMemcpyDeviceToHost));
   if (edges) std::memcpy(edges, m->h_edges.data(), 2 * (size_t)m->n_e * 4);
   if (tri_f) {
-    for (int t = 0; t < m->t_c; ++t) {
-      const int a = m->h_tri_c[3 * t], b = m->h_tri_c[3 * t + 1], c = m->h_tri_c[3 * t + 2];
-      const int mab = m->h_tri_mid[3 * t], mbc = m->h_tri_mid[3 * t + 1], mca = m->h_tri_mid[3 * t + 2];
+    const std::vector<int>& tp = m->levels >= 2 ? m->h_tri_par : m->h_tri_c;
+    const std::vector<int>& mp = m->levels >= 2 ? m->h_mid_par : m->h_tri_mid;
+    for (int t = 0; t < m->t_par; ++t) {
+      const int a = tp[3 * t], b = tp[3 * t + 1], c = tp[3 * t + 2];
+      const int mab = mp[3 * t], mbc = mp[3 * t + 1], mca = mp[3 * t + 2];
       const int ch[4][3] = {{a, mab, mca}, {mab, b, mbc}, {mca, mbc, c}, {mab, mbc, mca}};
       for (int k = 0; k < 4; ++k)
         for (int l = 0; l < 3; ++l) tri_f[(size_t)(4 * t + k) * 3 + l] = ch[k][l];
@@ -328,6 +410,7 @@ extern "C" int cgp_mesh_destroy(cgp_mesh m) {
   cudaDeviceSynchronize();
   for (auto& pl : m->plans)
     if (pl.base) cudaFree(pl.base);
+  if (m->vinc_base) cudaFree(m->vinc_base);
   if (m->d_base) cudaFree(m->d_base);
   if (m->h_res) cudaFreeHost(m->h_res);
   delete m;

@@ -177,13 +177,13 @@ def evaluate(torch, mesh, net, xy_f, seeds, steps, B=(0.0, 0.0, 1.0), noise_std=
 
 def run_protocol(torch, mesh, xy_f, train_seeds=(0, 1, 2, 3, 4), train_stuart=(0.5, 1.0, 2.0, 5.0), steps=200,
                  test_seeds=(100, 101, 102, 103, 104), test_steps=200, iterations=(2000, 1000), lrs=(1e-3, 3e-4),
-                 batch=32, seed=0):
+                 batch=32, seed=0, noise_std=1e-3):
     """Generate training solves, train the network, evaluate on held-out seeds."""
     t0 = time.perf_counter()
     seqs = {}
     for stuart in train_stuart:           # the potential does not depend on N: solved per N as the protocol asks
         for s in train_seeds:
-            seqs[(stuart, s)] = solve_sequence(torch, mesh, xy_f, s, steps)
+            seqs[(stuart, s)] = solve_sequence(torch, mesh, xy_f, s, steps, noise_std=noise_std)
     gen_s = time.perf_counter() - t0
     distinct = [seqs[(train_stuart[0], s)] for s in train_seeds]
     samples = make_samples(torch, distinct)
@@ -194,7 +194,7 @@ def run_protocol(torch, mesh, xy_f, train_seeds=(0, 1, 2, 3, 4), train_stuart=(0
         losses += train(torch, net, samples, iterations=iters, batch=batch, lr=lr, seed=seed)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    ev = evaluate(torch, mesh, net, xy_f, test_seeds, test_steps)
+    ev = evaluate(torch, mesh, net, xy_f, test_seeds, test_steps, noise_std=noise_std)
     ev.update(training_solves=len(seqs) * steps, distinct_samples=int(samples[0].shape[0]),
               generation_seconds=gen_s, training_seconds=train_s, loss_first=losses[0], loss_last=losses[-1],
               train_iterations=int(sum(iterations)))

@@ -135,9 +135,10 @@ def test_one_adam_step_matches_the_oracle(cgp, setting):
     net.close()
 
 
-@pytest.mark.parametrize("shape", [(16, 8), (33, 17), (64, 32)])
+@pytest.mark.parametrize("shape", [(16, 8), (33, 17), (64, 32), (128, 64)])
 def test_fused_inference_matches_the_batched_forward(cgp, shape):
-    """cgp_gnn_predict (one cooperative launch over node chunks of 128, ragged last chunk)
+    """cgp_gnn_predict (one cooperative launch over 16-node chunks, ragged last chunk; the
+    batched forward when there are more chunks than co-resident blocks, as at 128x64)
     runs the batched kernels' arithmetic in the same order: the same FP32 outputs."""
     xy, tri = inputs.ogrid(*shape)
     m = cgp.Mesh(xy, tri)

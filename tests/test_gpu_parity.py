@@ -396,3 +396,69 @@ def test_autotune_times_candidates_and_caches_the_choice(cgp, tmp_path):
     assert info["status"] == cgp.CGP_OK
     assert rel(x.cpu().numpy(), ref["x"]) <= 1e-8
     m.close()
+
+
+# ----------------------------------------------------------------------------
+# nested coarsening levels k = 2, 3
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("levels", [2, 3])
+@pytest.mark.parametrize("name", ["one-triangle", "square", "ogrid-7x3", "ogrid-33x17"])
+def test_multilevel_mesh_maps_and_step_match_oracle(cgp, levels, name):
+    xy, tri = meshes()[name]
+    m = cgp.Mesh(xy, tri, levels)
+    om = O.OracleMesh(xy, tri, levels=levels)
+    assert m.levels == levels
+    assert m.level_nodes == [lv[0].shape[0] for lv in om.levels]
+    xy_f, tri_f, edges = m.fine_geometry()
+    np.testing.assert_array_equal(edges, om.edges)
+    np.testing.assert_array_equal(tri_f, om.tri_f)
+    np.testing.assert_array_equal(xy_f, om.xy_f)
+    # prolongation: one level at a time on both sides
+    rng = np.random.default_rng(3)
+    q = rng.standard_normal(m.n_c)
+    qf = torch.empty(m.n_f, dtype=torch.float64, device=DEV)
+    cgp.cgp_prolong(m.handle, T(q), qf)
+    torch.cuda.synchronize()
+    assert rel(qf.cpu().numpy(), om.prolong(q)) <= 1e-14
+    # gradient and force on the fine triangles
+    u, v = velocity_for(om)
+    phi = rng.standard_normal(m.n_f)
+    B, sigma = (0.3, 0.5, 1.1), 2.5
+    grad = torch.empty(2 * m.t_f, dtype=torch.float64, device=DEV)
+    force = torch.empty_like(grad)
+    cgp.cgp_lorentz(m.handle, T(phi), T(u), T(v), B, sigma, grad, force)
+    torch.cuda.synchronize()
+    g_ref, f_ref = O.lorentz(om.xy_f, om.tri_f, phi, u, v, B, sigma)
+    assert rel(grad.cpu().numpy().reshape(2, -1).T, g_ref) <= 1e-13
+    assert rel(force.cpu().numpy().reshape(2, -1).T, f_ref) <= 1e-13
+    # a whole CGP potential step at tight tolerance
+    if m.n_c >= 4:
+        out = run_step(cgp, m, u, v, B, sigma, tol=1e-12)
+        ref = om.solve(u, v, O.POTENTIAL, B=B, sigma=sigma, tol=1e-12)
+        assert rel(out["phi_f"], ref["phi_f"]) <= 1e-10
+        assert rel(out["force"], ref["force"]) <= 1e-9
+    m.close()
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("name", ["one-triangle", "square", "ogrid-7x3", "ogrid-33x17"])
+def test_velocity_correction_matches_oracle(cgp, levels, name):
+    xy, tri = meshes()[name]
+    m = cgp.Mesh(xy, tri, levels)
+    om = O.OracleMesh(xy, tri, levels=levels)
+    rng = np.random.default_rng(6)
+    p = rng.standard_normal(m.n_f)
+    ut, vt = rng.standard_normal(m.n_f), rng.standard_normal(m.n_f)
+    u = torch.empty(m.n_f, dtype=torch.float64, device=DEV)
+    v = torch.empty_like(u)
+    cgp.cgp_velocity_correct(m.handle, T(p), T(ut), T(vt), 0.05, u, v)
+    ref_u, ref_v = O.velocity_correct(om.xy_f, om.tri_f, p, ut, vt, 0.05)
+    assert rel(u.cpu().numpy() - ut, ref_u - ut) <= 1e-13
+    assert rel(v.cpu().numpy() - vt, ref_v - vt) <= 1e-13
+    # in place, and again (the incidence is built once)
+    uu, vv = T(ut), T(vt)
+    cgp.cgp_velocity_correct(m.handle, T(p), uu, vv, 0.05, uu, vv)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(uu.cpu().numpy(), u.cpu().numpy())
+    np.testing.assert_array_equal(vv.cpu().numpy(), v.cpu().numpy())
+    m.close()

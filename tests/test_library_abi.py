@@ -61,12 +61,15 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     with pytest.raises(cgp.CgpError) as e:
         cgp.cgp_assemble(xy, np.array([[0, 2, 5]], dtype=np.int32))
     assert e.value.status == cgp.CGP_ERR_INVALID_ARG
-    # only one coarsening level
-    with pytest.raises(cgp.CgpError) as e:
-        cgp.cgp_assemble(xy, np.array([[0, 2, 1]], dtype=np.int32), levels=2)
-    assert e.value.status == cgp.CGP_ERR_INVALID_ARG
+    # one to three coarsening levels (Eq. 18)
+    for bad in (0, 4):
+        with pytest.raises(cgp.CgpError) as e:
+            cgp.cgp_assemble(xy, np.array([[0, 2, 1]], dtype=np.int32), levels=bad)
+        assert e.value.status == cgp.CGP_ERR_INVALID_ARG and "levels" in str(e.value)
     # NULL handles
     assert lib.cgp_prolong(None, None, None, None) == cgp.CGP_ERR_INVALID_ARG
+    assert lib.cgp_velocity_correct(None, None, None, None, 0.05, None, None, None) == cgp.CGP_ERR_INVALID_ARG
+    assert lib.cgp_mesh_levels(None, None, None) == cgp.CGP_ERR_INVALID_ARG
     assert lib.cgp_set_tuning(None, 0, 0, 0, 0, 0) == cgp.CGP_ERR_INVALID_ARG
     assert lib.cgp_barrier_selftest(0, 0, 1, None) == cgp.CGP_ERR_INVALID_ARG
     assert b"nblk" in lib.cgp_last_error()

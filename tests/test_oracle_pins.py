@@ -447,3 +447,112 @@ def test_planted_mistakes_are_caught():
         return qf
 
     assert not check_prolong_linear(prolong_wrong_vertex, m)
+
+
+# ----------------------------------------------------------------------------
+# nested coarsening levels k = 2, 3 (Sect. 2.3, Eq. 18; prolongation one level at a time)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [2, 3])
+def test_nested_levels_counts_prefix_and_areas(k):
+    nt, nr = 12, 5
+    xy, tri = inputs.ogrid(nt, nr)
+    levels = O.split_levels(xy, tri, k)
+    for l in range(k):
+        xy_l, tri_l = levels[l][0], levels[l][1]
+        xy_n, tri_n = levels[l + 1][0], levels[l + 1][1]
+        # Eq. 18 per level, and the annulus count E = V + T the paper's four meshes obey (golden fixture)
+        assert tri_n.shape[0] == 4 * tri_l.shape[0]
+        assert xy_n.shape[0] == xy_l.shape[0] + (xy_l.shape[0] + tri_l.shape[0])
+        np.testing.assert_array_equal(xy_n[: xy_l.shape[0]], xy_l)     # injection is a prefix at every level
+    # level k of the n_theta x n_r O-grid has the node count of the 2^k n_theta x 2^k n_r O-grid
+    assert levels[k][0].shape[0] == (2 ** k * nt) * (2 ** k * nr + 1)
+    # the 4^k consecutive fine triangles from 4^k T tile coarse triangle T in equal, counter-clockwise parts
+    a_c, _, _ = O.p1_gradients(levels[0][0], levels[0][1].astype(np.int64))
+    a_f, _, _ = O.p1_gradients(levels[k][0], levels[k][1].astype(np.int64))
+    assert np.all(a_f > 0)
+    np.testing.assert_allclose(a_f.reshape(-1, 4 ** k), np.repeat(a_c[:, None], 4 ** k, axis=1) / 4 ** k,
+                               rtol=1e-12)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_nested_prolongation_is_the_coarse_p1_interpolant(k):
+    xy, tri = inputs.ogrid(10, 4)
+    om = O.OracleMesh(xy, tri, levels=k)
+    # exact on linear fields
+    lin = lambda p: 0.3 + 1.7 * p[:, 0] - 0.4 * p[:, 1]  # noqa: E731
+    np.testing.assert_allclose(om.prolong(lin(om.xy_c)), lin(om.xy_f), rtol=0, atol=1e-12)
+    # k one-level prolongations equal Eq. 20 evaluated directly in the coarse triangle of each fine node
+    rng = np.random.default_rng(5)
+    q = rng.standard_normal(om.n_c)
+    qf = om.prolong(q)
+    parent_c = np.arange(om.tri_f.shape[0]) // 4 ** k
+    direct = O.prolong(om.xy_c, om.tri_c, om.xy_f, om.tri_f, parent_c, q)
+    np.testing.assert_allclose(qf, direct, rtol=0, atol=1e-12 * np.max(np.abs(q)))
+    # so the fine gradients are the coarse triangle's gradient on all of its 4^k descendants
+    gx_c, gy_c = O.gradient(om.xy_c, om.tri_c, q)
+    gx_f, gy_f = O.gradient(om.xy_f, om.tri_f, qf)
+    scale = np.max(np.abs(np.concatenate([gx_c, gy_c])))
+    np.testing.assert_allclose(gx_f, np.repeat(gx_c, 4 ** k), rtol=0, atol=1e-10 * scale)
+    np.testing.assert_allclose(gy_f, np.repeat(gy_c, 4 ** k), rtol=0, atol=1e-10 * scale)
+
+
+# ----------------------------------------------------------------------------
+# velocity correction (Eqs. 16-17) with the lumped P1 mass
+# ----------------------------------------------------------------------------
+def regular_grid(n):
+    """Unit square, n x n cells, every cell cut by its rising diagonal (counter-clockwise)."""
+    g = np.linspace(0.0, 1.0, n + 1)
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)
+    tri = []
+    for j in range(n):
+        for i in range(n):
+            a, b, c, d = j * (n + 1) + i, j * (n + 1) + i + 1, (j + 1) * (n + 1) + i + 1, (j + 1) * (n + 1) + i
+            tri += [[a, b, c], [a, c, d]]
+    return xy, np.array(tri, dtype=np.int32)
+
+
+def test_velocity_correction_is_exact_for_a_linear_pressure():
+    xy, tri = inputs.ogrid(9, 4)
+    xy_f, tri_f, _, _ = O.split4(xy, tri)
+    rng = np.random.default_rng(8)
+    ut, vt = rng.standard_normal(xy_f.shape[0]), rng.standard_normal(xy_f.shape[0])
+    p = 2.0 - 0.7 * xy_f[:, 0] + 1.3 * xy_f[:, 1]
+    u, v = O.velocity_correct(xy_f, tri_f, p, ut, vt, 0.05)
+    np.testing.assert_allclose(u, ut - 0.05 * (-0.7), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(v, vt - 0.05 * 1.3, rtol=0, atol=1e-12)
+
+
+def test_velocity_correction_recovers_quadratic_gradients_on_symmetric_patches():
+    # the area-weighted mean of P1 gradients over a point-symmetric patch is exact for quadratics
+    xy, tri = regular_grid(6)
+    x, y = xy[:, 0], xy[:, 1]
+    p = 0.5 * x * x - 1.2 * x * y + 0.8 * y * y
+    u, v = O.velocity_correct(xy, tri, p, np.zeros_like(x), np.zeros_like(x), 1.0)
+    interior = (x > 1e-9) & (x < 1 - 1e-9) & (y > 1e-9) & (y < 1 - 1e-9)
+    np.testing.assert_allclose(-u[interior], (x - 1.2 * y)[interior], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(-v[interior], (-1.2 * x + 1.6 * y)[interior], rtol=0, atol=1e-12)
+    # the check is not vacuous: on the one-sided boundary patches the recovery is not exact
+    assert np.max(np.abs(-u[~interior] - (x - 1.2 * y)[~interior])) > 1e-3
+
+
+def test_velocity_correction_integrates_to_the_boundary_integral():
+    # sum_i M_L,ii (u~_i - u_i) / c = int grad p_h dx = closed integral of p_h n ds (Gauss), on an annulus
+    xy, tri = inputs.ogrid(11, 5)
+    xy_f, tri_f, _, _ = O.split4(xy, tri)
+    rng = np.random.default_rng(4)
+    p = rng.standard_normal(xy_f.shape[0])
+    c = 0.05
+    u, v = O.velocity_correct(xy_f, tri_f, p, np.zeros(xy_f.shape[0]), np.zeros(xy_f.shape[0]), c)
+    area2, _, _ = O.p1_gradients(xy_f, tri_f.astype(np.int64))
+    mass = np.bincount(tri_f.ravel(), weights=np.repeat(area2 / 6.0, 3), minlength=xy_f.shape[0])
+    lhs = np.array([np.sum(mass * -u), np.sum(mass * -v)]) / c
+    # boundary edges: sides used by one triangle only, oriented as in their (counter-clockwise) triangle
+    sides = np.concatenate([tri_f[:, [0, 1]], tri_f[:, [1, 2]], tri_f[:, [2, 0]]])
+    key = np.minimum(sides[:, 0], sides[:, 1]) * xy_f.shape[0] + np.maximum(sides[:, 0], sides[:, 1])
+    uniq, cnt = np.unique(key, return_counts=True)
+    bnd = sides[np.isin(key, uniq[cnt == 1])]
+    a, b = bnd[:, 0], bnd[:, 1]
+    pm = 0.5 * (p[a] + p[b])
+    rhs = np.array([np.sum(pm * (xy_f[b, 1] - xy_f[a, 1])), np.sum(-pm * (xy_f[b, 0] - xy_f[a, 0]))])
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-10, atol=1e-10 * np.sum(np.abs(pm)))
