@@ -399,6 +399,7 @@ def run_mine(args, rank, world, local_rank):
         from paper_2003_00082_gb300 import configs
         result["mixed_64x32"] = run_mixed_small(cgp, inputs, torch, dev)
         result["levels"] = run_levels(cgp, inputs, torch, dev, flush)
+        result["far_field"] = run_far_field(cgp, inputs, torch, dev, flush)
         result["batched"] = run_batched(cgp, inputs, configs, torch, dev, flush, peak)
         result["learned_guess"] = run_learned_guess(cgp, inputs, torch)
     mesh.close()
@@ -524,6 +525,51 @@ def run_levels(cgp, inputs, torch, dev, flush, steps=10, warm=3):
                         "rel_res_true_max": max(r["rel_res_true"] for r in recs),
                         "launch": cgp.cgp_last_launch(m.handle)}
         m.close()
+    return out
+
+
+def run_far_field(cgp, inputs, torch, dev, flush, steps=8, warm=3):
+    """c2 potential solves (512x256, vortex train, B = k, tol 1e-8, previous-step x0) with the
+    natural condition everywhere and with phi = 0 on the outer boundary: iterations and solves/s."""
+    xy, tri = inputs.ogrid(N_THETA, N_R)
+    m = cgp.Mesh(xy, tri)
+    xy_f, _, _ = m.fine_geometry()
+    f64 = dict(dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    U = []
+    for t in range(warm + steps):
+        u, v = inputs.velocity(xy_f, t, SEED, vortices=True)
+        U.append((torch.as_tensor(u, device=dev), torch.as_tensor(v, device=dev)))
+    B = torch.empty((warm + steps, m.n_c), **f64)
+    for t in range(warm + steps):
+        cgp.cgp_restrict(m.handle, cgp.CGP_RHS_POTENTIAL, B_FIELD, RHO_OVER_DT, U[t][0], U[t][1], B[t])
+    out = {"workload": "512x256 potential solves, vortex train, B = k, tol 1e-8, previous-step x0"}
+    for name, mode in (("natural", 0), ("dirichlet_far", 1)):
+        cgp.cgp_set_far_field(m.handle, mode)
+        x = torch.zeros(m.n_c, **f64)
+        cgp.cgp_autotune(m.handle, cgp.CGP_FP64, B[0], x)
+        x.zero_()
+        infos = torch.zeros((warm + steps) * cgp.INFO_BYTES, dtype=torch.uint8, device=dev)
+        ms = 0.0
+        for t in range(warm + steps):
+            if t >= warm:
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            cgp.cgp_poisson_solve_async(m.handle, B[t], x, tol=TOL, use_x0=t > 0,
+                                        info_dev=infos.data_ptr() + t * cgp.INFO_BYTES)
+            if t >= warm:
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        recs = cgp.decode_infos(bytes(infos.cpu().numpy()), warm + steps)[warm:]
+        out[name] = {"solves_per_s": steps / (ms * 1e-3),
+                     "iterations_mean": statistics.mean(r["iterations"] for r in recs),
+                     "all_converged": all(r["status"] == cgp.CGP_OK for r in recs)}
+    cgp.cgp_set_far_field(m.handle, 0)
+    m.close()
     return out
 
 
@@ -855,6 +901,8 @@ def main():
             line["mixed_64x32"] = res["mixed_64x32"]
         if "levels" in res:
             line["levels"] = res["levels"]
+        if "far_field" in res:
+            line["far_field"] = res["far_field"]
         if "batched" in res:
             line["batched"] = res["batched"]
         if "learned_guess" in res:

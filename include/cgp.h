@@ -107,6 +107,29 @@ int cgp_mesh_query(cgp_mesh m, int* n_c, int* t_c, int* n_e, int* n_f, int* t_f,
 int cgp_mesh_levels(cgp_mesh m, int* levels, int* nodes);
 
 /*
+ * cgp_set_far_field - boundary condition of the solves on this mesh far from
+ * the cylinder.  dirichlet = 0 (default): the natural condition everywhere
+ * (d_n x = F . n, the reading of "the electric field vanishes far away" as
+ * j . n = 0; K is singular and b, x0 and x are projected to mean zero).
+ * dirichlet = 1: x = 0 on the outer boundary (the other reading of the same
+ * sentence, Sect. 3), the natural condition on the other boundaries; the
+ * outer-boundary rows and columns of K become the identity, b and x0 are
+ * taken as zero there, nothing is projected.  The outer boundary is every
+ * boundary curve (sides of one triangle, oriented as in their triangle) of
+ * positive signed area; curves around holes are negative.  The first call
+ * with 1 builds that system (synchronous; one allocation of about
+ * 12 nnz + 13 n_c bytes, freed with the mesh).  Affects every later solve on
+ * the mesh, batched ones included.  INVALID_ARG for other values or when the
+ * mesh has no outer boundary.
+ */
+int cgp_set_far_field(cgp_mesh m, int dirichlet);
+
+/* The outer-boundary nodes the Dirichlet variant holds at zero, ascending:
+ * count (nullable) and nodes host [count] (nullable); INVALID_ARG before the
+ * first cgp_set_far_field(m, 1). */
+int cgp_far_field_nodes(cgp_mesh m, int* count, int* nodes);
+
+/*
  * cgp_mesh_fine_geometry - host copies of the fine mesh (synchronous).
  * xy_f  host [n_f][2] or NULL;  tri_f host [t_f][3] or NULL;  edges host [n_e][2]
  * (the coarse edges) or NULL.

@@ -44,6 +44,7 @@ import math
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.csgraph  # noqa: F401  (connected components of the boundary curves)
 
 # solver status codes of the oracle (its own numbering)
 OK = 0
@@ -270,6 +271,38 @@ def dense_solve(K, b):
     return np.linalg.solve(Kd + np.ones((n, n)) / n, project_mean(b))
 
 
+def outer_boundary(xy, tri):
+    """Nodes on the outer boundary: boundary edges (sides of one triangle only), oriented as in
+    their counter-clockwise triangle, grouped into connected boundary curves; a curve enclosing
+    the domain has positive signed area, one around a hole negative."""
+    xy = np.asarray(xy, dtype=np.float64)
+    tri = np.asarray(tri, dtype=np.int64)
+    n = xy.shape[0]
+    sides = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]])
+    key = np.minimum(sides[:, 0], sides[:, 1]) * n + np.maximum(sides[:, 0], sides[:, 1])
+    uniq, cnt = np.unique(key, return_counts=True)
+    bnd = sides[np.isin(key, uniq[cnt == 1])]
+    G = sp.coo_matrix((np.ones(len(bnd)), (bnd[:, 0], bnd[:, 1])), shape=(n, n))
+    _, label = sp.csgraph.connected_components(G, directed=False)
+    a, b = bnd[:, 0], bnd[:, 1]
+    area2 = np.bincount(label[a], weights=xy[a, 0] * xy[b, 1] - xy[b, 0] * xy[a, 1],
+                        minlength=label.max() + 1)
+    nodes = np.unique(bnd.ravel())
+    return nodes[area2[label[nodes]] > 0]
+
+
+def dirichlet_system(K, fixed):
+    """K with the rows and columns of the fixed nodes replaced by the identity (their value is zero),
+    and its diagonal: the far-field reading phi = 0 on the outer boundary."""
+    n = K.shape[0]
+    free = np.ones(n)
+    free[fixed] = 0.0
+    Df = sp.diags(free)
+    Kd = (Df @ K @ Df + sp.diags(1.0 - free)).tocsr()
+    Kd.sort_indices()
+    return Kd, Kd.diagonal().copy()
+
+
 # ----------------------------------------------------------------------------
 # 6. prolongation by P1 shape functions (Eq. 20)
 # ----------------------------------------------------------------------------
@@ -449,13 +482,20 @@ class OracleMesh:
         return q
 
     def solve(self, u_f, v_f, kind=POTENTIAL, B=(0.0, 0.0, 1.0), sigma=1.0, rho_over_dt=20.0,
-              tol=1e-8, x0=None, max_it=20000, mixed=False, inner_tol=1e-4):
-        """One CGP solve: restrict, RHS, PCG (or mixed IR), prolong, gradient and force."""
+              tol=1e-8, x0=None, max_it=20000, mixed=False, inner_tol=1e-4, far_dirichlet=False):
+        """One CGP solve: restrict, RHS, PCG (or mixed IR), prolong, gradient and force.
+        far_dirichlet: phi = 0 on the outer boundary instead of the natural condition there."""
         u_c = self.restrict(u_f)
         v_c = self.restrict(v_f)
         Fx, Fy = source_field(kind, u_c, v_c, B, rho_over_dt)
         b = rhs(self.Gx, self.Gy, Fx, Fy)
-        if mixed:
+        if far_dirichlet:
+            fixed = outer_boundary(self.xy_c, self.tri_c)
+            Kd, dd = dirichlet_system(self.K, fixed)
+            bd = b.copy()
+            bd[fixed] = 0.0
+            info = pcg(Kd, dd, bd, x0, tol=tol, max_it=max_it, project=False)
+        elif mixed:
             info = mixed_ir(self.K, self.d, b, x0, tol=tol, inner_tol=inner_tol)
         else:
             info = pcg(self.K, self.d, b, x0, tol=tol, max_it=max_it)

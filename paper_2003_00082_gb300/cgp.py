@@ -32,7 +32,8 @@ CGP_FP64 = 0
 CGP_MIXED = 1
 CGP_FP32 = 1          # precision argument of cgp_spmv for the FP32 copy of K
 
-EXPORTS = ("cgp_assemble", "cgp_mesh_query", "cgp_mesh_levels", "cgp_mesh_fine_geometry", "cgp_mesh_matrices",
+EXPORTS = ("cgp_assemble", "cgp_mesh_query", "cgp_mesh_levels", "cgp_set_far_field", "cgp_far_field_nodes",
+           "cgp_mesh_fine_geometry", "cgp_mesh_matrices",
            "cgp_restrict", "cgp_poisson_solve", "cgp_poisson_solve_async",
            "cgp_poisson_solve_noalloc", "cgp_prolong", "cgp_lorentz", "cgp_velocity_correct", "cgp_spmv",
            "cgp_set_tuning", "cgp_get_tuning", "cgp_autotune", "cgp_last_launch", "cgp_barrier_selftest",
@@ -98,6 +99,8 @@ def load(path: str | None = None):
                                       ctypes.POINTER(SolveInfo), vp],
         "cgp_prolong": [vp, vp, vp, vp],
         "cgp_mesh_levels": [vp, ip, ip],
+        "cgp_set_far_field": [vp, i],
+        "cgp_far_field_nodes": [vp, ip, ip],
         "cgp_velocity_correct": [vp, vp, vp, vp, d, vp, vp, vp],
         "cgp_lorentz": [vp, vp, vp, vp, dp, d, vp, vp, vp],
         "cgp_spmv": [vp, i, vp, vp, vp],
@@ -200,6 +203,18 @@ def cgp_mesh_levels(mesh):
     nodes = (ctypes.c_int * (k.value + 1))()
     _check(load().cgp_mesh_levels(mesh, None, nodes))
     return k.value, list(nodes)
+
+
+def cgp_set_far_field(mesh, dirichlet):
+    _check(load().cgp_set_far_field(mesh, int(dirichlet)))
+
+
+def cgp_far_field_nodes(mesh):
+    cnt = ctypes.c_int()
+    _check(load().cgp_far_field_nodes(mesh, ctypes.byref(cnt), None))
+    nodes = np.empty(cnt.value, dtype=np.int32)
+    _check(load().cgp_far_field_nodes(mesh, None, nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return nodes
 
 
 def cgp_mesh_fine_geometry(mesh):

@@ -117,6 +117,16 @@ struct cgp_mesh_impl {
   SolveResult* h_res = nullptr;  // pinned host mirror
   int max_blocks = 0;
 
+  // far-field Dirichlet variant (phi = 0 on the outer boundary), built on first use
+  int far_dirichlet = 0;
+  std::vector<int> h_outer;        // coarse nodes on the outer boundary loops
+  unsigned char* fixed = nullptr;  // [n_c] 1 on those nodes
+  double* Kd = nullptr;            // [nnz] K with their rows and columns replaced by the identity
+  float* Kd32 = nullptr;
+  double* dinvd = nullptr;         // [n_c]
+  float* dinvd32 = nullptr;
+  void* dir_base = nullptr;
+
   // fine node -> incident fine triangles, each entry the other two vertices in
   // counter-clockwise order (built on the first velocity correction)
   int* vinc_ptr = nullptr;   // [n_f + 1]

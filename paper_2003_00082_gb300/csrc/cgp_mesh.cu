@@ -367,6 +367,110 @@ extern "C" int cgp_mesh_query(cgp_mesh m, int* n_c, int* t_c, int* n_e, int* n_f
   return CGP_OK;
 }
 
+// Nodes of the outer boundary: boundary edges (sides of exactly one triangle)
+// oriented as in their counter-clockwise triangle form closed loops; a loop
+// around the domain runs counter-clockwise (positive signed area), a loop
+// around a hole clockwise.
+static std::vector<int> outer_boundary_nodes(const cgp_mesh_impl* m, const double* xy) {
+  const int n = m->n_c, t = m->t_c;
+  std::vector<std::pair<long long, int>> sides(3 * (size_t)t);   // (undirected key, directed side)
+  for (int q = 0; q < t; ++q)
+    for (int k = 0; k < 3; ++k) {
+      const int a = m->h_tri_c[3 * q + k], b = m->h_tri_c[3 * q + (k + 1) % 3];
+      sides[3 * (size_t)q + k] = {(long long)std::min(a, b) * n + std::max(a, b), 3 * q + k};
+    }
+  std::sort(sides.begin(), sides.end());
+  std::vector<int> next(n, -1);
+  for (size_t i = 0; i < sides.size();) {
+    size_t j = i;
+    while (j < sides.size() && sides[j].first == sides[i].first) ++j;
+    if (j - i == 1) {
+      const int s = sides[i].second, q = s / 3, k = s % 3;
+      next[m->h_tri_c[3 * q + k]] = m->h_tri_c[3 * q + (k + 1) % 3];
+    }
+    i = j;
+  }
+  std::vector<int> out;
+  std::vector<char> seen(n, 0);
+  for (int s = 0; s < n; ++s) {
+    if (next[s] < 0 || seen[s]) continue;
+    std::vector<int> loop;
+    double area2 = 0.0;
+    for (int a = s; !seen[a] && next[a] >= 0; a = next[a]) {
+      seen[a] = 1;
+      loop.push_back(a);
+      const int b = next[a];
+      area2 += xy[2 * a] * xy[2 * b + 1] - xy[2 * b] * xy[2 * a + 1];
+    }
+    if (area2 > 0.0) out.insert(out.end(), loop.begin(), loop.end());
+  }
+  std::sort(out.begin(), out.end());
+  return out;
+}
+
+extern "C" int cgp_set_far_field(cgp_mesh m, int dirichlet) {
+  if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_set_far_field: NULL mesh");
+  if (dirichlet != 0 && dirichlet != 1) return fail(CGP_ERR_INVALID_ARG, "cgp_set_far_field: dirichlet must be 0 or 1");
+  if (dirichlet && !m->dir_base) {
+    const size_t n = m->n_c, nz = m->nnz;
+    std::vector<double> K(nz), xy(2 * n);
+    CGP_CUDA(cudaDeviceSynchronize());
+    CGP_CUDA(cudaMemcpy(K.data(), m->K, nz * 8, cudaMemcpyDeviceToHost));
+    CGP_CUDA(cudaMemcpy(xy.data(), m->xy_c, 2 * n * 8, cudaMemcpyDeviceToHost));
+    m->h_outer = outer_boundary_nodes(m, xy.data());
+    if (m->h_outer.empty()) return fail(CGP_ERR_INVALID_ARG, "cgp_set_far_field: the mesh has no outer boundary");
+    std::vector<unsigned char> fix(n, 0);
+    for (int i : m->h_outer) fix[i] = 1;
+    std::vector<float> K32(nz), di32(n);
+    std::vector<double> di(n);
+    for (size_t i = 0; i < n; ++i) {
+      double diag = 0.0;
+      for (int k = m->h_rowptr[i]; k < m->h_rowptr[i + 1]; ++k) {
+        const int j = m->h_col[k];
+        if (j == (int)i) {
+          if (fix[i]) K[k] = 1.0;       // identity row of a fixed node
+          diag = K[k];
+        } else if (fix[i] || fix[j]) {
+          K[k] = 0.0;                   // eliminated coupling (the fixed value is zero)
+        }
+        K32[k] = (float)K[k];
+      }
+      di[i] = 1.0 / diag;
+      di32[i] = (float)di[i];
+    }
+    const size_t o_k32 = align_up(nz * 8, 256), o_d = o_k32 + align_up(nz * 4, 256),
+                 o_d32 = o_d + align_up(n * 8, 256), o_f = o_d32 + align_up(n * 4, 256), bytes = o_f + n;
+    void* base = nullptr;
+    CGP_CUDA(cudaMalloc(&base, bytes));
+    char* b = static_cast<char*>(base);
+    cudaError_t e = cudaMemcpy(b, K.data(), nz * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_k32, K32.data(), nz * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_d, di.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_d32, di32.data(), n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + o_f, fix.data(), n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(base);
+      return cuda_fail(e, "cudaMemcpy(far-field system)");
+    }
+    m->dir_base = base;
+    m->Kd = reinterpret_cast<double*>(b);
+    m->Kd32 = reinterpret_cast<float*>(b + o_k32);
+    m->dinvd = reinterpret_cast<double*>(b + o_d);
+    m->dinvd32 = reinterpret_cast<float*>(b + o_d32);
+    m->fixed = reinterpret_cast<unsigned char*>(b + o_f);
+  }
+  m->far_dirichlet = dirichlet;
+  return CGP_OK;
+}
+
+extern "C" int cgp_far_field_nodes(cgp_mesh m, int* count, int* nodes) {
+  if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_far_field_nodes: NULL mesh");
+  if (!m->dir_base) return fail(CGP_ERR_INVALID_ARG, "cgp_far_field_nodes: call cgp_set_far_field(m, 1) first");
+  if (count) *count = (int)m->h_outer.size();
+  if (nodes) std::memcpy(nodes, m->h_outer.data(), m->h_outer.size() * 4);
+  return CGP_OK;
+}
+
 extern "C" int cgp_mesh_levels(cgp_mesh m, int* levels, int* nodes) {
   if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_mesh_levels: NULL mesh");
   if (levels) *levels = m->levels;
@@ -411,6 +515,7 @@ extern "C" int cgp_mesh_destroy(cgp_mesh m) {
   for (auto& pl : m->plans)
     if (pl.base) cudaFree(pl.base);
   if (m->vinc_base) cudaFree(m->vinc_base);
+  if (m->dir_base) cudaFree(m->dir_base);
   if (m->d_base) cudaFree(m->d_base);
   if (m->h_res) cudaFreeHost(m->h_res);
   delete m;

@@ -74,6 +74,7 @@ struct Desc {
   double tol, inner_tol;
   int max_it, max_sweeps, use_x0, mixed;
   int classic;        // FP64: two barriers per iteration (Saad, Alg. 9.1) instead of the single-reduction form
+  const unsigned char* fixed;  // far-field Dirichlet rows (phi = 0), or NULL for the natural condition everywhere
   int res_nnz_cap;    // RES: capacity of the shared-memory CSR slice
   int halo_cap;       // RES: capacity of the halo gather buffer
   const int* lcol;    // RES: columns renumbered per block (halo plan)
@@ -81,6 +82,10 @@ struct Desc {
   const int* hidx;
   long long spin_ns;
 };
+
+// Rows held at zero by the far-field Dirichlet condition; with it, K has no
+// null space and b, x0 and x are not projected to mean zero.
+__device__ __forceinline__ bool is_fixed(const Desc& d, int i) { return d.fixed && d.fixed[i]; }
 
 template <typename V>
 __device__ __forceinline__ V warp_sum(V v) {
@@ -434,15 +439,15 @@ __device__ void solve_fp64(const Desc& d, int lb, Shared& sh) {
     get_totals<2>(d, red, sh);
     ++red;
   }
-  const double mb = sh.tot[0] / d.n, mx = sh.tot[1] / d.n;
+  const double mb = d.fixed ? 0.0 : sh.tot[0] / d.n, mx = d.fixed ? 0.0 : sh.tot[1] / d.n;
   // ---- projected b and x0; x0 published for the first product ----
   {
     double v1[1] = {0.0};
     for (int i = tid; i < nloc; i += bd) {
-      const double bi = d.b[r0 + i] - mb;
+      const double bi = is_fixed(d, r0 + i) ? 0.0 : d.b[r0 + i] - mb;
       L.bp[i] = bi;
       v1[0] += bi * bi;
-      const double xi = d.use_x0 ? d.x[r0 + i] - mx : 0.0;
+      const double xi = (d.use_x0 && !is_fixed(d, r0 + i)) ? d.x[r0 + i] - mx : 0.0;
       L.x[i] = xi;
       if (RES) {
         d.x[r0 + i] = xi;
@@ -593,7 +598,7 @@ __device__ void solve_fp64(const Desc& d, int lb, Shared& sh) {
     get_totals<1>(d, red, sh);
     ++red;
   }
-  const double mxf = sh.tot[0] / d.n;
+  const double mxf = d.fixed ? 0.0 : sh.tot[0] / d.n;
   for (int i = tid; i < nloc; i += bd) {
     const double xi = L.x[i] - mxf;
     L.x[i] = xi;
@@ -738,13 +743,13 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
   }
   // ---- projected b and x0; x0 published for the first product ----
   {
-    const double mb = sh.tot[0] / d.n, mx = sh.tot[1] / d.n;
+    const double mb = d.fixed ? 0.0 : sh.tot[0] / d.n, mx = d.fixed ? 0.0 : sh.tot[1] / d.n;
     double v1[1] = {0.0};
     for (int i = tid; i < nloc; i += bd) {
-      const double bi = d.b[r0 + i] - mb;
+      const double bi = is_fixed(d, r0 + i) ? 0.0 : d.b[r0 + i] - mb;
       bp[i] = bi;
       v1[0] += bi * bi;
-      const double xi = d.use_x0 ? d.x[r0 + i] - mx : 0.0;
+      const double xi = (d.use_x0 && !is_fixed(d, r0 + i)) ? d.x[r0 + i] - mx : 0.0;
       x[i] = xi;
       if (RES) d.x[r0 + i] = xi;
     }
@@ -948,7 +953,7 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       get_totals<1>(d, red, sh);
       ++red;
     }
-    const double mxf = sh.tot[0] / d.n;
+    const double mxf = d.fixed ? 0.0 : sh.tot[0] / d.n;
     for (int i = tid; i < nloc; i += bd) {
       const double xi = x[i] - mxf;
       x[i] = xi;
@@ -1150,13 +1155,13 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
     ++red;
   }
   {
-    const double mb = sh.tot[0] / d.n, mx = sh.tot[1] / d.n;
+    const double mb = d.fixed ? 0.0 : sh.tot[0] / d.n, mx = d.fixed ? 0.0 : sh.tot[1] / d.n;
     double v1[1] = {0.0};
     for (int i = tid; i < nloc; i += bd) {
-      const double bi = d.b[r0 + i] - mb;
+      const double bi = is_fixed(d, r0 + i) ? 0.0 : d.b[r0 + i] - mb;
       bp[i] = bi;
       v1[0] += bi * bi;
-      x[i] = d.use_x0 ? x[i] - mx : 0.0;
+      x[i] = (d.use_x0 && !is_fixed(d, r0 + i)) ? x[i] - mx : 0.0;
     }
     put_partials<1>(d, lb, red, v1, sh);
     if (!grp.sync(sh)) return;
@@ -1195,7 +1200,7 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
       ++red;
     }
     {
-      const double mr = sh.tot[0] / d.n;
+      const double mr = d.fixed ? 0.0 : sh.tot[0] / d.n;
       double v1[1] = {0.0};
       for (int i = tid; i < nloc; i += bd) {
         const double ri = r64[i] - mr;
@@ -1369,7 +1374,7 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
       if (!grp.sync(sh)) return;
       get_totals<1>(d, red, sh);
       ++red;
-      const double mx = sh.tot[0] / d.n;
+      const double mx = d.fixed ? 0.0 : sh.tot[0] / d.n;
       for (int i = tid; i < nloc; i += bd) x[i] -= mx;
       if (!grp.sync(sh)) return;
     }
@@ -1657,10 +1662,11 @@ Desc make_desc(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opt
   d.n = m->n_c;
   d.rowptr = m->rowptr;
   d.col = m->col;
-  d.val = m->K;
-  d.val32 = m->K32;
-  d.dinv = m->dinv;
-  d.dinv32 = m->dinv32;
+  d.val = m->far_dirichlet ? m->Kd : m->K;
+  d.val32 = m->far_dirichlet ? m->Kd32 : m->K32;
+  d.dinv = m->far_dirichlet ? m->dinvd : m->dinv;
+  d.dinv32 = m->far_dirichlet ? m->dinvd32 : m->dinv32;
+  d.fixed = m->far_dirichlet ? m->fixed : nullptr;
   d.b = b;
   d.x = x;
   d.bp = m->bp;

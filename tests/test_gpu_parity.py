@@ -462,3 +462,34 @@ def test_velocity_correction_matches_oracle(cgp, levels, name):
     np.testing.assert_array_equal(uu.cpu().numpy(), u.cpu().numpy())
     np.testing.assert_array_equal(vv.cpu().numpy(), v.cpu().numpy())
     m.close()
+
+
+# ----------------------------------------------------------------------------
+# far-field Dirichlet variant
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,flags", [(0, 0), (0, 1), (0, 2), (1, 0)])
+@pytest.mark.parametrize("name", ["square", "ogrid-7x3", "ogrid-33x17", "ogrid-64x32"])
+def test_far_field_dirichlet_solve_matches_oracle(cgp, name, precision, flags):
+    xy, tri = meshes()[name]
+    m = cgp.Mesh(xy, tri)
+    om = O.OracleMesh(xy, tri)
+    cgp.cgp_set_far_field(m.handle, 1)
+    np.testing.assert_array_equal(cgp.cgp_far_field_nodes(m.handle), O.outer_boundary(xy, tri))
+    what = cgp.CGP_TUNE_SOLVE_MIXED if precision else cgp.CGP_TUNE_SOLVE_FP64
+    cgp.cgp_set_tuning(m.handle, what, 0, 0, 0, flags)
+    u, v = velocity_for(om)
+    B, sigma = (0.2, -0.3, 1.0), 1.5
+    tol = 1e-8 if precision else 1e-12
+    out = run_step(cgp, m, u, v, B, sigma, tol=tol, precision=precision)
+    ref = om.solve(u, v, O.POTENTIAL, B=B, sigma=sigma, tol=1e-13, far_dirichlet=True)
+    assert out["info"]["status"] == cgp.CGP_OK, out["info"]
+    fixed = O.outer_boundary(xy, tri)
+    assert np.all(out["phi_c"][fixed] == 0.0)
+    assert rel(out["phi_c"], ref["phi_c"]) <= (1e-7 if precision else 1e-10)
+    assert rel(out["force"], ref["force"]) <= (1e-6 if precision else 1e-9)
+    # back to the natural condition: the Neumann answer again
+    cgp.cgp_set_far_field(m.handle, 0)
+    out_n = run_step(cgp, m, u, v, B, sigma, tol=1e-12)
+    ref_n = om.solve(u, v, O.POTENTIAL, B=B, sigma=sigma, tol=1e-13)
+    assert rel(out_n["phi_c"], ref_n["phi_c"]) <= 1e-10
+    m.close()

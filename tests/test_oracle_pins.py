@@ -556,3 +556,35 @@ def test_velocity_correction_integrates_to_the_boundary_integral():
     pm = 0.5 * (p[a] + p[b])
     rhs = np.array([np.sum(pm * (xy_f[b, 1] - xy_f[a, 1])), np.sum(-pm * (xy_f[b, 0] - xy_f[a, 0]))])
     np.testing.assert_allclose(lhs, rhs, rtol=1e-10, atol=1e-10 * np.sum(np.abs(pm)))
+
+
+# ----------------------------------------------------------------------------
+# far-field Dirichlet variant: phi = 0 on the outer boundary (reading of "the electric field vanishes far away")
+# ----------------------------------------------------------------------------
+def test_outer_boundary_is_the_far_ring():
+    nt, nr = 10, 4
+    xy, tri = inputs.ogrid(nt, nr)
+    np.testing.assert_array_equal(O.outer_boundary(xy, tri), np.arange(nr * nt, (nr + 1) * nt))
+    # a mesh without a hole: its whole boundary
+    sq = (np.array([[2.0, 1.0], [3.0, 1.0], [3.0, 2.0], [2.0, 2.0], [2.5, 1.5]]),
+          np.array([[0, 1, 4], [1, 2, 4], [2, 3, 4], [3, 0, 4]]))
+    np.testing.assert_array_equal(O.outer_boundary(*sq), [0, 1, 2, 3])
+
+
+def test_far_field_dirichlet_potential_converges_to_its_closed_form():
+    # potential flow, B = k: Laplace equation, d_r phi = -2 U sin(theta) on the cylinder (natural
+    # condition j.n = 0), phi = 0 at r = R: phi = alpha (r - R^2 / r) sin(theta),
+    # alpha = -2 U a^2 / (a^2 + R^2)
+    a, R, U = inputs.R_IN, inputs.R_OUT, 1.0
+    alpha = -2.0 * U * a * a / (a * a + R * R)
+    errs = []
+    for nt, nr in ((32, 16), (64, 32)):
+        xy, tri = inputs.ogrid(nt, nr)
+        om = O.OracleMesh(xy, tri)
+        u, v = inputs.potential_flow(om.xy_f)
+        out = om.solve(u, v, O.POTENTIAL, B=(0.0, 0.0, 1.0), tol=1e-13, far_dirichlet=True)
+        r = np.hypot(xy[:, 0], xy[:, 1])
+        exact = alpha * (r - R * R / r) * (xy[:, 1] / r)
+        errs.append(np.linalg.norm(out["phi_c"] - exact) / np.linalg.norm(exact))
+        assert np.all(out["phi_c"][nr * nt:] == 0.0)
+    assert errs[1] < 0.05 and errs[0] / errs[1] > 3.0, errs     # second-order convergence
