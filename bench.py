@@ -56,9 +56,9 @@ def workload_config(precision="fp64"):
 # taken on: when the sources' hash differs the traffic is reported as null.
 SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_sync.h", "cgp_fixed.h", "cgp_internal.h")
 SOLVER_TRAFFIC = {
-    "sha256": "228da2b8365f977c7e6df9b2117738beec735534842ca332a3b8186155765069",
-    "fp64": 14491904 + 246528,
-    "mixed": 21242880 + 246016,
+    "sha256": "e300e520628485d5a520861a794e3337ee2473253602a213bfa857e6ed8f793f",
+    "fp64": 14513408 + 249856,
+    "mixed": 21243904 + 247040,
 }
 
 
@@ -698,6 +698,30 @@ def spmv_bench(cgp, inputs, torch, dev, peak, reps=20):
         key = "fp64" if prec == cgp.CGP_FP64 else "fp32"
         out[key] = {"best_lanes": best, "ms": per[best], "gb_s": gbs, "frac": gbs / peak,
                     "bytes": bytes_, "ms_by_lanes": per}
+    # the O-grid stencil form of the same matrix: seven value planes, no indices (9 s n bytes)
+    cgp.cgp_mesh_set_ogrid(m.handle, *SPMV_MESH)
+    out["stencil"] = {"format": "7 value planes at fixed O-grid offsets, no column indices; bytes 9 s n"}
+    for prec, dt, s_, what in ((cgp.CGP_FP64, torch.float64, 8, cgp.CGP_TUNE_SPMV_FP64),
+                               (cgp.CGP_FP32, torch.float32, 4, cgp.CGP_TUNE_SPMV_FP32)):
+        x = torch.randn(n, dtype=dt, device=dev)
+        y = torch.empty(n, dtype=dt, device=dev)
+        cgp.cgp_set_tuning(m.handle, what, 256, 0, 0, 1)
+        for _ in range(3):
+            cgp.cgp_spmv(m.handle, prec, x, y)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            cgp.cgp_spmv(m.handle, prec, x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        key = "fp64" if prec == cgp.CGP_FP64 else "fp32"
+        bytes_ = 9 * s_ * n
+        out["stencil"][key] = {"ms": ms, "gb_s": bytes_ / (ms * 1e-3) / 1e9, "frac": bytes_ / (ms * 1e-3) / 1e9 / peak,
+                               "bytes": bytes_, "speedup_vs_csr": out[key]["ms"] / ms}
+        cgp.cgp_set_tuning(m.handle, what, 0, 0, 0, 0)
     m.close()
     return out
 

@@ -386,6 +386,21 @@ int cgp_velocity_correct(cgp_mesh m, const double* p_f, const double* u_t, const
 int cgp_spmv(cgp_mesh m, int precision, const void* x, void* y, void* stream);
 
 /*
+ * cgp_mesh_set_ogrid - declare the coarse mesh an n_theta x n_r O-grid
+ * (node (j, i) = j * n_theta + i, ring j = 0 .. n_r, angle i periodic, every
+ * quad cut along its (i, j) - (i+1, j+1) diagonal) and build the seven-plane
+ * stencil form of K: values at the fixed (angle, ring) offsets (0,0), (+-1,0),
+ * (0,+-1), (+1,+1), (-1,-1), zeros where a neighbour does not exist, and no
+ * column indices (9 s n bytes per product against CSR's 12 s n + 4 n; SURVEY's
+ * structured-stencil format, a storage choice beside the paper's unstructured
+ * CSR).  Afterwards SpMV tuning flag bit 0 selects it for cgp_spmv.
+ * Synchronous; one allocation of 84 n_c bytes (FP64 and FP32 planes), freed
+ * with the mesh.  INVALID_ARG if n_theta * (n_r + 1) != n_c or if any row's
+ * CSR pattern differs from the stencil.
+ */
+int cgp_mesh_set_ogrid(cgp_mesh m, int n_theta, int n_r);
+
+/*
  * cgp_set_tuning / cgp_get_tuning - launch shape of a kernel family on this mesh.
  *
  * what    CGP_TUNE_SOLVE_FP64, CGP_TUNE_SOLVE_MIXED (the persistent solver),
@@ -399,6 +414,8 @@ int cgp_spmv(cgp_mesh m, int precision, const void* x, void* y, void* stream);
  * flags   solver: bit 0 keeps each block's rows in global memory instead of
  *         shared memory; bit 1 (FP64 only) runs the textbook two-barrier CG
  *         iteration instead of the single-reduction form; other bits must be 0.
+ *         SpMV: bit 0 uses the O-grid stencil form (cgp_mesh_set_ogrid) with
+ *         one thread per row (lanes ignored).
  * Invalid shapes are rejected with INVALID_ARG.  cgp_autotune sets these.
  */
 typedef enum {

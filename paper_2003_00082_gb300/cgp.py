@@ -33,7 +33,7 @@ CGP_MIXED = 1
 CGP_FP32 = 1          # precision argument of cgp_spmv for the FP32 copy of K
 
 EXPORTS = ("cgp_assemble", "cgp_mesh_query", "cgp_mesh_levels", "cgp_set_far_field", "cgp_far_field_nodes",
-           "cgp_mesh_fine_geometry", "cgp_mesh_matrices",
+           "cgp_mesh_set_ogrid", "cgp_mesh_fine_geometry", "cgp_mesh_matrices",
            "cgp_restrict", "cgp_poisson_solve", "cgp_poisson_solve_async",
            "cgp_poisson_solve_noalloc", "cgp_prolong", "cgp_lorentz", "cgp_velocity_correct", "cgp_spmv",
            "cgp_set_tuning", "cgp_get_tuning", "cgp_autotune", "cgp_last_launch", "cgp_barrier_selftest",
@@ -100,6 +100,7 @@ def load(path: str | None = None):
         "cgp_prolong": [vp, vp, vp, vp],
         "cgp_mesh_levels": [vp, ip, ip],
         "cgp_set_far_field": [vp, i],
+        "cgp_mesh_set_ogrid": [vp, i, i],
         "cgp_far_field_nodes": [vp, ip, ip],
         "cgp_velocity_correct": [vp, vp, vp, vp, d, vp, vp, vp],
         "cgp_lorentz": [vp, vp, vp, vp, dp, d, vp, vp, vp],
@@ -203,6 +204,10 @@ def cgp_mesh_levels(mesh):
     nodes = (ctypes.c_int * (k.value + 1))()
     _check(load().cgp_mesh_levels(mesh, None, nodes))
     return k.value, list(nodes)
+
+
+def cgp_mesh_set_ogrid(mesh, n_theta, n_r):
+    _check(load().cgp_mesh_set_ogrid(mesh, int(n_theta), int(n_r)))
 
 
 def cgp_set_far_field(mesh, dirichlet):

@@ -117,6 +117,12 @@ struct cgp_mesh_impl {
   SolveResult* h_res = nullptr;  // pinned host mirror
   int max_blocks = 0;
 
+  // seven-plane stencil form of K for an O-grid (cgp_mesh_set_ogrid)
+  int st_nt = 0, st_nj = 0;
+  double* st_val = nullptr;   // [7][n_c]
+  float* st_val32 = nullptr;  // [7][n_c]
+  void* st_base = nullptr;
+
   // far-field Dirichlet variant (phi = 0 on the outer boundary), built on first use
   int far_dirichlet = 0;
   std::vector<int> h_outer;        // coarse nodes on the outer boundary loops
@@ -149,6 +155,7 @@ int launch_velocity_correct(cgp_mesh_impl* m, const double* p_f, const double* u
 int launch_lorentz(cgp_mesh_impl* m, const double* phi, const double* u, const double* v,
                    const double B[3], double sigma, double* grad, double* force, cudaStream_t s);
 int launch_spmv(cgp_mesh_impl* m, int precision, const void* x, void* y, cudaStream_t s);
+int launch_spmv_stencil(cgp_mesh_impl* m, int precision, const void* x, void* y, int block, cudaStream_t s);
 int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opts& o,
                  cgp_solve_info* info_dev, cudaStream_t s);
 int solver_max_blocks(int device);

@@ -1787,6 +1787,7 @@ int launch_solve_fp64_raw(int device, const RawSystem& sys, const RawScratch& sc
 int launch_spmv(cgp_mesh_impl* m, int precision, const void* x, void* y, cudaStream_t s) {
   const int sms = std::max(1, dev_info(m->device).sms);
   const SolverTuning& tu = m->tune[precision == CGP_FP64 ? CGP_TUNE_SPMV_FP64 : CGP_TUNE_SPMV_FP32];
+  if (tu.flags & 1) return launch_spmv_stencil(m, precision, x, y, tu.block, s);   // O-grid stencil form
   const int block = tu.block > 0 ? tu.block : 256;
   const int lanes = tu.lanes > 0 ? tu.lanes : (precision == CGP_FP64 ? 1 : 4);
   long long grid = tu.blocks;

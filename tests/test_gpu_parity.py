@@ -493,3 +493,52 @@ def test_far_field_dirichlet_solve_matches_oracle(cgp, name, precision, flags):
     ref_n = om.solve(u, v, O.POTENTIAL, B=B, sigma=sigma, tol=1e-13)
     assert rel(out_n["phi_c"], ref_n["phi_c"]) <= 1e-10
     m.close()
+
+
+# ----------------------------------------------------------------------------
+# O-grid stencil form of K
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("nt,nr", [(3, 1), (7, 3), (33, 17), (64, 32)])
+def test_stencil_spmv_matches_oracle(cgp, nt, nr):
+    xy, tri = inputs.ogrid(nt, nr)
+    m = cgp.Mesh(xy, tri)
+    om = O.OracleMesh(xy, tri)
+    cgp.cgp_mesh_set_ogrid(m.handle, nt, nr)
+    rng = np.random.default_rng(17)
+    x = rng.standard_normal(m.n_c)
+    ref = om.K @ x
+    scale = np.abs(om.K) @ np.abs(x)
+    for prec, what, dt, eps in ((cgp.CGP_FP64, cgp.CGP_TUNE_SPMV_FP64, torch.float64, 1e-15),
+                                (cgp.CGP_FP32, cgp.CGP_TUNE_SPMV_FP32, torch.float32, 1e-6)):
+        cgp.cgp_set_tuning(m.handle, what, 128, 0, 0, 1)
+        y = torch.empty(m.n_c, dtype=dt, device=DEV)
+        cgp.cgp_spmv(m.handle, prec, T(x, dt), y)
+        torch.cuda.synchronize()
+        assert np.all(np.abs(y.cpu().numpy() - ref) <= eps * 8 * scale + 1e-300), prec
+    m.close()
+
+
+def test_stencil_form_rejects_other_meshes(cgp):
+    xy, tri = inputs.ogrid(9, 4)
+    m = cgp.Mesh(xy, tri)
+    with pytest.raises(cgp.CgpError):
+        cgp.cgp_mesh_set_ogrid(m.handle, 10, 4)        # wrong size
+    with pytest.raises(cgp.CgpError):
+        cgp.cgp_mesh_set_ogrid(m.handle, 15, 2)        # right size (45 = 15 x 3), wrong pattern
+    # the same nodes with every quad cut along its other diagonal: a different stencil
+    nt, nr = 9, 4
+    jj, ii = np.meshgrid(np.arange(nr), np.arange(nt), indexing="ij")
+    jj, ii = jj.ravel(), ii.ravel()
+    n00, n10 = jj * nt + ii, jj * nt + (ii + 1) % nt
+    n01, n11 = (jj + 1) * nt + ii, (jj + 1) * nt + (ii + 1) % nt
+    other = np.concatenate([np.stack([n00, n10, n01], 1), np.stack([n10, n11, n01], 1)]).astype(np.int32)
+    a2, _, _ = O.p1_gradients(xy, other.astype(np.int64))
+    other[a2 < 0] = other[a2 < 0][:, [0, 2, 1]]
+    mm = cgp.Mesh(xy, other)
+    with pytest.raises(cgp.CgpError):
+        cgp.cgp_mesh_set_ogrid(mm.handle, nt, nr)
+    cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SPMV_FP64, 128, 0, 0, 1)
+    with pytest.raises(cgp.CgpError):                  # stencil requested before it was built
+        cgp.cgp_spmv(m.handle, cgp.CGP_FP64, T(np.zeros(m.n_c)), torch.empty(m.n_c, dtype=torch.float64, device=DEV))
+    m.close()
+    mm.close()

@@ -71,6 +71,7 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert lib.cgp_velocity_correct(None, None, None, None, 0.05, None, None, None) == cgp.CGP_ERR_INVALID_ARG
     assert lib.cgp_mesh_levels(None, None, None) == cgp.CGP_ERR_INVALID_ARG
     assert lib.cgp_set_far_field(None, 1) == cgp.CGP_ERR_INVALID_ARG
+    assert lib.cgp_mesh_set_ogrid(None, 8, 4) == cgp.CGP_ERR_INVALID_ARG
     assert lib.cgp_far_field_nodes(None, None, None) == cgp.CGP_ERR_INVALID_ARG
     assert lib.cgp_set_tuning(None, 0, 0, 0, 0, 0) == cgp.CGP_ERR_INVALID_ARG
     assert lib.cgp_barrier_selftest(0, 0, 1, None) == cgp.CGP_ERR_INVALID_ARG
