@@ -124,6 +124,20 @@ struct Group {
     __syncthreads();
     return sh.flag != 0;
   }
+
+  // The same barrier split in two: work between arrive() and wait() overlaps
+  // the other blocks' arrival; it must not write what other blocks read.
+  __device__ void arrive() {
+    __syncthreads();
+    if (nblk == 1) return;
+    ++epoch;
+    if (threadIdx.x == 0) red_release_add(bar, 1u);
+  }
+  __device__ bool wait(Shared& sh) {
+    if (nblk > 1 && threadIdx.x == 0) sh.flag = barrier_wait(bar, timeout, nblk, epoch, spin_ns) ? 1 : 0;
+    __syncthreads();
+    return nblk == 1 || sh.flag != 0;
+  }
 };
 
 __device__ __forceinline__ fx::I128 shfl_xor_i128(fx::I128 a, int o) {
@@ -669,6 +683,7 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
   double* const S1 = d.pub64 + 5 * n;
 
   double *x, *r, *u, *w, *p, *s, *bp, *ext = nullptr;
+  double* u2 = nullptr;   // RES: second buffer of u (u_k and u_(k+1) alternate)
   double *stR = nullptr, *stW = nullptr, *stS = nullptr;  // RES: staged halo r, w, s of the next iteration
   const double* di;
   const double* dih = nullptr;  // RES: D^-1 of the halo rows
@@ -685,7 +700,8 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
     s = base + 5 * chunk;
     double* dil = base + 6 * chunk;
     bp = base + 7 * chunk;
-    ext = base + 8 * chunk;                  // [chunk + halo_cap]: own u, then gathered halo u
+    u2 = base + 8 * chunk;
+    ext = base + 9 * chunk;                  // [chunk + halo_cap]: own u, then gathered halo u
     double* dh = ext + chunk + d.halo_cap;   // [halo_cap]
     double* val = dh + d.halo_cap;           // [nnz_cap]
     stR = val + d.res_nnz_cap;               // [halo_cap] each
@@ -889,17 +905,23 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       double* Rn = (k & 1) ? R0 : R1;
       double* Wn = (k & 1) ? W0 : W1;
       double* Sn = (k & 1) ? S0 : S1;
-      // own rows: p, s, x, r, u; r and s published
+      // RES: u_k stays in uc while u_(k+1) goes to un, so that p and x (off the
+      // critical path) are updated while the other blocks arrive at the barrier
+      double* uc = (RES && (k & 1)) ? u2 : u;
+      double* un = (RES && !(k & 1)) ? u2 : u;
+      // own rows: s, r, u (and without RES p, x); r and s published
       for (int i = tid; i < nloc; i += bd) {
-        const double pi = k == 0 ? u[i] : fma(beta, p[i], u[i]);
         const double si = k == 0 ? w[i] : fma(beta, s[i], w[i]);
-        p[i] = pi;
+        if (!RES) {
+          const double pi = k == 0 ? u[i] : fma(beta, p[i], u[i]);
+          p[i] = pi;
+          x[i] = fma(alpha, pi, x[i]);
+        }
         s[i] = si;
-        x[i] = fma(alpha, pi, x[i]);
         const double ri = fma(-alpha, si, r[i]);
         r[i] = ri;
         const double ui = di[i] * ri;
-        u[i] = ui;
+        un[i] = ui;
         Rn[r0 + i] = ri;
         Sn[r0 + i] = si;
         if (RES) ext[i] = ui;
@@ -924,7 +946,7 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       auto op = [&](int il, double sum) {
         w[il] = sum;
         Wn[r0 + il] = sum;
-        const double ui = u[il], ri = r[il];
+        const double ui = un[il], ri = r[il];
         v3[0] += ri * ui;
         v3[1] += sum * ui;
         v3[2] += ri * ri;
@@ -933,10 +955,18 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
         spmv_ext<T>(L.row, L.col, L.val, ext, nloc, op);
       } else {
         spmv_local<T, double>(
-            L, r0, nloc, [&](int jl) { return u[jl]; }, [&](int j) { return halo_u(j, d.dinv[j]); }, op);
+            L, r0, nloc, [&](int jl) { return un[jl]; }, [&](int j) { return halo_u(j, d.dinv[j]); }, op);
       }
       put_partials<3>(d, lb, red, v3, sh);
-      if (!grp.sync(sh)) return;
+      grp.arrive();
+      if constexpr (RES) {   // p_k = u_k + beta p_(k-1), x += alpha p_k while the barrier fills
+        for (int i = tid; i < nloc; i += bd) {
+          const double pi = k == 0 ? uc[i] : fma(beta, p[i], uc[i]);
+          p[i] = pi;
+          x[i] = fma(alpha, pi, x[i]);
+        }
+      }
+      if (!grp.wait(sh)) return;
       ++k;
       stage(k);
       get_totals_then<3>(d, red, sh, derive);
@@ -1565,7 +1595,7 @@ SolverKind solver_kind(bool mixed, int flags) {
 
 // Dynamic shared memory of a block that keeps its rows resident: the classic
 // FP64 solver needs seven vectors, the halo buffer and an FP64 CSR slice; the
-// single-reduction FP64 solver eight vectors, the halo buffer, D^-1 of the
+// single-reduction FP64 solver nine vectors, the halo buffer, D^-1 of the
 // halo, three staging buffers of the halo and the slice; the mixed solver six
 // FP32 vectors, D^-1, the halo buffer, D^-1 of the halo, three staging
 // buffers and an FP32 slice.
@@ -1577,7 +1607,7 @@ size_t res_smem_bytes(SolverKind kind, int chunk, const HaloPlan& hp) {
   else if (kind == KIND_FP64_CLASSIC)
     s = 8 * ((size_t)7 * chunk + hp.max_halo + hp.max_nnz) + ints;
   else
-    s = 8 * ((size_t)9 * chunk + 5 * (size_t)hp.max_halo + hp.max_nnz) + ints;
+    s = 8 * ((size_t)10 * chunk + 5 * (size_t)hp.max_halo + hp.max_nnz) + ints;
   return (s + 15) / 16 * 16;
 }
 
@@ -1624,7 +1654,7 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
   }
   const size_t limit = (size_t)std::max(0, optin_smem(device) - (int)fa.sharedSizeBytes - 1024);
   const SolverKind kind = solver_kind(mixed, tu.flags);
-  if ((size_t)chunk * (kind == KIND_FP64_SR ? 72 : 56) + (size_t)rough_nnz * 12 > limit) return CGP_OK;
+  if ((size_t)chunk * (kind == KIND_FP64_SR ? 80 : 56) + (size_t)rough_nnz * 12 > limit) return CGP_OK;
   HaloPlan hp;
   int st = get_halo_plan(m, nblk, hp);
   if (st != CGP_OK) return st;
@@ -1923,7 +1953,7 @@ int batch_plan(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
     cgp_mesh_impl* m = B->meshes[i];
     const int chunk = (m->n_c + nb[i] - 1) / nb[i];
     const int rough_nnz = m->h_rowptr[std::min(m->n_c, chunk)] - m->h_rowptr[0];
-    if ((size_t)chunk * (kind == KIND_FP64_SR ? 72 : 56) + (size_t)rough_nnz * 12 > limit) {
+    if ((size_t)chunk * (kind == KIND_FP64_SR ? 80 : 56) + (size_t)rough_nnz * 12 > limit) {
       res = false;
       break;
     }

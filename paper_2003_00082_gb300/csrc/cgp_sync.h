@@ -31,11 +31,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Thread 0 of the block: arrive and wait for the `epoch`-th completion of the
-// barrier over nblk blocks; returns false when the wait gave up.
-__device__ __forceinline__ bool barrier_arrive_wait(unsigned* bar, int* timeout, unsigned nblk, unsigned epoch,
-                                                    long long spin_ns) {
-  red_release_add(bar, 1u);
+// Thread 0 of the block: wait for the `epoch`-th completion of the barrier
+// over nblk blocks (after this block's arrival); returns false when the wait
+// gave up.
+__device__ __forceinline__ bool barrier_wait(unsigned* bar, int* timeout, unsigned nblk, unsigned epoch,
+                                             long long spin_ns) {
   const unsigned target = epoch * nblk;
   unsigned long long t0 = 0;
   unsigned spins = 0;
@@ -53,6 +53,13 @@ __device__ __forceinline__ bool barrier_arrive_wait(unsigned* bar, int* timeout,
   }
   (void)ld_acquire(bar);
   return true;
+}
+
+// Thread 0 of the block: arrive, then wait as above.
+__device__ __forceinline__ bool barrier_arrive_wait(unsigned* bar, int* timeout, unsigned nblk, unsigned epoch,
+                                                    long long spin_ns) {
+  red_release_add(bar, 1u);
+  return barrier_wait(bar, timeout, nblk, epoch, spin_ns);
 }
 
 }  // namespace cgp
