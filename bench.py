@@ -408,7 +408,8 @@ def run_mine(args, rank, world, local_rank):
 
 
 def run_batched(cgp, inputs, configs, torch, dev, flush, peak, reps=5):
-    """64 uneven CGP potential solves (n_theta in {64,...,512}) in one persistent launch, mixed precision."""
+    """64 uneven CGP potential solves (n_theta in {64,...,512}), mixed precision, in the batched persistent
+    solver (wave-scheduled launches or one packed launch, as its autotuner picks) replayed from a CUDA graph."""
     insts = configs.batched_instances()
     meshes, bs, xs = [], [], []
     for inst in insts:

@@ -232,35 +232,44 @@ int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* col, const do
                               const cgp_solve_opts* opts, cgp_solve_info* info, void* stream);
 
 /*
- * Batched solves: many independent systems in one persistent launch.
+ * Batched solves: many independent systems in persistent launches.
  *
  * A batch fixes a list of distinct meshes (count >= 1; sizes may differ),
  * one right-hand side b[i] and one solution/initial-guess buffer x[i] per
  * mesh (device pointers, caller-owned, length n_c of that mesh; host arrays
- * of pointers, copied) and the solve options.  cgp_batch_solve then runs
- * every system's Jacobi-PCG (FP64 or mixed precision, as in
- * cgp_poisson_solve) in ONE cooperative launch: the grid is split into one
- * group of blocks per system, sized in proportion to the system's work
- * (nnz * sqrt(n)), each group with its own barriers and reductions, so the
- * systems progress side by side.  The launch needs no host work, so it can
- * be captured in a CUDA graph and replayed.  This is the many-instance
- * workload of the spec addition (2); the paper solves one system per
- * time step (Sect. 2.2).
+ * of pointers, copied) and the solve options.  cgp_batch_solve runs every
+ * system's Jacobi-PCG (FP64 or mixed precision, as in cgp_poisson_solve),
+ * each system on its own group of blocks with its own barriers and
+ * reductions, in one of two schedules:
+ *   - waves (default): each system gets the blocks a solve of it alone would
+ *     use (about 256 rows per block, at most blocks_per_sm x SMs), so that its
+ *     rows fit in shared memory; systems are packed largest first into waves
+ *     of at most blocks_per_sm x SMs blocks, and the waves run as consecutive
+ *     cooperative launches: small systems share the GPU, large ones get all
+ *     of it;
+ *   - packed (tuning flag bit 2): ONE cooperative launch holds every system,
+ *     block groups sized in proportion to each system's work (nnz sqrt(n)).
+ * Neither needs host work between launches, so a solve can be captured in a
+ * CUDA graph and replayed.  This is the many-instance workload of the
+ * spec addition (2); the paper solves one system per time step
+ * (Sect. 2.2).
  *
- * cgp_batch_create    plans the launch (blocks per system, shared-memory
- *                     residency, halo lists) and allocates the batch's small
- *                     device descriptors; synchronous.  INVALID_ARG if a
- *                     mesh repeats (their scratch would be shared) or there
- *                     are more systems than co-resident blocks.
- * cgp_batch_solve     one launch on `stream`, asynchronous.
+ * cgp_batch_create    plans the launches (blocks per system, waves,
+ *                     shared-memory residency, halo lists) and allocates the
+ *                     batch's small device descriptors; synchronous.
+ *                     INVALID_ARG if a mesh repeats (their scratch would be
+ *                     shared) or a packed launch has more systems than
+ *                     co-resident blocks.
+ * cgp_batch_solve     the launches on `stream`, asynchronous.
  * cgp_batch_info      synchronises the device and reads each system's
  *                     outcome; seconds[i] (nullable) is the device time from
  *                     the launch's start to system i's finish.  Returns the
  *                     first non-OK status among the systems.
  * cgp_batch_set_tuning  re-plans with threads per block, lanes per CSR row,
- *                     blocks per SM (0 = as many as fit) and flags (bit 0:
- *                     rows in global memory; bit 1: FP64 textbook iteration,
- *                     as for cgp_set_tuning).
+ *                     blocks per SM (0 = as many as fit; waves: 0 or 1 =
+ *                     one block per SM) and flags (bit 0: rows in global
+ *                     memory; bit 1: FP64 textbook iteration, as for
+ *                     cgp_set_tuning; bit 2: one packed launch, not waves).
  * cgp_batch_autotune  times a set of launch shapes on the batch's own
  *                     systems (from x = 0) and keeps the fastest; writes the
  *                     best time in ms to best_ms (nullable).  Synchronous;

@@ -1433,7 +1433,7 @@ __global__ void __launch_bounds__(MAX_BLOCK)
     pcg_batched_kernel(const Desc* __restrict__ descs, const int* __restrict__ blk_inst,
                        unsigned long long* t_start) {
   __shared__ Shared sh;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *t_start = global_ns();
+  if (t_start && blockIdx.x == 0 && threadIdx.x == 0) *t_start = global_ns();
   const Desc& d = descs[blk_inst[blockIdx.x]];
   const int lb = blockIdx.x - d.blk0;
   mark_pending(d, lb);
@@ -1857,7 +1857,7 @@ struct BatchShape {
   int block = 512;
   int lanes = 1;
   int per_sm = 0;   // blocks per SM (0: as many as can be co-resident)
-  int flags = 0;    // bit 0: rows in global memory; bit 1: classic FP64 iteration
+  int flags = 0;    // bit 0: rows in global memory; bit 1: classic FP64 iteration; bit 2: one packed launch
 };
 
 }  // namespace cgp
@@ -1876,6 +1876,16 @@ struct cgp_batch_s {
   size_t smem = 0;
   cgp::BatchFn fn = nullptr;
   std::vector<int> nblk;
+  // waves: cooperative launches run one after the other, each over a subset of
+  // the instances (one wave holding all of them when packed)
+  struct Wave {
+    int grid;
+    int blk_off;    // offset of its block -> instance map
+    bool res;
+    size_t smem;
+    cgp::BatchFn fn;
+  };
+  std::vector<Wave> waves;
   // device buffers: descriptors, block -> instance map, control area
   void* d_desc = nullptr;
   int* d_blk_inst = nullptr;
@@ -1977,6 +1987,7 @@ int batch_plan(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
     }
   }
   if (!res) smem = 0;
+  B->waves.assign(1, cgp_batch_s::Wave{total, 0, res, smem, res ? fnr : fn0});
   // descriptors
   std::vector<Desc> desc(count);
   std::vector<int> blk_inst(total);
@@ -2011,13 +2022,145 @@ int batch_plan(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
   return CGP_OK;
 }
 
+// Wave schedule: every instance gets the block count a solve of it alone
+// would use (about 256 rows per block, at most one SM's worth of blocks
+// each), so that it can keep its rows in shared memory; instances are packed
+// largest first into waves of at most blocks_per_sm x SMs blocks, and the
+// waves run as consecutive cooperative launches.  Small instances then share
+// the GPU while each large one gets all of it.
+int batch_plan_waves(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
+  const int lanes = sh.lanes > 0 ? sh.lanes : 1;
+  const int block = sh.block > 0 ? sh.block : 512;
+  const bool mixed = o.precision == CGP_MIXED;
+  BatchFn fn0 = batched_kernel_for(lanes, false), fnr = batched_kernel_for(lanes, true);
+  if (!fn0 || block < 64 || block > MAX_BLOCK || block % 32 != 0 || block % lanes != 0)
+    return fail(CGP_ERR_INVALID_ARG, "batch tuning: bad block or lanes");
+  const int sms = std::max(1, dev_info(B->device).sms);
+  const int cap = sms * std::max(1, sh.per_sm);
+  const int count = B->count;
+  const SolverKind kind = solver_kind(mixed, sh.flags);
+  std::vector<int> nb(count), order(count);
+  for (int i = 0; i < count; ++i) {
+    const int n = B->meshes[i]->n_c;
+    nb[i] = std::max(1, std::min(std::min(cap, B->meshes[i]->max_blocks), (n + 255) / 256));
+    order[i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nb[a] > nb[b]; });
+  std::vector<std::vector<int>> groups;
+  std::vector<int> used;
+  for (int i : order) {
+    size_t g = 0;
+    while (g < groups.size() && used[g] + nb[i] > cap) ++g;
+    if (g == groups.size()) {
+      groups.emplace_back();
+      used.push_back(0);
+    }
+    groups[g].push_back(i);
+    used[g] += nb[i];
+  }
+  cudaFuncAttributes fa{};
+  bool can_res = !(sh.flags & 1) && cudaFuncGetAttributes(&fa, (const void*)fnr) == cudaSuccess;
+  if (!can_res) cudaGetLastError();
+  const size_t limit = can_res ? (size_t)std::max(0, optin_smem(B->device) - (int)fa.sharedSizeBytes - 1024) : 0;
+  std::vector<Desc> desc(count);
+  std::vector<int> blk_inst;
+  std::vector<cgp_batch_s::Wave> waves;
+  size_t max_smem = 0;
+  for (const auto& grp : groups) {
+    int total = 0;
+    for (int i : grp) total += nb[i];
+    bool res = can_res;
+    size_t smem = 0;
+    std::vector<HaloPlan> hp(count);
+    for (int i : grp) {
+      if (!res) break;
+      cgp_mesh_impl* m = B->meshes[i];
+      const int chunk = (m->n_c + nb[i] - 1) / nb[i];
+      const int rough_nnz = m->h_rowptr[std::min(m->n_c, chunk)] - m->h_rowptr[0];
+      if ((size_t)chunk * (kind == KIND_FP64_SR ? 80 : 56) + (size_t)rough_nnz * 12 > limit) {
+        res = false;
+        break;
+      }
+      int st = get_halo_plan(m, nb[i], hp[i]);
+      if (st != CGP_OK) return st;
+      smem = std::max(smem, res_smem_bytes(kind, chunk, hp[i]));
+      if (smem > limit) res = false;
+    }
+    if (res) {
+      int per_sm = 0;
+      if (cudaFuncSetAttribute((const void*)fnr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)std::max(smem, max_smem)) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fnr, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+      }
+      if (per_sm * sms < total) res = false;
+    }
+    if (!res) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn0, block, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CGP_ERR_CUDA, "batch: occupancy query failed");
+      }
+      if (per_sm * sms < total) return fail(CGP_ERR_INVALID_ARG, "batch: a wave does not fit the device");
+      smem = 0;
+    }
+    max_smem = std::max(max_smem, smem);
+    const int off = (int)blk_inst.size();
+    int blk0 = 0;
+    for (int i : grp) {
+      cgp_mesh_impl* m = B->meshes[i];
+      LaunchPlan lp;
+      lp.nblk = nb[i];
+      lp.block = block;
+      if (res) {
+        lp.res = true;
+        lp.nnz_cap = hp[i].max_nnz;
+        lp.halo_cap = hp[i].max_halo;
+        lp.halo = hp[i];
+      }
+      unsigned char* ctrl = B->d_ctrl + kCtrlPerInstance * i;
+      desc[i] = make_desc(m, B->b[i], B->x[i], o, nb[i], lp, reinterpret_cast<unsigned*>(ctrl),
+                          reinterpret_cast<SolveResult*>(ctrl + 256), sh.flags);
+      desc[i].blk0 = blk0;
+      if (max_epochs(o) * nb[i] >= (1LL << 31)) return fail(CGP_ERR_INVALID_ARG, "batch: max_it too large");
+      for (int k = 0; k < nb[i]; ++k) blk_inst.push_back(i);
+      blk0 += nb[i];
+    }
+    waves.push_back(cgp_batch_s::Wave{total, off, res, smem, res ? fnr : fn0});
+  }
+  if (blk_inst.size() > (size_t)sms * std::max(32, count)) return fail(CGP_ERR_INVALID_ARG, "batch: too many blocks");
+  CGP_CUDA(cudaMemcpy(B->d_desc, desc.data(), sizeof(Desc) * count, cudaMemcpyHostToDevice));
+  CGP_CUDA(cudaMemcpy(B->d_blk_inst, blk_inst.data(), sizeof(int) * blk_inst.size(), cudaMemcpyHostToDevice));
+  B->waves = waves;
+  B->grid = 0;
+  B->res = true;
+  for (const auto& w : waves) {
+    B->grid = std::max(B->grid, w.grid);
+    B->res = B->res && w.res;
+  }
+  B->smem = max_smem;
+  B->fn = waves[0].fn;
+  B->nblk = nb;
+  B->shape = BatchShape{block, lanes, sh.per_sm, sh.flags};
+  return CGP_OK;
+}
+
+int batch_plan_any(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
+  return (sh.flags & 4) ? batch_plan(B, sh, o) : batch_plan_waves(B, sh, o);
+}
+
 int batch_launch(cgp_batch_s* B, cudaStream_t s) {
   CGP_CUDA(cudaMemsetAsync(B->d_ctrl, 0, B->ctrl_bytes, s));
   unsigned long long* t_start = reinterpret_cast<unsigned long long*>(B->d_ctrl + kCtrlPerInstance * B->count);
   const Desc* descs = static_cast<const Desc*>(B->d_desc);
-  const int* bi = B->d_blk_inst;
-  void* args[] = {&descs, &bi, &t_start};
-  CGP_CUDA(cudaLaunchCooperativeKernel((const void*)B->fn, dim3(B->grid), dim3(B->shape.block), args, B->smem, s));
+  for (size_t w = 0; w < B->waves.size(); ++w) {
+    const int* bi = B->d_blk_inst + B->waves[w].blk_off;
+    unsigned long long* ts = w == 0 ? t_start : nullptr;   // the batch starts with its first wave
+    void* args[] = {&descs, &bi, &ts};
+    CGP_CUDA(cudaLaunchCooperativeKernel((const void*)B->waves[w].fn, dim3(B->waves[w].grid),
+                                         dim3(B->shape.block), args, B->waves[w].smem, s));
+  }
   return CGP_OK;
 }
 
@@ -2187,7 +2330,7 @@ extern "C" int cgp_batch_create(const cgp_mesh* meshes, int count, const double*
   }
   B->ctrl_bytes = kCtrlPerInstance * count + 256;
   const int sms = std::max(1, dev_info(B->device).sms);
-  const size_t max_grid = (size_t)sms * 32;
+  const size_t max_grid = (size_t)sms * std::max(32, count);   // waves: up to one SM's worth of blocks per instance
   e = cudaMalloc(&B->d_desc, sizeof(Desc) * count);
   if (e == cudaSuccess) e = cudaMalloc(&B->d_blk_inst, sizeof(int) * max_grid);
   if (e == cudaSuccess) e = cudaMalloc(&B->d_ctrl, B->ctrl_bytes);
@@ -2195,7 +2338,7 @@ extern "C" int cgp_batch_create(const cgp_mesh* meshes, int count, const double*
     cgp_batch_destroy(B);
     return cuda_fail(e, "cudaMalloc(batch)");
   }
-  st = batch_plan(B, BatchShape{}, o);
+  st = batch_plan_any(B, BatchShape{}, o);
   if (st != CGP_OK) {
     cgp_batch_destroy(B);
     return st;
@@ -2206,9 +2349,9 @@ extern "C" int cgp_batch_create(const cgp_mesh* meshes, int count, const double*
 
 extern "C" int cgp_batch_set_tuning(cgp_batch batch, int block, int lanes, int blocks_per_sm, int flags) {
   if (!batch) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_set_tuning: NULL batch");
-  if (!valid_shape(CGP_TUNE_SOLVE_FP64, block, lanes) || blocks_per_sm < 0 || (flags & ~3))
+  if (!valid_shape(CGP_TUNE_SOLVE_FP64, block, lanes) || blocks_per_sm < 0 || (flags & ~7))
     return fail(CGP_ERR_INVALID_ARG, "cgp_batch_set_tuning: bad shape");
-  return batch_plan(batch, BatchShape{block, lanes, blocks_per_sm, flags}, batch->opts);
+  return batch_plan_any(batch, BatchShape{block, lanes, blocks_per_sm, flags}, batch->opts);
 }
 
 extern "C" int cgp_batch_solve(cgp_batch batch, void* stream) {
@@ -2267,12 +2410,12 @@ extern "C" int cgp_batch_autotune(cgp_batch batch, void* stream, double* best_ms
   const int lanes[2] = {1, 2};
   const int per_sm[2] = {1, 2};
   const int nflags = batch->opts.precision == CGP_MIXED ? 2 : 4;
-  for (int fl = 0; fl < nflags; ++fl)
+  for (int fl = 0; fl < 2 * nflags; ++fl)   // bit 2 (one packed launch instead of waves) on top
     for (int bk : blocks)
       for (int ln : lanes)
         for (int ps : per_sm) {
-          BatchShape cand{bk, ln, ps, fl};
-          if (batch_plan(batch, cand, o) != CGP_OK) continue;
+          BatchShape cand{bk, ln, ps, (fl % nflags) | (fl >= nflags ? 4 : 0)};
+          if (batch_plan_any(batch, cand, o) != CGP_OK) continue;
           float t = 1e30f;
           for (int rep = 0; rep < 2; ++rep) {
             if (cudaEventRecord(e0, s) != cudaSuccess || batch_launch(batch, s) != CGP_OK ||
@@ -2290,7 +2433,7 @@ extern "C" int cgp_batch_autotune(cgp_batch batch, void* stream, double* best_ms
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best_t >= 1e29f) return fail(CGP_ERR_CUDA, "cgp_batch_autotune: no candidate ran");
-  int st = batch_plan(batch, best, batch->opts);
+  int st = batch_plan_any(batch, best, batch->opts);
   if (st != CGP_OK) return st;
   if (best_ms) *best_ms = best_t;
   return CGP_OK;

@@ -49,13 +49,21 @@ def systems(cgp):
         s["mesh"].close()
 
 
+@pytest.mark.parametrize("packed", [False, True])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batched_instances_match_the_oracle(cgp, systems, precision):
+def test_batched_instances_match_the_oracle(cgp, systems, precision, packed):
     bs = [T(s["b"]) for s in systems]
     xs = [torch.zeros_like(b) for b in bs]
     batch = cgp.Batch([s["mesh"] for s in systems], bs, xs, tol=1e-10, precision=precision)
+    if packed:   # one launch holding every system
+        batch.set_tuning(512, 1, 0, 4)
     q = batch.query()
-    assert q["grid"] == sum(q["blocks"]) and min(q["blocks"]) >= 1
+    if packed:
+        assert q["grid"] == sum(q["blocks"])
+    else:        # waves: each system gets what it would get alone (about 256 rows a block)
+        assert q["grid"] <= sum(q["blocks"])
+        assert q["blocks"] == [max(1, (s["mesh"].n_c + 255) // 256) for s in systems]
+    assert min(q["blocks"]) >= 1
     batch.solve()
     infos, secs = batch.info()
     for s, x, info, t in zip(systems, xs, infos, secs):
@@ -68,7 +76,8 @@ def test_batched_instances_match_the_oracle(cgp, systems, precision):
     batch.close()
 
 
-@pytest.mark.parametrize("block,lanes,per_sm,flags", [(256, 1, 1, 0), (512, 2, 2, 1), (128, 4, 0, 0), (64, 8, 1, 1)])
+@pytest.mark.parametrize("block,lanes,per_sm,flags", [(256, 1, 1, 0), (512, 2, 2, 1), (128, 4, 0, 0), (64, 8, 1, 1),
+                                                     (256, 1, 1, 4), (512, 2, 2, 5), (256, 1, 2, 2), (128, 1, 0, 6)])
 def test_batched_launch_shapes(cgp, systems, block, lanes, per_sm, flags):
     bs = [T(s["b"]) for s in systems]
     xs = [torch.zeros_like(b) for b in bs]
@@ -76,7 +85,7 @@ def test_batched_launch_shapes(cgp, systems, block, lanes, per_sm, flags):
     batch.set_tuning(block, lanes, per_sm, flags)
     q = batch.query()
     assert q["block"] == block and q["lanes"] == lanes
-    if flags:
+    if flags & 1:
         assert q["resident"] == 0
     batch.solve()
     infos, _ = batch.info()
