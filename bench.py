@@ -452,7 +452,7 @@ def run_batched(cgp, inputs, configs, torch, dev, flush, peak, reps=5):
     alg = sum(mixed_launch_bytes(i["iterations"], i["outer_sweeps"], m.n_c, m.nnz) for i, m in zip(infos, meshes))
     q = batch.query()
     out = {"workload": "64 CGP potential solves, coarse O-grids n_theta ~ U{64,128,256,512} (n_r = n_theta/2), "
-                       "N ~ U[0.5,5], B = (cos a, sin a, 1), one persistent launch replayed from a CUDA graph",
+                       "N ~ U[0.5,5], B = (cos a, sin a, 1), batched persistent launches (autotuned schedule) replayed from a CUDA graph",
            "instances": len(meshes), "coarse_rows_total": sum(m.n_c for m in meshes),
            "fine_nodes_total": sum(m.n_f for m in meshes), "precision": "fp32 inner + fp64 refinement",
            "tol": TOL, "value": len(meshes) / (ms * 1e-3), "unit": "solves/s", "ms_per_batch": ms,
