@@ -842,7 +842,8 @@ def profile_case(case):
         x = torch.zeros(m.n_c, dtype=torch.float64, device=dev)
         prec = cgp.CGP_MIXED if case == "mixed" else cgp.CGP_FP64
         what = cgp.CGP_TUNE_SOLVE_MIXED if case == "mixed" else cgp.CGP_TUNE_SOLVE_FP64
-        cgp.cgp_set_tuning(m.handle, what, 512, 1, 152, 0)    # the shape the autotuner picks on GB300
+        # the shapes the autotuner picks on GB300 (FP64: rows renumbered by coordinate bisection)
+        cgp.cgp_set_tuning(m.handle, what, 512, 1, 152, 0 if case == "mixed" else 4)
         for _ in range(2):
             x.zero_()
             info = cgp.cgp_poisson_solve(m.handle, b, x, tol=TOL, precision=prec)

@@ -422,7 +422,12 @@ int cgp_mesh_set_ogrid(cgp_mesh m, int n_theta, int n_r);
  *         co-resident); SpMV: grid size; 0 = chosen from the size.
  * flags   solver: bit 0 keeps each block's rows in global memory instead of
  *         shared memory; bit 1 (FP64 only) runs the textbook two-barrier CG
- *         iteration instead of the single-reduction form; other bits must be 0.
+ *         iteration instead of the single-reduction form; bit 2 renumbers the
+ *         rows by recursive coordinate bisection so that every block's chunk
+ *         is a compact patch of the mesh (smaller halos; b and x pass through
+ *         a gather and a scatter launch; the renumbered system is built once
+ *         per block count and boundary condition, about 12 nnz + 45 n_c
+ *         bytes); other bits must be 0.
  *         SpMV: bit 0 uses the O-grid stencil form (cgp_mesh_set_ogrid) with
  *         one thread per row (lanes ignored).
  * Invalid shapes are rejected with INVALID_ARG.  cgp_autotune sets these.
@@ -444,7 +449,8 @@ int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks, in
  * the caller's right-hand side b (device [n_c]) for every candidate of
  * threads per block {256, 512}, lanes per CSR row {1, 2, 4}, grid size (a
  * few counts around the SM count, and 1..16 blocks for small systems),
- * shared-memory residency and, for FP64, the iteration form (flag bit 1),
+ * shared-memory residency, the row order (flag bit 2) and, for FP64, the
+ * iteration form (flag bit 1),
  * and keeps the fastest with cgp_set_tuning.  Every candidate meets the
  * same tolerance on the true residual.  x
  * (device [n_c]) is overwritten.  cache_path (nullable) names a text file of

@@ -66,6 +66,26 @@ struct HaloPlan {
   void* base = nullptr;  // the one allocation holding the three arrays
 };
 
+// A solve's system with its rows renumbered so that every block's contiguous
+// chunk is a compact patch of the mesh (recursive coordinate bisection),
+// which shrinks the halo each block rebuilds every iteration.
+struct PermSystem {
+  int nblk = 0, dirichlet = 0, n = 0;
+  std::vector<int> h_rowptr, h_col;   // permuted pattern (host)
+  int* perm = nullptr;                // [n] new row -> mesh node
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* K = nullptr;
+  float* K32 = nullptr;
+  double* dinv = nullptr;
+  float* dinv32 = nullptr;
+  unsigned char* fixed = nullptr;     // Dirichlet rows (permuted), or NULL
+  double* bbuf = nullptr;             // [n] b in the new order
+  double* xbuf = nullptr;             // [n] x in the new order
+  HaloPlan plan;                      // halo lists of the permuted pattern
+  void* base = nullptr;
+};
+
 struct cgp_mesh_impl {
   int device = 0;
   int n_c = 0, t_c = 0, n_e = 0, n_f = 0, t_f = 0, nnz = 0;
@@ -140,6 +160,7 @@ struct cgp_mesh_impl {
   void* vinc_base = nullptr;
 
   std::vector<HaloPlan> plans;   // cached per block count
+  std::vector<PermSystem> psys;  // cached per (block count, boundary condition)
   SolverTuning tune[4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};  // by cgp_tune_target
   PlanRecord last_plan[2] = {{0, 0, 0, 0}, {0, 0, 0, 0}};                          // FP64, MIXED
 };

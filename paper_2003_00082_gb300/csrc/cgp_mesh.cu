@@ -516,6 +516,10 @@ extern "C" int cgp_mesh_destroy(cgp_mesh m) {
     if (pl.base) cudaFree(pl.base);
   if (m->vinc_base) cudaFree(m->vinc_base);
   if (m->dir_base) cudaFree(m->dir_base);
+  for (auto& ps : m->psys) {
+    if (ps.base) cudaFree(ps.base);
+    if (ps.plan.base) cudaFree(ps.plan.base);
+  }
   if (m->st_base) cudaFree(m->st_base);
   if (m->d_base) cudaFree(m->d_base);
   if (m->h_res) cudaFreeHost(m->h_res);

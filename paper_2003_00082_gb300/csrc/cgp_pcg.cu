@@ -1535,16 +1535,10 @@ struct LaunchPlan {
 };
 
 // Build (once per block count) the row partition and halo lists of a mesh.
-int get_halo_plan(cgp_mesh_impl* m, int nblk, HaloPlan& out) {
-  for (const HaloPlan& p : m->plans)
-    if (p.nblk == nblk) {
-      out = p;
-      return CGP_OK;
-    }
-  const int n = m->n_c, nnz = m->nnz;
+// Halo lists of a pattern split into nblk contiguous row chunks.
+int build_halo_plan(const std::vector<int>& rp, const std::vector<int>& cl, int n, int nblk, HaloPlan& out) {
+  const int nnz = rp[n];
   const int chunk = (n + nblk - 1) / nblk;
-  const std::vector<int>& rp = m->h_rowptr;
-  const std::vector<int>& cl = m->h_col;
   std::vector<int> lcol(nnz), hptr(nblk + 1, 0), hidx, h;
   HaloPlan p;
   p.nblk = nblk;
@@ -1581,8 +1575,139 @@ int get_halo_plan(cgp_mesh_impl* m, int nblk, HaloPlan& out) {
     cudaFree(p.base);
     return cuda_fail(e, "cudaMemcpy(halo plan)");
   }
+  out = p;
+  return CGP_OK;
+}
+
+int get_halo_plan(cgp_mesh_impl* m, int nblk, HaloPlan& out) {
+  for (const HaloPlan& p : m->plans)
+    if (p.nblk == nblk) {
+      out = p;
+      return CGP_OK;
+    }
+  HaloPlan p;
+  int st = build_halo_plan(m->h_rowptr, m->h_col, m->n_c, nblk, p);
+  if (st != CGP_OK) return st;
   m->plans.push_back(p);
   out = p;
+  return CGP_OK;
+}
+
+// Recursive coordinate bisection of the nodes idx[lo, hi) into k parts whose
+// sizes follow the solver's chunking (every part `chunk` rows but the last):
+// the left side takes k/2 parts, split along the wider side of the bounding
+// box; ties broken by node index, so the partition is deterministic.
+void rcb(std::vector<int>& idx, int lo, int hi, int k, int chunk, const std::vector<double>& xy) {
+  if (k <= 1 || hi - lo <= 1) return;
+  double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+  for (int q = lo; q < hi; ++q) {
+    const double x = xy[2 * (size_t)idx[q]], y = xy[2 * (size_t)idx[q] + 1];
+    x0 = std::min(x0, x); x1 = std::max(x1, x); y0 = std::min(y0, y); y1 = std::max(y1, y);
+  }
+  const int axis = (x1 - x0) >= (y1 - y0) ? 0 : 1;
+  const int k1 = k / 2;
+  const int mid = std::min(hi, lo + k1 * chunk);
+  std::nth_element(idx.begin() + lo, idx.begin() + mid, idx.begin() + hi, [&](int a, int b) {
+    const double va = xy[2 * (size_t)a + axis], vb = xy[2 * (size_t)b + axis];
+    return va < vb || (va == vb && a < b);
+  });
+  rcb(idx, lo, mid, k1, chunk, xy);
+  rcb(idx, mid, hi, k - k1, chunk, xy);
+}
+
+// The system of a solve on nblk blocks in the bisection order (built once per
+// block count and boundary condition): permuted pattern, values, D^-1, the
+// Dirichlet mask, b and x buffers in the new order, and its halo plan.
+int get_perm_system(cgp_mesh_impl* m, int nblk, PermSystem*& out) {
+  const int dir = m->far_dirichlet;
+  for (PermSystem& ps : m->psys)
+    if (ps.nblk == nblk && ps.dirichlet == dir) {
+      out = &ps;
+      return CGP_OK;
+    }
+  const int n = m->n_c, nnz = m->nnz, chunk = (n + nblk - 1) / nblk;
+  std::vector<double> xy(2 * (size_t)n), K(nnz), dv(n);
+  CGP_CUDA(cudaDeviceSynchronize());
+  CGP_CUDA(cudaMemcpy(xy.data(), m->xy_c, xy.size() * 8, cudaMemcpyDeviceToHost));
+  CGP_CUDA(cudaMemcpy(K.data(), dir ? m->Kd : m->K, (size_t)nnz * 8, cudaMemcpyDeviceToHost));
+  CGP_CUDA(cudaMemcpy(dv.data(), dir ? m->dinvd : m->dinv, (size_t)n * 8, cudaMemcpyDeviceToHost));
+  std::vector<unsigned char> fix;
+  if (dir) {
+    fix.resize(n);
+    CGP_CUDA(cudaMemcpy(fix.data(), m->fixed, n, cudaMemcpyDeviceToHost));
+  }
+  std::vector<int> perm(n), inv(n);
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  rcb(perm, 0, n, nblk, chunk, xy);
+  for (int b = 0; b < nblk; ++b) {   // mesh order inside every chunk (locality of the slices)
+    const int r0 = std::min(n, b * chunk), r1 = std::min(n, r0 + chunk);
+    std::sort(perm.begin() + r0, perm.begin() + r1);
+  }
+  for (int i = 0; i < n; ++i) inv[perm[i]] = i;
+  PermSystem ps;
+  ps.nblk = nblk;
+  ps.dirichlet = dir;
+  ps.n = n;
+  ps.h_rowptr.assign(n + 1, 0);
+  ps.h_col.resize(nnz);
+  std::vector<double> pk(nnz), pd(n);
+  std::vector<float> pk32(nnz), pd32(n);
+  std::vector<unsigned char> pfix(dir ? n : 0);
+  std::vector<std::pair<int, double>> row;
+  for (int r = 0; r < n; ++r) {
+    const int o = perm[r];
+    row.clear();
+    for (int k = m->h_rowptr[o]; k < m->h_rowptr[o + 1]; ++k) row.push_back({inv[m->h_col[k]], K[k]});
+    std::sort(row.begin(), row.end());
+    const int k0 = ps.h_rowptr[r];
+    for (size_t q = 0; q < row.size(); ++q) {
+      ps.h_col[k0 + q] = row[q].first;
+      pk[k0 + q] = row[q].second;
+      pk32[k0 + q] = (float)row[q].second;
+    }
+    ps.h_rowptr[r + 1] = k0 + (int)row.size();
+    pd[r] = dv[o];
+    pd32[r] = (float)dv[o];
+    if (dir) pfix[r] = fix[o];
+  }
+  int st = build_halo_plan(ps.h_rowptr, ps.h_col, n, nblk, ps.plan);
+  if (st != CGP_OK) return st;
+  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+  const size_t o_perm = 0, o_rp = o_perm + al((size_t)n * 4), o_col = o_rp + al((size_t)(n + 1) * 4),
+               o_k = o_col + al((size_t)nnz * 4), o_k32 = o_k + al((size_t)nnz * 8), o_d = o_k32 + al((size_t)nnz * 4),
+               o_d32 = o_d + al((size_t)n * 8), o_b = o_d32 + al((size_t)n * 4), o_x = o_b + al((size_t)n * 8),
+               o_f = o_x + al((size_t)n * 8), bytes = o_f + al((size_t)n);
+  cudaError_t e = cudaMalloc(&ps.base, bytes);
+  if (e != cudaSuccess) {
+    cudaFree(ps.plan.base);
+    return cuda_fail(e, "cudaMalloc(permuted system)");
+  }
+  char* b = static_cast<char*>(ps.base);
+  ps.perm = (int*)(b + o_perm);
+  ps.rowptr = (int*)(b + o_rp);
+  ps.col = (int*)(b + o_col);
+  ps.K = (double*)(b + o_k);
+  ps.K32 = (float*)(b + o_k32);
+  ps.dinv = (double*)(b + o_d);
+  ps.dinv32 = (float*)(b + o_d32);
+  ps.bbuf = (double*)(b + o_b);
+  ps.xbuf = (double*)(b + o_x);
+  ps.fixed = dir ? (unsigned char*)(b + o_f) : nullptr;
+  if (e == cudaSuccess) e = cudaMemcpy(ps.perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ps.rowptr, ps.h_rowptr.data(), (size_t)(n + 1) * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ps.col, ps.h_col.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ps.K, pk.data(), (size_t)nnz * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ps.K32, pk32.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ps.dinv, pd.data(), (size_t)n * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ps.dinv32, pd32.data(), (size_t)n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && dir) e = cudaMemcpy(ps.fixed, pfix.data(), (size_t)n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(ps.base);
+    cudaFree(ps.plan.base);
+    return cuda_fail(e, "cudaMemcpy(permuted system)");
+  }
+  m->psys.push_back(ps);
+  out = &m->psys.back();
   return CGP_OK;
 }
 
@@ -1620,7 +1745,7 @@ long long max_epochs(const cgp_solve_opts& o) {
 // block's rows go to shared memory when the largest chunk, its halo and its
 // CSR slice fit and the grid stays co-resident.
 int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const SolverTuning& tu, bool mixed,
-               LaunchPlan& out) {
+               LaunchPlan& out, PermSystem** ps_out = nullptr) {
   const int lanes = tu.lanes > 0 ? tu.lanes : 1;
   const int block = tu.block > 0 ? tu.block : 512;
   PcgFn fn0 = pcg_kernel_for(lanes, false);
@@ -1642,10 +1767,19 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
   out.fn = fn0;
   out.nblk = nblk;
   out.block = block;
+  // tuning flag bit 2: rows renumbered by coordinate bisection (compact chunks, smaller halos)
+  PermSystem* ps = nullptr;
+  if (m && (tu.flags & 4)) {
+    int st = get_perm_system(m, nblk, ps);
+    if (st != CGP_OK) return st;
+    out.halo = ps->plan;   // the non-resident path reads the permuted pattern directly
+  }
+  if (ps_out) *ps_out = ps;
   if (!m || (tu.flags & 1)) return CGP_OK;
   const int chunk = (n + nblk - 1) / nblk;
+  const std::vector<int>& hrp = ps ? ps->h_rowptr : m->h_rowptr;
   // rough size check before building a plan
-  const int rough_nnz = m->h_rowptr[std::min(n, chunk)] - m->h_rowptr[0];
+  const int rough_nnz = hrp[std::min(n, chunk)] - hrp[0];
   PcgFn fnr = pcg_kernel_for(lanes, true);
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, (const void*)fnr) != cudaSuccess) {
@@ -1656,8 +1790,12 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
   const SolverKind kind = solver_kind(mixed, tu.flags);
   if ((size_t)chunk * (kind == KIND_FP64_SR ? 80 : 56) + (size_t)rough_nnz * 12 > limit) return CGP_OK;
   HaloPlan hp;
-  int st = get_halo_plan(m, nblk, hp);
-  if (st != CGP_OK) return st;
+  if (ps) {
+    hp = ps->plan;
+  } else {
+    int st = get_halo_plan(m, nblk, hp);
+    if (st != CGP_OK) return st;
+  }
   const size_t smem = res_smem_bytes(kind, chunk, hp);
   if (smem > limit) return CGP_OK;
   if (cudaFuncSetAttribute((const void*)fnr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -1734,12 +1872,32 @@ Desc make_desc(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opt
 
 }  // namespace
 
+namespace {
+// b and x0 into the bisection order, and the solution back
+__global__ void perm_gather_kernel(int n, const int* __restrict__ perm, const double* __restrict__ b,
+                                   const double* __restrict__ x, int use_x0, double* __restrict__ bo,
+                                   double* __restrict__ xo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int o = perm[i];
+  bo[i] = b[o];
+  if (use_x0) xo[i] = x[o];
+}
+
+__global__ void perm_scatter_kernel(int n, const int* __restrict__ perm, const double* __restrict__ xi,
+                                    double* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[perm[i]] = xi[i];
+}
+}  // namespace
+
 int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opts& o, cgp_solve_info* info_dev,
                  cudaStream_t s) {
   const bool mixed = o.precision == CGP_MIXED;
   const SolverTuning& tu = m->tune[mixed ? CGP_TUNE_SOLVE_MIXED : CGP_TUNE_SOLVE_FP64];
   LaunchPlan plan;
-  int st = plan_solve(m, m->device, m->n_c, m->max_blocks, tu, mixed, plan);
+  PermSystem* ps = nullptr;
+  int st = plan_solve(m, m->device, m->n_c, m->max_blocks, tu, mixed, plan, &ps);
   if (st != CGP_OK) return st;
   const int nblk = plan.nblk;
   // barrier epochs stay far below 2^32 / nblk
@@ -1747,11 +1905,32 @@ int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_o
 
   Desc d = make_desc(m, b, x, o, nblk, plan, m->bar, m->res, tu.flags);
   d.out = info_dev;
+  const int n = m->n_c;
+  if (ps) {   // the same solve on the renumbered system
+    d.rowptr = ps->rowptr;
+    d.col = ps->col;
+    d.val = ps->K;
+    d.val32 = ps->K32;
+    d.dinv = ps->dinv;
+    d.dinv32 = ps->dinv32;
+    d.fixed = ps->fixed;
+    d.b = ps->bbuf;
+    d.x = ps->xbuf;
+    d.lcol = ps->plan.lcol;
+    d.hptr = ps->plan.hptr;
+    d.hidx = ps->plan.hidx;
+    perm_gather_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, ps->perm, b, x, o.use_x0, ps->bbuf, ps->xbuf);
+    CGP_CUDA(cudaGetLastError());
+  }
 
   CGP_CUDA(cudaMemsetAsync(m->bar, 0, 256, s));
   CGP_CUDA(cudaMemsetAsync(m->res, 0, sizeof(SolveResult), s));
   void* args[] = {&d};
   CGP_CUDA(cudaLaunchCooperativeKernel((const void*)plan.fn, dim3(nblk), dim3(plan.block), args, plan.smem, s));
+  if (ps) {
+    perm_scatter_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, ps->perm, ps->xbuf, x);
+    CGP_CUDA(cudaGetLastError());
+  }
   m->last_plan[mixed ? 1 : 0] = PlanRecord{nblk, plan.block, plan.res ? 1 : 0, (int)plan.smem};
   return CGP_OK;
 }
@@ -2229,10 +2408,10 @@ static bool valid_shape(int what, int block, int lanes) {
 extern "C" int cgp_set_tuning(cgp_mesh m, int what, int block, int lanes, int blocks, int flags) {
   if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: NULL mesh");
   if (what < 0 || what > 3) return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: unknown target");
-  if (!valid_shape(what, block, lanes) || blocks < 0 || (flags & ~3))
+  if (!valid_shape(what, block, lanes) || blocks < 0 || (flags & ~7))
     return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: block must be 0 or a multiple of 32 in [64, 512] "
                                      "(solver) or [64, 256] (SpMV), "
-                                     "lanes 0, 1, 2, 4, 8 or 32, blocks >= 0, flags 0 to 3");
+                                     "lanes 0, 1, 2, 4, 8 or 32, blocks >= 0, flags 0 to 7");
   m->tune[what] = SolverTuning{block, lanes, blocks, flags};
   return CGP_OK;
 }
@@ -2542,10 +2721,11 @@ extern "C" int cgp_autotune(cgp_mesh m, int precision, const double* b, double* 
   SolverTuning best{};
   float best_t = 1e30f;
   const int nflags = precision == CGP_MIXED ? 2 : 4;   // bit 1 (classic FP64 iteration) only for FP64
-  for (int fl = 0; fl < nflags; ++fl)
+  for (int fl8 = 0; fl8 < 2 * nflags; ++fl8)            // bit 2 (bisection order) on top
     for (int bk : {256, 512})
       for (int ln : {1, 2, 4})
         for (int c : counts) {
+          const int fl = (fl8 % nflags) | (fl8 >= nflags ? 4 : 0);
           m->tune[what] = SolverTuning{bk, ln, c, fl};
           float t = 1e30f;
           for (int rep = 0; rep < 2; ++rep) {

@@ -162,10 +162,11 @@ def assert_iterations_match(info, ref_its, textbook):
 SHAPES = [(128, 1, 1), (128, 2, 5), (128, 4, 3), (256, 8, 7), (64, 32, 2), (64, 1, 13), (512, 1, 0)]
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2, 3])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("block,lanes,blocks", SHAPES)
 def test_fp64_solve_matches_oracle(pair, cgp, block, lanes, blocks, flags):
-    """Both FP64 iterations (bit 1: textbook, else single-reduction) in both storage modes (bit 0).
+    """Both FP64 iterations (bit 1: textbook, else single-reduction) in both storage modes (bit 0),
+    in the mesh's row order and renumbered by coordinate bisection (bit 2).
 
     The single-reduction form takes the same steps in exact arithmetic; its
     recurrences round differently, so its count may differ by a little more,
@@ -204,7 +205,8 @@ def test_fp64_solve_with_initial_guess(pair, cgp):
     assert rel(x.cpu().numpy(), ref["x"]) <= 1e-9
 
 
-MIXED_SHAPES = [(0, 0, 0, 0), (128, 1, 3, 0), (128, 2, 5, 1), (256, 4, 7, 0), (64, 8, 2, 1), (64, 1, 13, 0)]
+MIXED_SHAPES = [(0, 0, 0, 0), (128, 1, 3, 0), (128, 2, 5, 1), (256, 4, 7, 0), (64, 8, 2, 1), (64, 1, 13, 0),
+                (0, 0, 0, 4), (128, 1, 5, 5), (256, 2, 7, 4)]
 
 
 @pytest.mark.parametrize("block,lanes,blocks,flags", MIXED_SHAPES)
@@ -467,7 +469,7 @@ def test_velocity_correction_matches_oracle(cgp, levels, name):
 # ----------------------------------------------------------------------------
 # far-field Dirichlet variant
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("precision,flags", [(0, 0), (0, 1), (0, 2), (1, 0)])
+@pytest.mark.parametrize("precision,flags", [(0, 0), (0, 1), (0, 2), (1, 0), (0, 4), (1, 4)])
 @pytest.mark.parametrize("name", ["square", "ogrid-7x3", "ogrid-33x17", "ogrid-64x32"])
 def test_far_field_dirichlet_solve_matches_oracle(cgp, name, precision, flags):
     xy, tri = meshes()[name]
