@@ -39,6 +39,7 @@ RHO_OVER_DT = 20.0
 L2_FLUSH_BYTES = 512 << 20
 SPMV_MESH = (3072, 1536)       # matrix + vectors: 490 MB FP64, 320 MB FP32 (L2 is 129 MB)
 KERNELS_PER_STEP = 8           # 2 x (restrict_rhs, persistent PCG, prolong, lorentz)
+PERM_KERNELS_PER_SOLVE = 2     # gather and scatter around a solve in the bisection row order (tuning flag bit 2)
 FP64_PEAK_TFLOPS = 1.25        # nominal dense FP64 of a GB300
 
 
@@ -56,9 +57,8 @@ def workload_config(precision="fp64"):
 # taken on: when the sources' hash differs the traffic is reported as null.
 SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_sync.h", "cgp_fixed.h", "cgp_internal.h")
 SOLVER_TRAFFIC = {
-    "sha256": "e300e520628485d5a520861a794e3337ee2473253602a213bfa857e6ed8f793f",
-    "fp64": 14513408 + 249856,
-    "mixed": 21243904 + 247040,
+    "sha256": "4d86e4ce8e2f955fe45c50b1b0e0a2450fad5ee83d1b41146658df919ebd5894",
+    "fp64": 13954560 + 303616,
 }
 
 
@@ -68,7 +68,7 @@ def solver_traffic(precision):
     for f in SOLVER_SOURCES:
         with open(os.path.join(ROOT, "paper_2003_00082_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return SOLVER_TRAFFIC[precision] if h.hexdigest() == SOLVER_TRAFFIC["sha256"] else None
+    return SOLVER_TRAFFIC.get(precision) if h.hexdigest() == SOLVER_TRAFFIC["sha256"] else None
 
 
 def read_peaks():
@@ -842,8 +842,8 @@ def profile_case(case):
         x = torch.zeros(m.n_c, dtype=torch.float64, device=dev)
         prec = cgp.CGP_MIXED if case == "mixed" else cgp.CGP_FP64
         what = cgp.CGP_TUNE_SOLVE_MIXED if case == "mixed" else cgp.CGP_TUNE_SOLVE_FP64
-        # the shapes the autotuner picks on GB300 (FP64: rows renumbered by coordinate bisection)
-        cgp.cgp_set_tuning(m.handle, what, 512, 1, 152, 0 if case == "mixed" else 4)
+        # the shape the autotuner picks on GB300 (rows renumbered by coordinate bisection)
+        cgp.cgp_set_tuning(m.handle, what, 512, 1, 152, 4)
         for _ in range(2):
             x.zero_()
             info = cgp.cgp_poisson_solve(m.handle, b, x, tol=TOL, precision=prec)
@@ -932,7 +932,8 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": total_solves / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},
-            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "gpu_launches": (KERNELS_PER_STEP + (2 * PERM_KERNELS_PER_SOLVE if res["tuned"][args.precision]["flags"] & 4
+                                                 else 0)) * args.steps,
             "clocks": res["clocks"],
             "iterations": {"per_solve_mean": statistics.mean(res["its"]), "min": min(res["its"]),
                            "max": max(res["its"]), "rel_res_true_max": res["rel_res_true_max"]},
