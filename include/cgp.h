@@ -250,9 +250,9 @@ int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* col, const do
  *   - packed (tuning flag bit 2): ONE cooperative launch holds every system,
  *     block groups sized in proportion to each system's work (nnz sqrt(n)).
  * Neither needs host work between launches, so a solve can be captured in a
- * CUDA graph and replayed.  This is the many-instance workload of the
- * spec addition (2); the paper solves one system per time step
- * (Sect. 2.2).
+ * CUDA graph and replayed.  The paper solves one system per time step
+ * (Sect. 2.2); this serves many uneven independent systems at once (several
+ * meshes, right-hand sides or Stuart numbers).
  *
  * cgp_batch_create    plans the launches (blocks per system, waves,
  *                     shared-memory residency, halo lists) and allocates the
@@ -295,8 +295,8 @@ int cgp_poisson_solve_batched(const cgp_mesh* meshes, int count, const double* c
 /*
  * Learned initial guess: a message-passing network on the coarse mesh's edges.
  *
- * The paper has no learned component; this is the spec addition (4)
- * that predicts the PCG starting point of the potential solve (Eq. 12) from
+ * The paper has no learned component; this addition to the method
+ * predicts the PCG starting point of the potential solve (Eq. 12) from
  * the right-hand side b and the two previous solutions.  Per coarse node i,
  * f_i = [r/s_r, (phi1 - phi2)/s_d, b/s_b, x/15, y/15] with r = b - K phi1
  * (s = rms over nodes, each input scaled by its own size);
@@ -400,9 +400,8 @@ int cgp_spmv(cgp_mesh m, int precision, const void* x, void* y, void* stream);
  * quad cut along its (i, j) - (i+1, j+1) diagonal) and build the seven-plane
  * stencil form of K: values at the fixed (angle, ring) offsets (0,0), (+-1,0),
  * (0,+-1), (+1,+1), (-1,-1), zeros where a neighbour does not exist, and no
- * column indices (9 s n bytes per product against CSR's 12 s n + 4 n; SURVEY's
- * structured-stencil format, a storage choice beside the paper's unstructured
- * CSR).  Afterwards SpMV tuning flag bit 0 selects it for cgp_spmv.
+ * column indices (9 s n bytes per product against CSR's 12 s n + 4 n; a
+ * structured-stencil storage choice beside the paper's unstructured CSR).  Afterwards SpMV tuning flag bit 0 selects it for cgp_spmv.
  * Synchronous; one allocation of 84 n_c bytes (FP64 and FP32 planes), freed
  * with the mesh.  INVALID_ARG if n_theta * (n_r + 1) != n_c or if any row's
  * CSR pattern differs from the stencil.

@@ -3,7 +3,7 @@
 Tolerances: integer structure (CSR pattern, fine numbering, edges) is
 compared bit for bit; the assembled values are computed with separately
 rounded products on both sides and are compared to 1 ulp-level relative
-error; the solve is compared at the spec gates (phi <= 1e-8,
+error; the solve is compared at the accuracy gates (phi <= 1e-8,
 J x B <= 1e-6 relative L2) and, tighter, to what two FP64 CG runs that
 differ only in summation order reach (1e-10 at tol 1e-12).
 """
