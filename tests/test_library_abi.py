@@ -61,6 +61,12 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     with pytest.raises(cgp.CgpError) as e:
         cgp.cgp_assemble(xy, np.array([[0, 2, 5]], dtype=np.int32))
     assert e.value.status == cgp.CGP_ERR_INVALID_ARG
+    # the fine mesh of k levels must stay within 32-bit indexing (checked before any GPU work)
+    big = np.zeros((6_000_000, 3), dtype=np.int32)
+    with pytest.raises(cgp.CgpError) as e:
+        cgp.cgp_assemble(xy, big, levels=3)
+    assert e.value.status == cgp.CGP_ERR_INVALID_ARG and "too large" in str(e.value)
+    del big
     # one to three coarsening levels (Eq. 18)
     for bad in (0, 4):
         with pytest.raises(cgp.CgpError) as e:
