@@ -66,56 +66,64 @@ __global__ void prolong_level_kernel(int n_l, int e_l, const int2* __restrict__ 
   xf[n_l + e] = (xf[ed.x] + xf[ed.y]) * 0.5;
 }
 
-struct Node {
-  double x, y, phi, u, v;
+// Ohm's law and the force with uniform B, u_z = 0 and the vertex means
+// (u_b, v_b) = (su, sv) / 3:  j = sigma (u x B - grad phi) and j x B expand to
+//   f_x = -su k1 + sv k2 - g_y k3,   f_y = su k2 - sv k4 + g_x k3,
+// k1 = sigma (B_y^2 + B_z^2) / 3, k2 = sigma B_x B_y / 3, k3 = sigma B_z,
+// k4 = sigma (B_x^2 + B_z^2) / 3, folded once on the host.
+struct ForceCoef {
+  double k1, k2, k3, k4;
 };
 
-__device__ __forceinline__ Node load_node(int i, const double2* __restrict__ xy,
-                                          const double* __restrict__ phi,
-                                          const double* __restrict__ u,
-                                          const double* __restrict__ v) {
-  const double2 p = xy[i];
-  return Node{p.x, p.y, phi[i], u[i], v[i]};
-}
-
-// grad(phi) on the P1 triangle (n0, n1, n2), then Ohm's law and j x B.
-__device__ __forceinline__ void child(const Node& n0, const Node& n1, const Node& n2, double bx,
-                                      double by, double bz, double sigma, double& gx, double& gy,
-                                      double& fx, double& fy) {
-  const double b0 = n1.y - n2.y, b1 = n2.y - n0.y, b2 = n0.y - n1.y;
-  const double c0 = n2.x - n1.x, c1 = n0.x - n2.x, c2 = n1.x - n0.x;
-  const double a2 = (n1.x - n0.x) * (n2.y - n0.y) - (n2.x - n0.x) * (n1.y - n0.y);
-  const double inv = 1.0 / a2;
-  gx = (n0.phi * b0 + n1.phi * b1 + n2.phi * b2) * inv;
-  gy = (n0.phi * c0 + n1.phi * c1 + n2.phi * c2) * inv;
-  const double ub = (n0.u + n1.u + n2.u) * (1.0 / 3.0);
-  const double vb = (n0.v + n1.v + n2.v) * (1.0 / 3.0);
-  // u x B with u_z = 0
-  const double cx = vb * bz, cy = -(ub * bz), cz = ub * by - vb * bx;
-  const double jx = sigma * (cx - gx), jy = sigma * (cy - gy), jz = sigma * cz;
-  fx = jy * bz - jz * by;
-  fy = jz * bx - jx * bz;
+// One fine child of a parent triangle.  A child of the midpoint split is the
+// parent scaled by 1/2 (the middle child also turned by half a turn): its
+// (b_i, c_i) are the parent's halved (for the middle child negated and
+// permuted) and its doubled area is the parent's over 4, so
+// grad phi = 2 sum_i phi_i (b_i, c_i) / a2_parent.  One division per parent
+// on the GPU's narrow FP64 pipe instead of one per child; the result differs
+// from the child's own geometry by rounding only.
+template <bool FORCE>
+__device__ __forceinline__ void child(double p0, double p1, double p2, double su, double sv, double b0, double b1,
+                                      double b2, double c0, double c1, double c2, double inv2, const ForceCoef& k,
+                                      double& gx, double& gy, double& fx, double& fy) {
+  gx = (p0 * b0 + p1 * b1 + p2 * b2) * inv2;
+  gy = (p0 * c0 + p1 * c1 + p2 * c2) * inv2;
+  if (FORCE) {
+    fx = sv * k.k2 - su * k.k1 - gy * k.k3;
+    fy = su * k.k2 - sv * k.k4 + gx * k.k3;
+  }
 }
 
 template <bool FORCE>
 __global__ void lorentz_kernel(int t_c, int t_f, const int* __restrict__ tri,
                                const int* __restrict__ mid, const double2* __restrict__ xy,
                                const double* __restrict__ phi, const double* __restrict__ u,
-                               const double* __restrict__ v, double bx, double by, double bz,
-                               double sigma, double* __restrict__ grad, double* __restrict__ force) {
+                               const double* __restrict__ v, ForceCoef k, double* __restrict__ grad,
+                               double* __restrict__ force) {
   const int T = blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= t_c) return;
-  const Node a = load_node(tri[3 * T], xy, phi, u, v);
-  const Node b = load_node(tri[3 * T + 1], xy, phi, u, v);
-  const Node c = load_node(tri[3 * T + 2], xy, phi, u, v);
-  const Node mab = load_node(mid[3 * T], xy, phi, u, v);
-  const Node mbc = load_node(mid[3 * T + 1], xy, phi, u, v);
-  const Node mca = load_node(mid[3 * T + 2], xy, phi, u, v);
+  const int ia = tri[3 * T], ib = tri[3 * T + 1], ic = tri[3 * T + 2];
+  const int iab = mid[3 * T], ibc = mid[3 * T + 1], ica = mid[3 * T + 2];
+  const double2 xa = xy[ia], xb = xy[ib], xc = xy[ic];
+  const double pa = phi[ia], pb = phi[ib], pc = phi[ic], pab = phi[iab], pbc = phi[ibc], pca = phi[ica];
+  // vertex sums of u and v for the four children, sharing the midpoint pairs
+  double su[4] = {0, 0, 0, 0}, sv[4] = {0, 0, 0, 0};
+  if (FORCE) {
+    const double uab = u[iab], ubc = u[ibc], uca = u[ica], vab = v[iab], vbc = v[ibc], vca = v[ica];
+    const double u_a = uab + uca, u_b = uab + ubc, u_c = uca + ubc;
+    const double v_a = vab + vca, v_b = vab + vbc, v_c = vca + vbc;
+    su[0] = u[ia] + u_a; su[1] = u[ib] + u_b; su[2] = u[ic] + u_c; su[3] = u_a + ubc;
+    sv[0] = v[ia] + v_a; sv[1] = v[ib] + v_b; sv[2] = v[ic] + v_c; sv[3] = v_a + vbc;
+  }
+  const double b0 = xb.y - xc.y, b1 = xc.y - xa.y, b2 = xa.y - xb.y;
+  const double c0 = xc.x - xb.x, c1 = xa.x - xc.x, c2 = xb.x - xa.x;
+  const double a2 = (xb.x - xa.x) * (xc.y - xa.y) - (xc.x - xa.x) * (xb.y - xa.y);
+  const double inv2 = 2.0 / a2;
   double gx[4], gy[4], fx[4], fy[4];
-  child(a, mab, mca, bx, by, bz, sigma, gx[0], gy[0], fx[0], fy[0]);
-  child(mab, b, mbc, bx, by, bz, sigma, gx[1], gy[1], fx[1], fy[1]);
-  child(mca, mbc, c, bx, by, bz, sigma, gx[2], gy[2], fx[2], fy[2]);
-  child(mab, mbc, mca, bx, by, bz, sigma, gx[3], gy[3], fx[3], fy[3]);
+  child<FORCE>(pa, pab, pca, su[0], sv[0], b0, b1, b2, c0, c1, c2, inv2, k, gx[0], gy[0], fx[0], fy[0]);
+  child<FORCE>(pab, pb, pbc, su[1], sv[1], b0, b1, b2, c0, c1, c2, inv2, k, gx[1], gy[1], fx[1], fy[1]);
+  child<FORCE>(pca, pbc, pc, su[2], sv[2], b0, b1, b2, c0, c1, c2, inv2, k, gx[2], gy[2], fx[2], fy[2]);
+  child<FORCE>(pab, pbc, pca, su[3], sv[3], -b2, -b0, -b1, -c2, -c0, -c1, inv2, k, gx[3], gy[3], fx[3], fy[3]);
   const size_t t0 = 4 * (size_t)T;
   // four consecutive children: 32-byte aligned vector stores
   reinterpret_cast<double4*>(grad + t0)[0] = make_double4(gx[0], gx[1], gx[2], gx[3]);
@@ -189,12 +197,12 @@ int launch_lorentz(cgp_mesh_impl* m, const double* phi, const double* u, const d
   // one thread per parent (level levels - 1) triangle and its four fine children
   const int bs = 128, gs = (m->t_par + bs - 1) / bs;
   const double2* xy = reinterpret_cast<const double2*>(m->xy_f);
+  const ForceCoef k{sigma * (B[1] * B[1] + B[2] * B[2]) / 3.0, sigma * B[0] * B[1] / 3.0, sigma * B[2],
+                    sigma * (B[0] * B[0] + B[2] * B[2]) / 3.0};
   if (force)
-    lorentz_kernel<true><<<gs, bs, 0, s>>>(m->t_par, m->t_f, m->tri_par, m->mid_par, xy, phi, u, v, B[0], B[1],
-                                           B[2], sigma, grad, force);
+    lorentz_kernel<true><<<gs, bs, 0, s>>>(m->t_par, m->t_f, m->tri_par, m->mid_par, xy, phi, u, v, k, grad, force);
   else
-    lorentz_kernel<false><<<gs, bs, 0, s>>>(m->t_par, m->t_f, m->tri_par, m->mid_par, xy, phi, u, v, B[0], B[1],
-                                            B[2], sigma, grad, force);
+    lorentz_kernel<false><<<gs, bs, 0, s>>>(m->t_par, m->t_f, m->tri_par, m->mid_par, xy, phi, u, v, k, grad, force);
   CGP_CUDA(cudaGetLastError());
   return CGP_OK;
 }
