@@ -269,7 +269,8 @@ int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* col, const do
  *                     blocks per SM (0 = as many as fit; waves: 0 or 1 =
  *                     one block per SM) and flags (bit 0: rows in global
  *                     memory; bit 1: FP64 textbook iteration, as for
- *                     cgp_set_tuning; bit 2: one packed launch, not waves).
+ *                     cgp_set_tuning; bit 2: one packed launch, not waves;
+ *                     bit 3: tagged reductions, as for cgp_set_tuning).
  * cgp_batch_autotune  times a set of launch shapes on the batch's own
  *                     systems (from x = 0) and keeps the fastest; writes the
  *                     best time in ms to best_ms (nullable).  Synchronous;
@@ -426,7 +427,11 @@ int cgp_mesh_set_ogrid(cgp_mesh m, int n_theta, int n_r);
  *         is a compact patch of the mesh (smaller halos; b and x pass through
  *         a gather and a scatter launch; the renumbered system is built once
  *         per block count and boundary condition, about 12 nnz + 45 n_c
- *         bytes); other bits must be 0.
+ *         bytes); bit 3 (FP64 single-reduction form only) passes each
+ *         grid-wide reduction through tagged 128-bit slots that show by
+ *         themselves when every block has stored its partial sum, instead of
+ *         a barrier counter followed by a read of the slots (the same totals,
+ *         bit for bit); other bits must be 0.
  *         SpMV: bit 0 uses the O-grid stencil form (cgp_mesh_set_ogrid) with
  *         one thread per row (lanes ignored).
  * Invalid shapes are rejected with INVALID_ARG.  cgp_autotune sets these.
@@ -449,7 +454,7 @@ int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks, in
  * threads per block {256, 512}, lanes per CSR row {1, 2, 4}, grid size (a
  * few counts around the SM count, and 1..16 blocks for small systems),
  * shared-memory residency, the row order (flag bit 2) and, for FP64, the
- * iteration form (flag bit 1),
+ * iteration form (flag bit 1) and the reduction form (flag bit 3),
  * and keeps the fastest with cgp_set_tuning.  Every candidate meets the
  * same tolerance on the true residual.  x
  * (device [n_c]) is overwritten.  cache_path (nullable) names a text file of

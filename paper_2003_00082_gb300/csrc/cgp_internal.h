@@ -132,6 +132,7 @@ struct cgp_mesh_impl {
   float* f32own = nullptr;   // [6 n] mixed without shared-memory residency: own inner vectors
   float* fpart = nullptr;    // [8 * max_blocks] FP32 partial sums
   double* part = nullptr;    // [max_blocks * 32] per-block fixed-point partial sums
+  unsigned long long* tpart = nullptr;  // [2][3][max_blocks] tagged 128-bit partial sums
   unsigned* bar = nullptr;   // grid barrier counter
   SolveResult* res = nullptr;
   SolveResult* h_res = nullptr;  // pinned host mirror

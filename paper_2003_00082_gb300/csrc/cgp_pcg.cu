@@ -66,6 +66,7 @@ struct Desc {
   float* f32own;      // mixed without RES: own r, u, w, p, s, e ([6][n])
   float* fpart;       // mixed: FP32 partial slots [2][NCOMP][part_stride]
   double* part;
+  unsigned long long* tpart;  // FP64 single-reduction: tagged slots [2][3][part_stride] (128-bit)
   int part_stride;
   unsigned* bar;
   SolveResult* res;
@@ -74,6 +75,7 @@ struct Desc {
   double tol, inner_tol;
   int max_it, max_sweeps, use_x0, mixed;
   int classic;        // FP64: two barriers per iteration (Saad, Alg. 9.1) instead of the single-reduction form
+  int tagged;         // FP64 single-reduction: reductions through tagged slots instead of the group barrier
   const unsigned char* fixed;  // far-field Dirichlet rows (phi = 0), or NULL for the natural condition everywhere
   int res_nnz_cap;    // RES: capacity of the shared-memory CSR slice
   int halo_cap;       // RES: capacity of the halo gather buffer
@@ -105,6 +107,7 @@ struct Shared {
   float ftot[4];
   float fsc[8];
   int flag;
+  int tflag;                    // outcome of the last tagged reduction's wait
 };
 
 // Barrier over the blocks of one instance (cgp_sync.h): a block that gives
@@ -138,6 +141,8 @@ struct Group {
     __syncthreads();
     return nblk == 1 || sh.flag != 0;
   }
+  // The wait of one thread (no block barrier): false when it gave up.
+  __device__ bool wait_one() { return nblk == 1 || barrier_wait(bar, timeout, nblk, epoch, spin_ns); }
 };
 
 __device__ __forceinline__ fx::I128 shfl_xor_i128(fx::I128 a, int o) {
@@ -166,12 +171,27 @@ __device__ __forceinline__ unsigned long long* part_slot(const Desc& d, int red,
   return reinterpret_cast<unsigned long long*>(d.part) + 4 * ((size_t)((red & 1) * NCOMP + c) * d.part_stride + blk);
 }
 
+// Tagged slots: one 128-bit word per (bank, component, block) that says by
+// itself whether it holds reduction `red`, so a block can read the slots
+// while it waits for the group barrier instead of after it:
+//   lo = m[0:56) << 8 | tag8,  hi = m[56:80) | E << 24 | tag24 << 40,
+// m = the block's fixed-point partial shifted right by kTagShift (a block of
+// <= 1024 threads sums to < 2^117, so m fits 80 signed bits), E its exponent.
+// tag24 = 2^23 | (red mod 2^23) is never 0 (a slot zeroed at the start of a
+// launch) nor all ones (a sign extension); tag8 repeats red in the low word.
+constexpr int kTagShift = 38;
+__device__ __forceinline__ unsigned long long tag24(int red) { return 0x800000ull | ((unsigned)red & 0x7FFFFFu); }
+__device__ __forceinline__ unsigned long long tag8(int red) { return ((unsigned)red & 0xFFu) ^ 0xA5u; }
+__device__ __forceinline__ ulonglong2* tag_slot(const Desc& d, int red, int c, int blk) {
+  return reinterpret_cast<ulonglong2*>(d.tpart) + ((size_t)((red & 1) * 3 + c) * d.part_stride + blk);
+}
+
 // Sum NC (<= 3) per-thread values over the block; warp c then folds
 // component c over the warps and stores it as this block's partial in bank
-// (red & 1).  The sums are exact fixed-point integer sums (cgp_fixed.h): they
-// run on the integer pipe, cost no FP64 instructions, and do not depend on
-// the order of the terms.
-template <int NC>
+// (red & 1): untagged in d.part, or TAGGED in d.tpart.  The sums are exact
+// fixed-point integer sums (cgp_fixed.h): they run on the integer pipe, cost
+// no FP64 instructions, and do not depend on the order of the terms.
+template <int NC, bool TAGGED = false>
 __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, double (&v)[NC], Shared& sh) {
   static_assert(NC >= 1 && NC <= 3, "one to three components per reduction");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -185,6 +205,7 @@ __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, dou
       sh.wexp[c][warp] = E;
     }
   }
+  if (TAGGED && threadIdx.x == 0) sh.tflag = 1;
   __syncthreads();
   for (int c = warp; c < NC; c += nw) {
     fx::I128 x = 0;
@@ -196,9 +217,17 @@ __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, dou
     const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
     x = warp_sum_i128(E < fx::kBadExp ? fx::sar(x, E - e) : (fx::I128)0);
     if (lane == 0) {
-      ulonglong2* slot = reinterpret_cast<ulonglong2*>(part_slot(d, red, c, lb));
-      slot[0] = make_ulonglong2((unsigned long long)x, (unsigned long long)(x >> 64));
-      slot[1] = make_ulonglong2((unsigned long long)E, 0ull);
+      if (TAGGED) {
+        const fx::I128 m = E < fx::kBadExp ? fx::sar(x, kTagShift) : (fx::I128)0;
+        const unsigned long long lo = ((unsigned long long)m << 8) | tag8(red);
+        const unsigned long long hi = ((unsigned long long)(m >> 56) & 0xFFFFFFull) |
+                                      ((unsigned long long)(E & 0xFFFF) << 24) | (tag24(red) << 40);
+        st_relaxed_b128(tag_slot(d, red, c, lb), lo, hi);
+      } else {
+        ulonglong2* slot = reinterpret_cast<ulonglong2*>(part_slot(d, red, c, lb));
+        slot[0] = make_ulonglong2((unsigned long long)x, (unsigned long long)(x >> 64));
+        slot[1] = make_ulonglong2((unsigned long long)E, 0ull);
+      }
     }
   }
 }
@@ -273,6 +302,133 @@ __device__ __forceinline__ void get_totals_then(const Desc& d, int red, Shared& 
   if (wk > 1 && (int)(threadIdx.x >> 5) < wk) asm volatile("bar.sync 1, %0;" ::"r"(wk * 32) : "memory");
   if (threadIdx.x == 0) derive(sh);
   __syncthreads();
+}
+
+// One warp: wait until every block of the group has stored component c of
+// reduction `red` in its tagged slot, then fold the slots as group_total does
+// (fixed order, identical bits in every block).  Each lane polls its slots
+// with relaxed loads, re-reading only those that did not yet carry the tag,
+// so the polling load on the slots' cache lines falls as blocks arrive.
+// (Visibility of the other blocks' published vectors comes from the group
+// barrier, not from these loads.)  Gives up (false on every lane) after
+// d.spin_ns of wall-clock time or when another block has given up.
+__device__ __forceinline__ bool tagged_total(const Desc& d, int red, int c, double& total) {
+  constexpr int PRE = 8;  // slots per lane per pass (groups of up to 256 blocks per pass)
+  const int lane = threadIdx.x & 31;
+  const unsigned long long w24 = tag24(red), w8 = tag8(red);
+  int* const timeout = &d.res->timeout;
+  fx::I128 acc = 0;
+  int Ea = 1;
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+  for (int base = 0; base < d.nblk; base += 32 * PRE) {
+    ulonglong2 w[PRE];
+    unsigned pend = 0;   // slots of this lane still without the tag
+#pragma unroll
+    for (int t = 0; t < PRE; ++t) {
+      w[t] = make_ulonglong2(0ull, 1ull << 24);  // m = 0, E = 1 for slots past the group
+      if (base + lane + 32 * t < d.nblk) pend |= 1u << t;
+    }
+    while (true) {
+      // every load of the round is issued before any is examined (a pending
+      // slot's word is overwritten; a tagged one is kept)
+      const unsigned pm = pend;
+#pragma unroll
+      for (int t = 0; t < PRE; ++t)
+        if (pm & (1u << t)) w[t] = ld_relaxed_b128(tag_slot(d, red, c, base + lane + 32 * t));
+#pragma unroll
+      for (int t = 0; t < PRE; ++t)
+        if ((pm & (1u << t)) && (w[t].y >> 40) == w24 && (w[t].x & 0xFFull) == w8) pend &= ~(1u << t);
+      if (__all_sync(0xffffffffu, pend == 0)) break;
+      if ((++spins & 63u) == 0) {
+        int give_up = 0;
+        if (lane == 0) {
+          if (*(volatile int*)timeout) {
+            give_up = 1;
+          } else {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) {
+              t0 = now;
+            } else if ((long long)(now - t0) > d.spin_ns) {
+              atomicExch(timeout, 1);
+              give_up = 1;
+            }
+          }
+        }
+        if (__shfl_sync(0xffffffffu, give_up, 0)) return false;
+      }
+    }
+    int ex[PRE];
+    int e = Ea;
+#pragma unroll
+    for (int t = 0; t < PRE; ++t) {
+      ex[t] = (int)((w[t].y >> 24) & 0xFFFFull);
+      e = max(e, ex[t]);
+    }
+    fx::I128 a = fx::sar(acc, e - Ea);
+#pragma unroll
+    for (int t = 0; t < PRE; ++t) {
+      const long long mh = ((long long)(w[t].y << 40)) >> 40;  // m[56:80), sign-extended
+      const fx::I128 m = ((fx::I128)mh << 56) | (fx::I128)(w[t].x >> 8);
+      a += fx::sar(m, e - ex[t]);
+    }
+    acc = a;
+    Ea = e;
+  }
+  const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)Ea);
+  const fx::I128 t = warp_sum_i128(E < fx::kBadExp ? fx::sar(acc, E - Ea) : (fx::I128)0);
+  total = E < fx::kBadExp ? fx::to_double(t, E + kTagShift) : fx::to_double(0, fx::kBadExp);
+  return true;
+}
+
+// One reduction of the FP64 single-reduction solver.  red_start publishes
+// the block's partials and arrives at the group barrier; work between the two
+// calls overlaps the other blocks' arrival and must not write what other
+// blocks read.  red_finish waits for the barrier (which makes the other
+// blocks' published vectors visible), leaves the totals in sh.tot, runs
+// stage() on every thread and derive(sh) on thread 0.
+//
+// Untagged, the slots are read after the barrier: two global round trips
+// after the last block arrives.  Tagged (d.tagged), warps 0 .. NC-1 poll the
+// slots while another thread waits on the barrier, so the totals are known
+// when the barrier completes.
+template <int NC>
+__device__ __forceinline__ void red_start(const Desc& d, Group& grp, int lb, int red, double (&v)[NC], Shared& sh) {
+  if (d.tagged) put_partials<NC, true>(d, lb, red, v, sh);
+  else put_partials<NC>(d, lb, red, v, sh);
+  grp.arrive();
+}
+
+template <int NC, typename F, typename G>
+__device__ __forceinline__ bool red_finish(const Desc& d, Group& grp, int red, Shared& sh, F derive, G stage) {
+  if (!d.tagged) {
+    if (!grp.wait(sh)) return false;
+    stage();
+    get_totals_then<NC>(d, red, sh, derive);
+    return true;
+  }
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < NC; c += nw) {
+    double t;
+    if (!tagged_total(d, red, c, t)) {
+      if ((threadIdx.x & 31) == 0) sh.tflag = 0;
+      break;
+    }
+    if ((threadIdx.x & 31) == 0) sh.tot[c] = t;
+  }
+  // the barrier wait: lane 0 of the first warp that polls no slots (thread 0 after its slots otherwise)
+  if (threadIdx.x == (nw > NC ? 32 * NC : 0) && !grp.wait_one()) sh.tflag = 0;
+  __syncthreads();
+  if (!sh.tflag) return false;
+  stage();
+  if (threadIdx.x == 0) derive(sh);
+  __syncthreads();
+  return true;
+}
+
+template <int NC>
+__device__ __forceinline__ bool red_finish(const Desc& d, Group& grp, int red, Shared& sh) {
+  return red_finish<NC>(d, grp, red, sh, [](Shared&) {}, [] {});
 }
 
 __device__ void finish(const Desc& d, int lb, int status, int its, int sweeps, double rel_rec, double rel_true,
@@ -645,7 +801,8 @@ __device__ void solve_fp64(const Desc& d, int lb, Shared& sh) {
 }
 
 // FP64 Jacobi-PCG in the single-reduction form of Chronopoulos and Gear:
-// one group barrier per iteration.
+// one grid-wide reduction per iteration (red_start / red_finish; with tuning
+// flag bit 3 its slots are tagged and read while the barrier fills).
 //
 // With u = D^-1 r and w = K u, the recurrences p = u + beta p and
 // s = w + beta s (so that s = K p) replace the product K p, and (r,u),
@@ -745,6 +902,15 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
     L.val = d.val;
   }
 
+  if (d.tagged) {
+    if (!d.tpart) {   // the tagged slots are part of every mesh's scratch; a descriptor without them is a bug
+      finish(d, lb, CGP_ERR_INVALID_ARG, 0, 0, 0.0, 0.0, 0.0);
+      return;
+    }
+    // this block's tagged slots start empty; the group barrier of the first
+    // reduction orders that before any block reads them
+    if (tid < 6) *tag_slot(d, tid / 3, tid % 3, lb) = make_ulonglong2(0ull, 0ull);
+  }
   // ---- means of b and x0 ----
   {
     double v2[2] = {0.0, 0.0};
@@ -769,9 +935,8 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       x[i] = xi;
       if (RES) d.x[r0 + i] = xi;
     }
-    put_partials<1>(d, lb, red, v1, sh);
-    if (!grp.sync(sh)) return;
-    get_totals<1>(d, red, sh);
+    red_start<1>(d, grp, lb, red, v1, sh);
+    if (!red_finish<1>(d, grp, red, sh)) return;
     ++red;
   }
   const double bnorm = sqrt(sh.tot[0]);
@@ -807,9 +972,8 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
         spmv_local<T, double>(
             L, r0, nloc, [&](int jl) { return x[jl]; }, [&](int j) { return __ldcg(d.x + j); }, op);
       }
-      put_partials<1>(d, lb, red, v1, sh);
-      if (!grp.sync(sh)) return;   // also publishes r for the first product
-      get_totals<1>(d, red, sh);
+      red_start<1>(d, grp, lb, red, v1, sh);
+      if (!red_finish<1>(d, grp, red, sh)) return;   // also publishes r for the first product
       ++red;
     }
     rr_true = sh.tot[0];
@@ -842,20 +1006,37 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
         spmv_local<T, double>(
             L, r0, nloc, [&](int jl) { return u[jl]; }, [&](int j) { return d.dinv[j] * __ldcg(R0 + j); }, op);
       }
-      put_partials<3>(d, lb, red, v3, sh);
-      if (!grp.sync(sh)) return;
+      red_start<3>(d, grp, lb, red, v3, sh);
     }
-    // RES: while warps 0-2 fetch the reduction's totals, the other warps stage the
-    // halo inputs r_j, w_j, s_j of the coming iteration (they do not depend on the
-    // scalars), so the two global round trips overlap
+    // RES: as soon as the reduction's slots show that every block has published,
+    // the threads above warp 2 load the halo inputs r_j, w_j, s_j of the coming
+    // iteration (they do not depend on the scalars).  A thread's first HREG
+    // entries go to registers and are consumed by the same thread after the
+    // own-row update, so the loads overlap the derivation and that update; any
+    // further entries go through shared memory.
     constexpr int TW = 3 * 32;
+    constexpr int HREG = 2;
     const bool staged = RES && bd > TW;
+    double hR[HREG], hW[HREG], hS[HREG];
+#pragma unroll
+    for (int q = 0; q < HREG; ++q) hR[q] = hW[q] = hS[q] = 0.0;
     auto stage = [&](int kk) {
       if (!staged || tid < TW) return;
       const double* Rc = (kk & 1) ? R1 : R0;
       const double* Wc = (kk & 1) ? W1 : W0;
       const double* Sc = (kk & 1) ? S1 : S0;
-      for (int h = tid - TW; h < nh; h += bd - TW) {
+      const int hs = bd - TW;
+      int h = tid - TW;
+#pragma unroll
+      for (int q = 0; q < HREG; ++q, h += hs) {
+        if (h < nh) {
+          const int j = hid[h];
+          hR[q] = __ldcg(Rc + j);
+          hW[q] = __ldcg(Wc + j);
+          if (kk > 0) hS[q] = __ldcg(Sc + j);
+        }
+      }
+      for (; h < nh; h += hs) {
         const int j = hid[h];
         stR[h] = __ldcg(Rc + j);
         stW[h] = __ldcg(Wc + j);
@@ -885,8 +1066,7 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       S.sc[2] = g;
       S.sc[5] = rr;
     };
-    stage(0);
-    get_totals_then<3>(d, red, sh, derive);
+    if (!red_finish<3>(d, grp, red, sh, derive, [&] { stage(0); })) return;
     ++red;
     while (true) {
       const int st = sh.isc[0];
@@ -906,7 +1086,7 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       double* Wn = (k & 1) ? W0 : W1;
       double* Sn = (k & 1) ? S0 : S1;
       // RES: u_k stays in uc while u_(k+1) goes to un, so that p and x (off the
-      // critical path) are updated while the other blocks arrive at the barrier
+      // critical path) are updated while the reduction completes
       double* uc = (RES && (k & 1)) ? u2 : u;
       double* un = (RES && !(k & 1)) ? u2 : u;
       // own rows: s, r, u (and without RES p, x); r and s published
@@ -933,9 +1113,20 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       };
       if constexpr (RES) {
         if (staged) {
-          for (int h = tid; h < nh; h += bd) {
-            const double sj = k == 0 ? stW[h] : fma(beta, stS[h], stW[h]);
-            ext[nloc + h] = dih[h] * fma(-alpha, sj, stR[h]);
+          if (tid >= TW) {   // the entries this thread staged
+            const int hs = bd - TW;
+            int h = tid - TW;
+#pragma unroll
+            for (int q = 0; q < HREG; ++q, h += hs) {
+              if (h < nh) {
+                const double sj = k == 0 ? hW[q] : fma(beta, hS[q], hW[q]);
+                ext[nloc + h] = dih[h] * fma(-alpha, sj, hR[q]);
+              }
+            }
+            for (; h < nh; h += hs) {
+              const double sj = k == 0 ? stW[h] : fma(beta, stS[h], stW[h]);
+              ext[nloc + h] = dih[h] * fma(-alpha, sj, stR[h]);
+            }
           }
         } else {
           for (int h = tid; h < nh; h += bd) ext[nloc + h] = halo_u(hid[h], dih[h]);
@@ -957,19 +1148,16 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
         spmv_local<T, double>(
             L, r0, nloc, [&](int jl) { return un[jl]; }, [&](int j) { return halo_u(j, d.dinv[j]); }, op);
       }
-      put_partials<3>(d, lb, red, v3, sh);
-      grp.arrive();
-      if constexpr (RES) {   // p_k = u_k + beta p_(k-1), x += alpha p_k while the barrier fills
+      red_start<3>(d, grp, lb, red, v3, sh);
+      if constexpr (RES) {   // p_k = u_k + beta p_(k-1), x += alpha p_k while the other blocks catch up
         for (int i = tid; i < nloc; i += bd) {
           const double pi = k == 0 ? uc[i] : fma(beta, p[i], uc[i]);
           p[i] = pi;
           x[i] = fma(alpha, pi, x[i]);
         }
       }
-      if (!grp.wait(sh)) return;
       ++k;
-      stage(k);
-      get_totals_then<3>(d, red, sh, derive);
+      if (!red_finish<3>(d, grp, red, sh, derive, [&] { stage(k); })) return;
       ++red;
     }
     its += k;
@@ -978,9 +1166,8 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
     {
       double v1[1] = {0.0};
       for (int i = tid; i < nloc; i += bd) v1[0] += x[i];
-      put_partials<1>(d, lb, red, v1, sh);
-      if (!grp.sync(sh)) return;
-      get_totals<1>(d, red, sh);
+      red_start<1>(d, grp, lb, red, v1, sh);
+      if (!red_finish<1>(d, grp, red, sh)) return;
       ++red;
     }
     const double mxf = d.fixed ? 0.0 : sh.tot[0] / d.n;
@@ -1848,6 +2035,7 @@ Desc make_desc(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opt
   d.f32own = m->f32own;
   d.fpart = m->fpart;
   d.part = m->part;
+  d.tpart = m->tpart;
   d.part_stride = m->max_blocks;
   d.bar = bar;
   d.res = res;
@@ -1861,6 +2049,7 @@ Desc make_desc(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_opt
   d.use_x0 = o.use_x0;
   d.mixed = o.precision == CGP_MIXED ? 1 : 0;
   d.classic = (flags & 2) ? 1 : 0;
+  d.tagged = (flags & 8) ? 1 : 0;
   d.res_nnz_cap = plan.nnz_cap;
   d.halo_cap = plan.halo_cap;
   d.lcol = plan.halo.lcol;
@@ -2408,10 +2597,10 @@ static bool valid_shape(int what, int block, int lanes) {
 extern "C" int cgp_set_tuning(cgp_mesh m, int what, int block, int lanes, int blocks, int flags) {
   if (!m) return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: NULL mesh");
   if (what < 0 || what > 3) return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: unknown target");
-  if (!valid_shape(what, block, lanes) || blocks < 0 || (flags & ~7))
+  if (!valid_shape(what, block, lanes) || blocks < 0 || (flags & ~15))
     return fail(CGP_ERR_INVALID_ARG, "cgp_set_tuning: block must be 0 or a multiple of 32 in [64, 512] "
                                      "(solver) or [64, 256] (SpMV), "
-                                     "lanes 0, 1, 2, 4, 8 or 32, blocks >= 0, flags 0 to 7");
+                                     "lanes 0, 1, 2, 4, 8 or 32, blocks >= 0, flags 0 to 15");
   m->tune[what] = SolverTuning{block, lanes, blocks, flags};
   return CGP_OK;
 }
@@ -2528,7 +2717,7 @@ extern "C" int cgp_batch_create(const cgp_mesh* meshes, int count, const double*
 
 extern "C" int cgp_batch_set_tuning(cgp_batch batch, int block, int lanes, int blocks_per_sm, int flags) {
   if (!batch) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_set_tuning: NULL batch");
-  if (!valid_shape(CGP_TUNE_SOLVE_FP64, block, lanes) || blocks_per_sm < 0 || (flags & ~7))
+  if (!valid_shape(CGP_TUNE_SOLVE_FP64, block, lanes) || blocks_per_sm < 0 || (flags & ~15))
     return fail(CGP_ERR_INVALID_ARG, "cgp_batch_set_tuning: bad shape");
   return batch_plan_any(batch, BatchShape{block, lanes, blocks_per_sm, flags}, batch->opts);
 }
@@ -2720,12 +2909,18 @@ extern "C" int cgp_autotune(cgp_mesh m, int precision, const double* b, double* 
   const SolverTuning saved = m->tune[what];
   SolverTuning best{};
   float best_t = 1e30f;
-  const int nflags = precision == CGP_MIXED ? 2 : 4;   // bit 1 (classic FP64 iteration) only for FP64
-  for (int fl8 = 0; fl8 < 2 * nflags; ++fl8)            // bit 2 (bisection order) on top
+  // bit 1 (classic FP64 iteration) and bit 3 (tagged reductions of the
+  // single-reduction form) only for FP64; bit 2 (bisection order) for both
+  std::vector<int> flag_set;
+  for (int fl = 0; fl < 16; ++fl) {
+    if (precision == CGP_MIXED && (fl & 10)) continue;
+    if ((fl & 2) && (fl & 8)) continue;
+    flag_set.push_back(fl);
+  }
+  for (int fl : flag_set)
     for (int bk : {256, 512})
       for (int ln : {1, 2, 4})
         for (int c : counts) {
-          const int fl = (fl8 % nflags) | (fl8 >= nflags ? 4 : 0);
           m->tune[what] = SolverTuning{bk, ln, c, fl};
           float t = 1e30f;
           for (int rep = 0; rep < 2; ++rep) {

@@ -1,8 +1,7 @@
 // Grid-wide barrier of a cooperative launch, with a wall-clock limit.
 //
 // Arrival is a release-add on a counter that only grows; a block waits until
-// the counter reaches epoch * nblk, polling with relaxed loads and finishing
-// with an acquire.  The wait gives up after spin_ns of wall-clock time, or as
+// the counter reaches epoch * nblk, polling with acquire loads.  The wait gives up after spin_ns of wall-clock time, or as
 // soon as another block has given up (the shared timeout word), and then
 // reports failure instead of hanging.
 #pragma once
@@ -13,16 +12,26 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+// One 128-bit access: a single memory operation (no tearing between the halves).
+__device__ __forceinline__ void st_relaxed_b128(void* p, unsigned long long lo, unsigned long long hi) {
+  asm volatile("{\n\t.reg .b128 t;\n\tmov.b128 t, {%1, %2};\n\tst.relaxed.gpu.global.b128 [%0], t;\n\t}" ::"l"(p),
+               "l"(lo), "l"(hi)
+               : "memory");
+}
+
+__device__ __forceinline__ ulonglong2 ld_relaxed_b128(const void* p) {
+  unsigned long long lo, hi;
+  asm volatile("{\n\t.reg .b128 t;\n\tld.relaxed.gpu.global.b128 t, [%2];\n\tmov.b128 {%0, %1}, t;\n\t}"
+               : "=l"(lo), "=l"(hi)
+               : "l"(p)
+               : "memory");
+  return make_ulonglong2(lo, hi);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -39,7 +48,9 @@ __device__ __forceinline__ bool barrier_wait(unsigned* bar, int* timeout, unsign
   const unsigned target = epoch * nblk;
   unsigned long long t0 = 0;
   unsigned spins = 0;
-  while (ld_relaxed(bar) < target) {
+  // acquire on every poll: the load that sees the count complete is itself the
+  // acquire, so no further round trip follows it
+  while (ld_acquire(bar) < target) {
     if ((++spins & 127u) == 0) {
       if (*(volatile int*)timeout) return false;
       const unsigned long long now = global_ns();
@@ -51,7 +62,6 @@ __device__ __forceinline__ bool barrier_wait(unsigned* bar, int* timeout, unsign
       }
     }
   }
-  (void)ld_acquire(bar);
   return true;
 }
 

@@ -162,11 +162,12 @@ def assert_iterations_match(info, ref_its, textbook):
 SHAPES = [(128, 1, 1), (128, 2, 5), (128, 4, 3), (256, 8, 7), (64, 32, 2), (64, 1, 13), (512, 1, 0)]
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 5, 6, 8, 9, 12, 13])
 @pytest.mark.parametrize("block,lanes,blocks", SHAPES)
 def test_fp64_solve_matches_oracle(pair, cgp, block, lanes, blocks, flags):
     """Both FP64 iterations (bit 1: textbook, else single-reduction) in both storage modes (bit 0),
-    in the mesh's row order and renumbered by coordinate bisection (bit 2).
+    in the mesh's row order and renumbered by coordinate bisection (bit 2), with the
+    single-reduction form's reductions behind the group barrier or through tagged slots (bit 3).
 
     The single-reduction form takes the same steps in exact arithmetic; its
     recurrences round differently, so its count may differ by a little more,
@@ -238,7 +239,7 @@ def test_solver_status_codes(cgp):
     u, v = velocity_for(om)
     b = oracle_rhs(om, u, v)
     x = torch.zeros(m.n_c, dtype=torch.float64, device=DEV)
-    for flags in (0, 2):     # single-reduction and textbook FP64 iterations
+    for flags in (0, 2, 8):     # single-reduction, textbook, single-reduction with tagged reductions
         cgp.cgp_set_tuning(m.handle, cgp.CGP_TUNE_SOLVE_FP64, 0, 0, 0, flags)
         x.zero_()
         info = cgp.cgp_poisson_solve(m.handle, T(b), x, tol=1e-12, max_it=3)
@@ -469,7 +470,7 @@ def test_velocity_correction_matches_oracle(cgp, levels, name):
 # ----------------------------------------------------------------------------
 # far-field Dirichlet variant
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("precision,flags", [(0, 0), (0, 1), (0, 2), (1, 0), (0, 4), (1, 4)])
+@pytest.mark.parametrize("precision,flags", [(0, 0), (0, 1), (0, 2), (1, 0), (0, 4), (1, 4), (0, 12)])
 @pytest.mark.parametrize("name", ["square", "ogrid-7x3", "ogrid-33x17", "ogrid-64x32"])
 def test_far_field_dirichlet_solve_matches_oracle(cgp, name, precision, flags):
     xy, tri = meshes()[name]
