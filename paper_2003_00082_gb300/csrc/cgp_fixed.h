@@ -134,5 +134,31 @@ CGP_HD inline double to_double(I128 X, int E) {
 
 CGP_HD inline I128 add(I128 a, I128 b) { return a + b; }
 
+// Tagged slot: one block's partial X (exponent E, |X| < 2^117 for a block of
+// <= 1024 threads) of reduction `red` in one 128-bit word that says by itself
+// whether it holds that reduction:
+//   lo = m[0:56) << 8 | tag8,  hi = m[56:80) | E << 24 | tag24 << 40,
+// m = X >> kTagShift (80 signed bits).  tag24 = 2^23 | (red mod 2^23) is
+// never 0 (a zeroed slot) nor all ones; tag8 repeats red in the low word, so
+// a word whose halves come from two different stores fails the check.  The
+// value of a slot is m * 2^(kTagShift + E - 1075 - kFrac).
+constexpr int kTagShift = 38;
+CGP_HD inline uint64_t tag24(int red) { return 0x800000ull | ((unsigned)red & 0x7FFFFFu); }
+CGP_HD inline uint64_t tag8(int red) { return ((unsigned)red & 0xFFu) ^ 0xA5u; }
+
+CGP_HD inline void pack_tagged(I128 x, int E, int red, uint64_t& lo, uint64_t& hi) {
+  const I128 m = E < kBadExp ? sar(x, kTagShift) : (I128)0;
+  lo = ((uint64_t)m << 8) | tag8(red);
+  hi = ((uint64_t)(m >> 56) & 0xFFFFFFull) | ((uint64_t)(E & 0xFFFF) << 24) | (tag24(red) << 40);
+}
+CGP_HD inline bool tagged_current(uint64_t lo, uint64_t hi, int red) {
+  return (hi >> 40) == tag24(red) && (lo & 0xFFull) == tag8(red);
+}
+CGP_HD inline int tagged_exponent(uint64_t hi) { return (int)((hi >> 24) & 0xFFFFull); }
+CGP_HD inline I128 tagged_mantissa(uint64_t lo, uint64_t hi) {
+  const int64_t mh = ((int64_t)(hi << 40)) >> 40;  // m[56:80), sign-extended
+  return ((I128)mh << 56) | (I128)(lo >> 8);
+}
+
 }  // namespace fx
 }  // namespace cgp

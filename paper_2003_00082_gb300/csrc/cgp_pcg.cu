@@ -171,17 +171,10 @@ __device__ __forceinline__ unsigned long long* part_slot(const Desc& d, int red,
   return reinterpret_cast<unsigned long long*>(d.part) + 4 * ((size_t)((red & 1) * NCOMP + c) * d.part_stride + blk);
 }
 
-// Tagged slots: one 128-bit word per (bank, component, block) that says by
-// itself whether it holds reduction `red`, so a block can read the slots
-// while it waits for the group barrier instead of after it:
-//   lo = m[0:56) << 8 | tag8,  hi = m[56:80) | E << 24 | tag24 << 40,
-// m = the block's fixed-point partial shifted right by kTagShift (a block of
-// <= 1024 threads sums to < 2^117, so m fits 80 signed bits), E its exponent.
-// tag24 = 2^23 | (red mod 2^23) is never 0 (a slot zeroed at the start of a
-// launch) nor all ones (a sign extension); tag8 repeats red in the low word.
-constexpr int kTagShift = 38;
-__device__ __forceinline__ unsigned long long tag24(int red) { return 0x800000ull | ((unsigned)red & 0x7FFFFFu); }
-__device__ __forceinline__ unsigned long long tag8(int red) { return ((unsigned)red & 0xFFu) ^ 0xA5u; }
+// Tagged slots (cgp_fixed.h: fx::pack_tagged): one 128-bit word per (bank,
+// component, block) that says by itself whether it holds reduction `red`, so
+// a block can read the slots while it waits for the group barrier instead of
+// after it.  A block zeroes its slots at the start of a launch.
 __device__ __forceinline__ ulonglong2* tag_slot(const Desc& d, int red, int c, int blk) {
   return reinterpret_cast<ulonglong2*>(d.tpart) + ((size_t)((red & 1) * 3 + c) * d.part_stride + blk);
 }
@@ -218,10 +211,8 @@ __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, dou
     x = warp_sum_i128(E < fx::kBadExp ? fx::sar(x, E - e) : (fx::I128)0);
     if (lane == 0) {
       if (TAGGED) {
-        const fx::I128 m = E < fx::kBadExp ? fx::sar(x, kTagShift) : (fx::I128)0;
-        const unsigned long long lo = ((unsigned long long)m << 8) | tag8(red);
-        const unsigned long long hi = ((unsigned long long)(m >> 56) & 0xFFFFFFull) |
-                                      ((unsigned long long)(E & 0xFFFF) << 24) | (tag24(red) << 40);
+        uint64_t lo, hi;
+        fx::pack_tagged(x, E, red, lo, hi);
         st_relaxed_b128(tag_slot(d, red, c, lb), lo, hi);
       } else {
         ulonglong2* slot = reinterpret_cast<ulonglong2*>(part_slot(d, red, c, lb));
@@ -315,7 +306,6 @@ __device__ __forceinline__ void get_totals_then(const Desc& d, int red, Shared& 
 __device__ __forceinline__ bool tagged_total(const Desc& d, int red, int c, double& total) {
   constexpr int PRE = 8;  // slots per lane per pass (groups of up to 256 blocks per pass)
   const int lane = threadIdx.x & 31;
-  const unsigned long long w24 = tag24(red), w8 = tag8(red);
   int* const timeout = &d.res->timeout;
   fx::I128 acc = 0;
   int Ea = 1;
@@ -338,7 +328,7 @@ __device__ __forceinline__ bool tagged_total(const Desc& d, int red, int c, doub
         if (pm & (1u << t)) w[t] = ld_relaxed_b128(tag_slot(d, red, c, base + lane + 32 * t));
 #pragma unroll
       for (int t = 0; t < PRE; ++t)
-        if ((pm & (1u << t)) && (w[t].y >> 40) == w24 && (w[t].x & 0xFFull) == w8) pend &= ~(1u << t);
+        if ((pm & (1u << t)) && fx::tagged_current(w[t].x, w[t].y, red)) pend &= ~(1u << t);
       if (__all_sync(0xffffffffu, pend == 0)) break;
       if ((++spins & 63u) == 0) {
         int give_up = 0;
@@ -362,22 +352,20 @@ __device__ __forceinline__ bool tagged_total(const Desc& d, int red, int c, doub
     int e = Ea;
 #pragma unroll
     for (int t = 0; t < PRE; ++t) {
-      ex[t] = (int)((w[t].y >> 24) & 0xFFFFull);
+      ex[t] = fx::tagged_exponent(w[t].y);
       e = max(e, ex[t]);
     }
     fx::I128 a = fx::sar(acc, e - Ea);
 #pragma unroll
     for (int t = 0; t < PRE; ++t) {
-      const long long mh = ((long long)(w[t].y << 40)) >> 40;  // m[56:80), sign-extended
-      const fx::I128 m = ((fx::I128)mh << 56) | (fx::I128)(w[t].x >> 8);
-      a += fx::sar(m, e - ex[t]);
+      a += fx::sar(fx::tagged_mantissa(w[t].x, w[t].y), e - ex[t]);
     }
     acc = a;
     Ea = e;
   }
   const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)Ea);
   const fx::I128 t = warp_sum_i128(E < fx::kBadExp ? fx::sar(acc, E - Ea) : (fx::I128)0);
-  total = E < fx::kBadExp ? fx::to_double(t, E + kTagShift) : fx::to_double(0, fx::kBadExp);
+  total = E < fx::kBadExp ? fx::to_double(t, E + fx::kTagShift) : fx::to_double(0, fx::kBadExp);
   return true;
 }
 

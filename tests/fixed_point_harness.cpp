@@ -5,6 +5,12 @@
 // are aligned to the overall largest exponent and added, exactly as the
 // GPU does per warp, per block and across blocks.  Prints the bit pattern
 // of the converted total.
+//
+// A first line "R red" selects the tagged form: every group sum (one
+// block's partial) goes through a tagged slot of reduction `red` and back
+// before the groups are added.  Exit status 3: a slot did not read as
+// current; 4: a slot built from halves of two stores, or a zeroed slot,
+// read as current.
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -17,7 +23,12 @@ int main() {
   std::vector<std::vector<double>> groups;
   char tag[8];
   int n;
+  int red = -1;
   while (std::scanf("%7s %d", tag, &n) == 2) {
+    if (tag[0] == 'R') {
+      red = n;
+      continue;
+    }
     std::vector<double> g(n);
     for (int i = 0; i < n; ++i) {
       unsigned long long b;
@@ -38,6 +49,20 @@ int main() {
     gsum.push_back(s);
     gexp.push_back(e);
     E = e > E ? e : E;
+  }
+  if (red >= 0) {
+    I128 t = 0;
+    for (size_t i = 0; i < gsum.size(); ++i) {
+      uint64_t lo, hi, lo2, hi2;
+      pack_tagged(gsum[i], gexp[i], red, lo, hi);
+      pack_tagged(gsum[i] + 12345, gexp[i], red - 2, lo2, hi2);   // the bank's previous store
+      if (!tagged_current(lo, hi, red)) return 3;
+      if (tagged_current(lo2, hi, red) || tagged_current(lo, hi2, red) || tagged_current(0, 0, red)) return 4;
+      if (tagged_exponent(hi) != gexp[i]) return 3;
+      if (E < kBadExp) t = add(t, sar(tagged_mantissa(lo, hi), E - gexp[i]));
+    }
+    std::printf("%016llx\n", (unsigned long long)dbits(E < kBadExp ? to_double(t, E + kTagShift) : to_double(0, kBadExp)));
+    return 0;
   }
   I128 t = 0;
   if (E < kBadExp)

@@ -34,8 +34,9 @@ def bits(v):
     return struct.unpack("<Q", struct.pack("<d", float(v)))[0]
 
 
-def run(harness, groups):
-    text = "".join(f"G {len(g)}\n" + " ".join(f"{bits(v):x}" for v in g) + "\n" for g in groups)
+def run(harness, groups, red=None):
+    text = "" if red is None else f"R {red}\n"
+    text += "".join(f"G {len(g)}\n" + " ".join(f"{bits(v):x}" for v in g) + "\n" for g in groups)
     r = subprocess.run([harness], input=text, capture_output=True, text=True, check=True)
     return struct.unpack("<d", struct.pack("<Q", int(r.stdout.strip(), 16)))[0]
 
@@ -97,3 +98,35 @@ def test_large_sums_do_not_overflow(harness):
     got = run(harness, groups)
     want = exact(groups)
     assert ulp_diff(got, want) <= 1
+
+
+# ---------------------------------------------------------------------------
+# tagged slots (tuning flag bit 3): each block's partial travels through an
+# 80-bit mantissa with its exponent and the reduction's tags
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(8))
+def test_tagged_slots_keep_the_sum_correctly_rounded(harness, seed):
+    rng = np.random.default_rng(100 + seed)
+    groups = []
+    for _ in range(int(rng.integers(1, 300))):       # up to a few hundred blocks
+        n = int(rng.integers(1, 64))
+        scale = 10.0 ** rng.uniform(-6, 6, size=n)
+        groups.append(list(rng.standard_normal(n) * scale))
+    red = int(rng.integers(2, 1 << 22))
+    got = run(harness, groups, red=red)
+    assert ulp_diff(got, exact(groups)) <= 1, (got, exact(groups))
+
+
+@pytest.mark.parametrize("red", [2, 3, 255, 256, 257, (1 << 23) - 1, 1 << 23, (1 << 23) + 5])
+def test_tagged_slots_reject_stale_torn_and_empty_words(harness, red):
+    # the harness exits non-zero if a current slot fails its check or a torn / stale / zero one passes;
+    # values straddle the 56-bit split of the mantissa and both signs
+    groups = [[1.0, -3.5e-7], [-2.0 ** 60, 5.0], [1e-300], [-7.25e12, 1.0 / 3.0]]
+    got = run(harness, groups, red=red)
+    assert ulp_diff(got, exact(groups)) <= 1
+
+
+def test_tagged_slots_cancel_and_propagate_non_finite(harness):
+    assert run(harness, [[1e16, 1.0, -1e16], [3.0, -3.0]], red=7) == 1.0
+    assert run(harness, [[0.0], [-0.0]], red=9) == 0.0
+    assert math.isnan(run(harness, [[1.0], [float("inf")]], red=11))
