@@ -879,6 +879,24 @@ def profile_case(case):
             info = cgp.cgp_poisson_solve(m.handle, b, x, tol=TOL, precision=prec)
         print(json.dumps({"case": case, "info": info, "launch": cgp.cgp_last_launch(m.handle, prec)}))
         m.close()
+    elif case == "gnn":
+        # the learned guess at the 64x32 size: 3 fused inferences, then 3 training steps of batch 16
+        from paper_2003_00082_gb300 import learned_guess
+        xy, tri = inputs.ogrid(64, 32)
+        m = cgp.Mesh(xy, tri)
+        net = cgp.GNN(m, 16, learned_guess.initial_params(0))
+        g = torch.Generator(device="cpu").manual_seed(SEED)
+        b, p1, p2, pt = (torch.randn((16, m.n_c), generator=g, dtype=torch.float64).to(dev) for _ in range(4))
+        x0 = torch.empty(m.n_c, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            net.predict(b[0], p1[0], p2[0], x0)
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        for _ in range(3):
+            net.train_step(16, b, p1, p2, pt, lr=1e-3, loss_dev=loss)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": case, "n": m.n_c, "loss": float(loss.item())}))
+        net.close()
+        m.close()
     elif case == "batched":
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
         out = run_batched(cgp, inputs, configs, torch, dev, flush, read_peaks()[0], reps=1)
@@ -900,7 +918,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true", help="skip the other-precision and batched passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--profile-case", choices=["fp64", "mixed", "batched", "spmv"], default=None,
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "batched", "spmv", "gnn"], default=None,
                     help="run one small case for a profiler and exit: two 512x256 potential solves, "
                          "one batched launch of the 64-instance workload, or the SpMV sweep")
     args = ap.parse_args()

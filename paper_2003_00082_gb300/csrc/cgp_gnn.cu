@@ -718,7 +718,17 @@ __global__ void decode_bwd_kernel(int rows, const float* __restrict__ P, const f
   dh[t] = dout[t / H] * P[OFF_WD + t % H];
 }
 
+// Blocks of the grid-stride backward kernels: enough to fill the GPU (a few
+// per SM at 32 KB of shared memory each), no more, so each block expands its
+// weight matrix once for many rows.
+inline unsigned bwd_grid(size_t outputs) {
+  const size_t need = (outputs + 255) / 256;
+  return (unsigned)(need < 1024 ? (need > 0 ? need : 1) : 1024);
+}
+
 // du = dh * [u > 0];  [dh_prev | da] = du Wu (Wu as its BF16 values); dh_prev += dh.
+// Grid-stride over the (row, output) pairs: a block expands Wu to FP32 in
+// shared memory once and reuses it for all the rows it visits.
 __global__ void update_bwd_kernel(int rows, const float* __restrict__ dh, const float* __restrict__ u,
                                   const bf16* __restrict__ Wb, float* __restrict__ du, float* __restrict__ dh_prev,
                                   float* __restrict__ da) {
@@ -726,25 +736,27 @@ __global__ void update_bwd_kernel(int rows, const float* __restrict__ dh, const 
   float* Wf = reinterpret_cast<float*>(smem);          // [H][KU]
   for (int i = threadIdx.x; i < H * KU; i += blockDim.x) Wf[i] = __bfloat162float(Wb[i]);
   __syncthreads();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = t / KU, k = t % KU;
-  if (r >= rows) return;
-  float s = 0.0f;
-  const float* dhr = dh + (size_t)r * H;
-  const float* ur = u + (size_t)r * H;
-  for (int o = 0; o < H; ++o) {
-    const float g = ur[o] > 0.0f ? dhr[o] : 0.0f;
-    s = fmaf(g, Wf[o * KU + k], s);
-  }
-  if (k < H) {
-    dh_prev[(size_t)r * H + k] = dhr[k] + s;
-    du[(size_t)r * H + k] = ur[k] > 0.0f ? dhr[k] : 0.0f;
-  } else {
-    da[(size_t)r * H + (k - H)] = s;
+  const size_t total = (size_t)rows * KU;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / KU), k = (int)(t % KU);
+    float s = 0.0f;
+    const float* dhr = dh + (size_t)r * H;
+    const float* ur = u + (size_t)r * H;
+    for (int o = 0; o < H; ++o) {
+      const float g = ur[o] > 0.0f ? dhr[o] : 0.0f;
+      s = fmaf(g, Wf[o * KU + k], s);
+    }
+    if (k < H) {
+      dh_prev[(size_t)r * H + k] = dhr[k] + s;
+      du[(size_t)r * H + k] = ur[k] > 0.0f ? dhr[k] : 0.0f;
+    } else {
+      da[(size_t)r * H + (k - H)] = s;
+    }
   }
 }
 
 // dz_e = da[dst] * [m_e > 0];  dx_e = dz_e Wm (first 2H inputs) for the node gathers.
+// Grid-stride over the (edge row, output) pairs, Wm expanded once per block.
 __global__ void message_bwd_kernel(int n, int E, int rows, const int* __restrict__ dst, const float* __restrict__ da,
                                    const bf16* __restrict__ m, const bf16* __restrict__ Wb, float* __restrict__ dz,
                                    float* __restrict__ dxe) {
@@ -752,19 +764,20 @@ __global__ void message_bwd_kernel(int n, int E, int rows, const int* __restrict
   float* Wf = reinterpret_cast<float*>(smem);          // [H][2H] (the h_i, h_j inputs)
   for (int i = threadIdx.x; i < H * KU; i += blockDim.x) Wf[i] = __bfloat162float(Wb[(i / KU) * KMP + i % KU]);
   __syncthreads();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = t / KU, k = t % KU;
-  if (r >= rows) return;
-  const int s = r / E, e = r % E;
-  const float* dar = da + ((size_t)s * n + dst[e]) * H;
-  const bf16* mr = m + (size_t)r * H;
-  float acc = 0.0f;
-  for (int o = 0; o < H; ++o) {
-    const float g = __bfloat162float(mr[o]) > 0.0f ? dar[o] : 0.0f;
-    acc = fmaf(g, Wf[o * KU + k], acc);
+  const size_t total = (size_t)rows * KU;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / KU), k = (int)(t % KU);
+    const int s = r / E, e = r % E;
+    const float* dar = da + ((size_t)s * n + dst[e]) * H;
+    const bf16* mr = m + (size_t)r * H;
+    float acc = 0.0f;
+    for (int o = 0; o < H; ++o) {
+      const float g = __bfloat162float(mr[o]) > 0.0f ? dar[o] : 0.0f;
+      acc = fmaf(g, Wf[o * KU + k], acc);
+    }
+    dxe[(size_t)r * KU + k] = acc;
+    if (k < H) dz[(size_t)r * H + k] = __bfloat162float(mr[k]) > 0.0f ? dar[k] : 0.0f;
   }
-  dxe[(size_t)r * KU + k] = acc;
-  if (k < H) dz[(size_t)r * H + k] = __bfloat162float(mr[k]) > 0.0f ? dar[k] : 0.0f;
 }
 
 // dh_prev[i] += sum over in-edges of dx_e[:, 0:H] + sum over out-edges of dx_e[:, H:2H]
@@ -982,7 +995,7 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
     const float* ul = g->u + (size_t)l * rn * H;
     const int off = layer_off(l);
     // node update
-    update_bwd_kernel<<<(rn * KU + 255) / 256, 256, (size_t)H * KU * sizeof(float), s>>>(
+    update_bwd_kernel<<<bwd_grid((size_t)rn * KU), 256, (size_t)H * KU * sizeof(float), s>>>(
         rn, dh, ul, g->Wu + (size_t)l * H * KU, g->du, dh_prev, g->da);
     {
       const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
@@ -992,7 +1005,7 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
                                                                     off + L_BU);
     }
     // messages
-    message_bwd_kernel<<<(re * KU + 255) / 256, 256, (size_t)H * KU * sizeof(float), s>>>(
+    message_bwd_kernel<<<bwd_grid((size_t)re * KU), 256, (size_t)H * KU * sizeof(float), s>>>(
         n, E, re, g->dst, g->da, ml, g->Wm + (size_t)l * H * KMP, g->dz, g->dxe);
     {
       const int chunks = (re + WG_ROWS - 1) / WG_ROWS;
