@@ -721,62 +721,77 @@ __global__ void decode_bwd_kernel(int rows, const float* __restrict__ P, const f
 // Blocks of the grid-stride backward kernels: enough to fill the GPU (a few
 // per SM at 32 KB of shared memory each), no more, so each block expands its
 // weight matrix once for many rows.
-inline unsigned bwd_grid(size_t outputs) {
-  const size_t need = (outputs + 255) / 256;
+inline unsigned bwd_grid(size_t threads) {
+  const size_t need = (threads + 255) / 256;
   return (unsigned)(need < 1024 ? (need > 0 ? need : 1) : 1024);
 }
 
 // du = dh * [u > 0];  [dh_prev | da] = du Wu (Wu as its BF16 values); dh_prev += dh.
-// Grid-stride over the (row, output) pairs: a block expands Wu to FP32 in
-// shared memory once and reuses it for all the rows it visits.
+// One warp per row (grid-stride): lane l forms outputs l, l + 32, l + 64,
+// l + 96, so each masked gradient is read once per warp, not once per
+// output; every output still sums o = 0 .. H-1 in order.  A block expands Wu
+// to FP32 in shared memory once for all the rows it visits.
 __global__ void update_bwd_kernel(int rows, const float* __restrict__ dh, const float* __restrict__ u,
                                   const bf16* __restrict__ Wb, float* __restrict__ du, float* __restrict__ dh_prev,
                                   float* __restrict__ da) {
+  static_assert(KU == 4 * 32 && H == 2 * 32, "one warp per row, four outputs per lane");
   extern __shared__ __align__(16) unsigned char smem[];
   float* Wf = reinterpret_cast<float*>(smem);          // [H][KU]
   for (int i = threadIdx.x; i < H * KU; i += blockDim.x) Wf[i] = __bfloat162float(Wb[i]);
   __syncthreads();
-  const size_t total = (size_t)rows * KU;
+  const int lane = threadIdx.x & 31;
+  const size_t total = (size_t)rows * 32;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / KU), k = (int)(t % KU);
-    float s = 0.0f;
+    const int r = (int)(t / 32);
     const float* dhr = dh + (size_t)r * H;
     const float* ur = u + (size_t)r * H;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int o = 0; o < H; ++o) {
       const float g = ur[o] > 0.0f ? dhr[o] : 0.0f;
-      s = fmaf(g, Wf[o * KU + k], s);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(g, Wf[o * KU + lane + 32 * q], acc[q]);
     }
-    if (k < H) {
-      dh_prev[(size_t)r * H + k] = dhr[k] + s;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int k = lane + 32 * q;
+      dh_prev[(size_t)r * H + k] = dhr[k] + acc[q];
       du[(size_t)r * H + k] = ur[k] > 0.0f ? dhr[k] : 0.0f;
-    } else {
-      da[(size_t)r * H + (k - H)] = s;
+      da[(size_t)r * H + k] = acc[q + 2];
     }
   }
 }
 
 // dz_e = da[dst] * [m_e > 0];  dx_e = dz_e Wm (first 2H inputs) for the node gathers.
-// Grid-stride over the (edge row, output) pairs, Wm expanded once per block.
+// One warp per edge row (grid-stride), four outputs per lane as in
+// update_bwd_kernel; Wm expanded once per block.
 __global__ void message_bwd_kernel(int n, int E, int rows, const int* __restrict__ dst, const float* __restrict__ da,
                                    const bf16* __restrict__ m, const bf16* __restrict__ Wb, float* __restrict__ dz,
                                    float* __restrict__ dxe) {
+  static_assert(KU == 4 * 32 && H == 2 * 32, "one warp per row, four outputs per lane");
   extern __shared__ __align__(16) unsigned char smem[];
   float* Wf = reinterpret_cast<float*>(smem);          // [H][2H] (the h_i, h_j inputs)
   for (int i = threadIdx.x; i < H * KU; i += blockDim.x) Wf[i] = __bfloat162float(Wb[(i / KU) * KMP + i % KU]);
   __syncthreads();
-  const size_t total = (size_t)rows * KU;
+  const int lane = threadIdx.x & 31;
+  const size_t total = (size_t)rows * 32;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / KU), k = (int)(t % KU);
+    const int r = (int)(t / 32);
     const int s = r / E, e = r % E;
     const float* dar = da + ((size_t)s * n + dst[e]) * H;
     const bf16* mr = m + (size_t)r * H;
-    float acc = 0.0f;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int o = 0; o < H; ++o) {
       const float g = __bfloat162float(mr[o]) > 0.0f ? dar[o] : 0.0f;
-      acc = fmaf(g, Wf[o * KU + k], acc);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(g, Wf[o * KU + lane + 32 * q], acc[q]);
     }
-    dxe[(size_t)r * KU + k] = acc;
-    if (k < H) dz[(size_t)r * H + k] = __bfloat162float(mr[k]) > 0.0f ? dar[k] : 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dxe[(size_t)r * KU + lane + 32 * q] = acc[q];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int k = lane + 32 * q;
+      dz[(size_t)r * H + k] = __bfloat162float(mr[k]) > 0.0f ? dar[k] : 0.0f;
+    }
   }
 }
 
@@ -804,28 +819,64 @@ __global__ void encode_bwd_kernel(int rows, const float* __restrict__ dh, const 
 // Weight gradient partials: for a chunk of ROWS rows, G[o][k] = sum_r D[r][o] X[r][k]
 // and G[o][K] = sum_r D[r][o] (the bias); X rows come from `load_x`.
 constexpr int WG_ROWS = 128;
+// shared-memory row stride of the inputs of a weight-gradient chunk (KX
+// inputs and the bias column, padded to 16-byte rows) and the chunk's bytes
+__host__ __device__ constexpr int wg_xs(int KX) { return (KX + 1 + 3) / 4 * 4; }
+constexpr size_t wg_smem(int KX, int NO) { return (size_t)WG_ROWS * (NO + wg_xs(KX)) * sizeof(float); }
 
 template <int KX, int NO, typename LoadX>
 __device__ void wgrad_chunk(int rows, const float* __restrict__ D, LoadX load_x, float* __restrict__ part) {
+  constexpr int XS = wg_xs(KX);
   extern __shared__ __align__(16) unsigned char smem[];
   float* Ds = reinterpret_cast<float*>(smem);          // [WG_ROWS][NO]
-  float* Xs = Ds + WG_ROWS * NO;                       // [WG_ROWS][KX + 1]
+  float* Xs = Ds + WG_ROWS * NO;                       // [WG_ROWS][XS]: KX inputs, the bias 1, zero padding
   const int r0 = blockIdx.x * WG_ROWS;
   for (int i = threadIdx.x; i < WG_ROWS * NO; i += blockDim.x) {
     const int rr = i / NO, o = i % NO, r = r0 + rr;
     Ds[i] = r < rows ? D[(size_t)r * NO + o] : 0.0f;
   }
-  for (int i = threadIdx.x; i < WG_ROWS * (KX + 1); i += blockDim.x) {
-    const int rr = i / (KX + 1), k = i % (KX + 1), r = r0 + rr;
-    Xs[i] = (r < rows) ? (k < KX ? load_x(r, k) : 1.0f) : 0.0f;
+  for (int i = threadIdx.x; i < WG_ROWS * XS; i += blockDim.x) {
+    const int rr = i / XS, k = i % XS, r = r0 + rr;
+    Xs[i] = (r < rows) ? (k < KX ? load_x(r, k) : (k == KX ? 1.0f : 0.0f)) : 0.0f;
   }
   __syncthreads();
   float* out = part + (size_t)blockIdx.x * NO * (KX + 1);
-  for (int j = threadIdx.x; j < NO * (KX + 1); j += blockDim.x) {
-    const int o = j / (KX + 1), k = j % (KX + 1);
-    float s = 0.0f;
-    for (int rr = 0; rr < WG_ROWS; ++rr) s = fmaf(Ds[rr * NO + o], Xs[rr * (KX + 1) + k], s);
-    out[j] = s;
+  if constexpr (NO % 4 == 0) {
+    // 4 x 4 tiles of (o, k) per thread: two 16-byte shared loads feed 16 FMAs.
+    // Each output still sums rr = 0 .. WG_ROWS-1 in order, as one output per
+    // thread would.
+    constexpr int NTK = XS / 4;
+    for (int tile = threadIdx.x; tile < (NO / 4) * NTK; tile += blockDim.x) {
+      const int to = tile / NTK, tk = tile % NTK;
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+      for (int rr = 0; rr < WG_ROWS; ++rr) {
+        const float4 dv = *reinterpret_cast<const float4*>(Ds + rr * NO + 4 * to);
+        const float4 xv = *reinterpret_cast<const float4*>(Xs + rr * XS + 4 * tk);
+        const float dd[4] = {dv.x, dv.y, dv.z, dv.w}, xx[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(dd[a], xx[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int k = 4 * tk + b;
+          if (k <= KX) out[(4 * to + a) * (KX + 1) + k] = acc[a][b];
+        }
+    }
+  } else {
+    for (int j = threadIdx.x; j < NO * (KX + 1); j += blockDim.x) {
+      const int o = j / (KX + 1), k = j % (KX + 1);
+      float s = 0.0f;
+      for (int rr = 0; rr < WG_ROWS; ++rr) s = fmaf(Ds[rr * NO + o], Xs[rr * XS + k], s);
+      out[j] = s;
+    }
   }
 }
 
@@ -981,7 +1032,7 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
   // decoder
   {
     const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
-    const size_t sm = (size_t)WG_ROWS * (1 + H + 1) * sizeof(float);
+    const size_t sm = wg_smem(H, 1);
     wgrad_decode_kernel<<<chunks, 256, sm, s>>>(rn, g->h + (size_t)NL * rn * H, g->dout, g->part);
     wgrad_reduce_kernel<<<1, 128, 0, s>>>(chunks, 1, H, g->part, g->G, OFF_WD, OFF_BD);
     decode_bwd_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, g->P, g->dout, g->dh);
@@ -995,21 +1046,21 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
     const float* ul = g->u + (size_t)l * rn * H;
     const int off = layer_off(l);
     // node update
-    update_bwd_kernel<<<bwd_grid((size_t)rn * KU), 256, (size_t)H * KU * sizeof(float), s>>>(
+    update_bwd_kernel<<<bwd_grid((size_t)rn * 32), 256, (size_t)H * KU * sizeof(float), s>>>(
         rn, dh, ul, g->Wu + (size_t)l * H * KU, g->du, dh_prev, g->da);
     {
       const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
-      const size_t sm = (size_t)WG_ROWS * (H + KU + 1) * sizeof(float);
+      const size_t sm = wg_smem(KU, H);
       wgrad_update_kernel<<<chunks, 256, sm, s>>>(rn, hl, al_, g->du, g->part);
       wgrad_reduce_kernel<<<(H * (KU + 1) + 255) / 256, 256, 0, s>>>(chunks, H, KU, g->part, g->G, off + L_WU,
                                                                     off + L_BU);
     }
     // messages
-    message_bwd_kernel<<<bwd_grid((size_t)re * KU), 256, (size_t)H * KU * sizeof(float), s>>>(
+    message_bwd_kernel<<<bwd_grid((size_t)re * 32), 256, (size_t)H * KU * sizeof(float), s>>>(
         n, E, re, g->dst, g->da, ml, g->Wm + (size_t)l * H * KMP, g->dz, g->dxe);
     {
       const int chunks = (re + WG_ROWS - 1) / WG_ROWS;
-      const size_t sm = (size_t)WG_ROWS * (H + KM + 1) * sizeof(float);
+      const size_t sm = wg_smem(KM, H);
       wgrad_message_kernel<<<chunks, 256, sm, s>>>(n, E, re, g->dst, g->src, g->ef, hl, g->dz, g->part);
       wgrad_reduce_kernel<<<(H * (KM + 1) + 255) / 256, 256, 0, s>>>(chunks, H, KM, g->part, g->G, off + L_WM,
                                                                     off + L_BM);
@@ -1022,7 +1073,7 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
   encode_bwd_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, dh, g->z0, g->du);
   {
     const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
-    const size_t sm = (size_t)WG_ROWS * (H + FIN + 1) * sizeof(float);
+    const size_t sm = wg_smem(FIN, H);
     wgrad_encode_kernel<<<chunks, 256, sm, s>>>(rn, g->f, g->du, g->part);
     wgrad_reduce_kernel<<<(H * (FIN + 1) + 255) / 256, 256, 0, s>>>(chunks, H, FIN, g->part, g->G, OFF_WE, OFF_BE);
   }
@@ -1152,8 +1203,8 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   st = refresh(g, 0);
   if (st == CGP_OK) st = smem_optin((const void*)message_fwd_kernel, (size_t)(H + TILE) * LDM * sizeof(bf16));
   if (st == CGP_OK) st = smem_optin((const void*)update_fwd_kernel, (size_t)(H + TILE) * LDU * sizeof(bf16));
-  if (st == CGP_OK) st = smem_optin((const void*)wgrad_message_kernel, (size_t)WG_ROWS * (H + KM + 1) * sizeof(float));
-  if (st == CGP_OK) st = smem_optin((const void*)wgrad_update_kernel, (size_t)WG_ROWS * (H + KU + 1) * sizeof(float));
+  if (st == CGP_OK) st = smem_optin((const void*)wgrad_message_kernel, wg_smem(KM, H));
+  if (st == CGP_OK) st = smem_optin((const void*)wgrad_update_kernel, wg_smem(KU, H));
   if (st == CGP_OK) st = smem_optin((const void*)update_bwd_kernel, (size_t)H * KU * sizeof(float));
   if (st == CGP_OK) st = smem_optin((const void*)message_bwd_kernel, (size_t)H * KU * sizeof(float));
   if (st == CGP_OK) st = smem_optin((const void*)infer_kernel, kInferSmem);
