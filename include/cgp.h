@@ -222,8 +222,11 @@ int cgp_poisson_solve_async(cgp_mesh m, const double* b, double* x, const cgp_so
  *
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU
- * race on it, so serialise them (one stream, one host thread at a time).
+ * capture.  The address is kept together with the identity of the device's
+ * CUDA context, so the first call after the caller resets the device
+ * (cudaDeviceReset) looks it up again.  All calls share the one array:
+ * calls that overlap on the GPU race on it, so serialise them (one stream,
+ * one host thread at a time).
  * info behaves as in cgp_poisson_solve (NULL: asynchronous).
  */
 #define CGP_STATIC_MAX_ROWS 65536
@@ -267,7 +270,8 @@ int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* col, const do
  *                     first non-OK status among the systems.
  * cgp_batch_set_tuning  re-plans with threads per block, lanes per CSR row,
  *                     blocks per SM (0 = as many as fit; waves: 0 or 1 =
- *                     one block per SM) and flags (bit 0: rows in global
+ *                     one block per SM, never more than blocks of that size
+ *                     fit on an SM) and flags (bit 0: rows in global
  *                     memory; bit 1: FP64 textbook iteration, as for
  *                     cgp_set_tuning; bit 2: one packed launch, not waves;
  *                     bit 3: tagged reductions, as for cgp_set_tuning).

@@ -191,6 +191,68 @@ def loss_and_grad(p, g: Graph, samples, bf16_storage=True):
     return total / count, grads
 
 
+def magnitudes(p, g: Graph, samples, bf16_storage=True):
+    """Size of the terms behind every output and gradient element, for elementwise bounds.
+
+    The same forward and backward passes as ``forward`` and
+    ``loss_and_grad`` with every weight, input and intermediate replaced by
+    its absolute value, so each returned element is the sum of the absolute
+    values of all the products that make up the corresponding element of the
+    network (relu(a) - relu(b) is bounded by a - b, so activations carry the
+    magnitude of their argument).  A relative perturbation eps of every
+    stored value changes an output or gradient element by at most about
+    eps times its magnitude.  The backward keeps the relu masks of the
+    rounded forward.  Returns (list of [n] output magnitudes, dict of
+    gradient magnitudes).
+    """
+    mags = {k: np.zeros_like(v) for k, v in p.items()}
+    outs = []
+    count = sum(s[0].shape[0] for s in samples)
+    A = {k: np.abs(v) for k, v in p.items()}
+    rd = bf16 if bf16_storage else (lambda v: np.asarray(v, dtype=np.float64))
+    for f, t in samples:
+        _, c = forward(p, g, f, bf16_storage)
+        e = np.abs(c["e"])
+        Mh = np.abs(f) @ A["We"].T + A["be"]
+        Mhs = [Mh]
+        ML = []
+        for l in range(N_LAYERS):
+            Wm, Wu = np.abs(rd(p[f"Wm{l}"])), np.abs(rd(p[f"Wu{l}"]))
+            Mxe = np.concatenate([Mh[g.dst], Mh[g.src], e], axis=1)
+            Mm = Mxe @ Wm.T + A[f"bm{l}"]
+            Ma = np.zeros((g.n, H))
+            np.add.at(Ma, g.dst, Mm)
+            Mxn = np.concatenate([Mh, Ma], axis=1)
+            Mu = Mxn @ Wu.T + A[f"bu{l}"]
+            ML.append(dict(Mxe=Mxe, Mxn=Mxn, Wm=Wm, Wu=Wu))
+            Mh = Mh + Mu
+            Mhs.append(Mh)
+        Mout = Mh @ A["Wd"][0] + A["bd"][0]
+        outs.append(Mout)
+        Mdout = 2.0 * (Mout + np.abs(t)) / count
+        mags["Wd"][0] += Mdout @ Mh
+        mags["bd"][0] += np.sum(Mdout)
+        Mdh = np.outer(Mdout, A["Wd"][0])
+        for l in reversed(range(N_LAYERS)):
+            L, M = c[f"L{l}"], ML[l]
+            Mdu = Mdh * (L["u"] > 0)
+            mags[f"Wu{l}"] += Mdu.T @ M["Mxn"]
+            mags[f"bu{l}"] += Mdu.sum(axis=0)
+            Mdxn = Mdu @ M["Wu"]
+            Mdh_prev = Mdh + Mdxn[:, :H]
+            Mdz = Mdxn[:, H:][g.dst] * (L["z"] > 0)
+            mags[f"Wm{l}"] += Mdz.T @ M["Mxe"]
+            mags[f"bm{l}"] += Mdz.sum(axis=0)
+            Mdxe = Mdz @ M["Wm"]
+            np.add.at(Mdh_prev, g.dst, Mdxe[:, :H])
+            np.add.at(Mdh_prev, g.src, Mdxe[:, H:2 * H])
+            Mdh = Mdh_prev
+        Mdz0 = Mdh * (c["z0"] > 0)
+        mags["We"] += Mdz0.T @ np.abs(c["f"])
+        mags["be"] += Mdz0.sum(axis=0)
+    return outs, mags
+
+
 class Adam:
     def __init__(self, p, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps

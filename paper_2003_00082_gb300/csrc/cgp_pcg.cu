@@ -2392,7 +2392,14 @@ int batch_plan_waves(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts&
   if (!fn0 || block < 64 || block > MAX_BLOCK || block % 32 != 0 || block % lanes != 0)
     return fail(CGP_ERR_INVALID_ARG, "batch tuning: bad block or lanes");
   const int sms = std::max(1, dev_info(B->device).sms);
-  const int cap = sms * std::max(1, sh.per_sm);
+  // blocks of this size that fit on one SM with rows in global memory: a wave
+  // never asks for more than that, whatever blocks_per_sm requests
+  int fit = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, (const void*)fn0, block, 0) != cudaSuccess || fit < 1) {
+    cudaGetLastError();
+    return fail(CGP_ERR_CUDA, "batch: occupancy query failed");
+  }
+  const int cap = sms * std::min(std::max(1, sh.per_sm), fit);
   const int count = B->count;
   const SolverKind kind = solver_kind(mixed, sh.flags);
   std::vector<int> nb(count), order(count);
@@ -2914,6 +2921,11 @@ extern "C" int cgp_autotune(cgp_mesh m, int precision, const double* b, double* 
           for (int rep = 0; rep < 2; ++rep) {
             if (cudaEventRecord(e0, s) != cudaSuccess || launch_solve(m, b, x, o, nullptr, s) != CGP_OK ||
                 cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+              break;
+            // only a candidate that converged counts
+            SolveResult r{};
+            if (cudaMemcpy(&r, m->res, sizeof(SolveResult), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                r.timeout || r.status != CGP_OK)
               break;
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);

@@ -14,6 +14,8 @@
 // point clears the barrier counter and the result record before each
 // launch; two calls that overlap on the GPU (on different streams, or from
 // different host threads) race on it and must be serialised by the caller.
+#include <cuda.h>
+
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -42,20 +44,63 @@ static_assert(sizeof(cgp::SolveResult) <= 256, "result record must fit its slot"
 static __device__ __align__(256) unsigned char g_cgp_static_scratch[kStaticBytes];
 
 std::mutex g_mu;
-void* g_addr[256] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side name of the array is not a device address).
+// The array's device address belongs to the CUDA context it was looked up
+// in.  Each device's entry keeps the identity of that context (cuCtxGetId,
+// unique for the life of the process), so after the caller resets the
+// device (cudaDeviceReset, or a reset of the primary context) the next call
+// looks the address up again instead of using a stale one.
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;   // 0: no valid entry
+  void* addr = nullptr;
+};
+ScratchAddr g_addr[256];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Identity of the context current on this thread, or 0 when none is current
+// or the driver cannot tell (then every call looks the address up again).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {   // called with g_mu held
+    resolved = true;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void**>(&get_current), 12000,
+                                         cudaEnableDefault, &q1) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess)
+      get_current = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void**>(&get_id), 12000,
+                                         cudaEnableDefault, &q2) != cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess)
+      get_id = nullptr;
+    cudaGetLastError();
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current device's context (the
+// host-side name of the array is not a device address).  Looked up once per
+// device and context, with that device current.
 int scratch_address(int device, unsigned char** out) {
   if (device < 0 || device >= 256) return cgp::fail(CGP_ERR_INVALID_ARG, "cgp_poisson_solve_noalloc: device id");
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[device]) {
+  ScratchAddr& a = g_addr[device];
+  const unsigned long long id = current_context_id();
+  if (id == 0 || a.ctx_id != id || !a.addr) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_cgp_static_scratch);
     if (e != cudaSuccess) return cgp::cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
-    g_addr[device] = p;
+    a.addr = p;
+    a.ctx_id = current_context_id();   // the lookup has made the device's context current
   }
-  *out = static_cast<unsigned char*>(g_addr[device]);
+  *out = static_cast<unsigned char*>(a.addr);
   return CGP_OK;
 }
 

@@ -1,5 +1,5 @@
-"""The benchmark's reference arm (the CPU oracle timed on the benchmark workload) runs without a GPU
-and prints the one-line JSON contract."""
+"""The benchmark's reference arm (the CPU oracle timed on the benchmark workload, one process per
+core) runs without a GPU and prints the one-line JSON contract."""
 import json
 import os
 import subprocess
@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_reference_arm_prints_the_contract_line():
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+                        "--warmup", "0", "--ref-procs", "2"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
     assert len(lines) == 1, r.stdout
@@ -22,6 +22,7 @@ def test_reference_arm_prints_the_contract_line():
     assert d["value"] > 0 and d["steps"] == 1 and d["higher_is_better"] is True
     assert d["dtype"] == "f64" and d["data"] == "synthetic" and d["gpu_launches"] == 0
     assert d["config"]["workload"] and d["config"]["coarse_nodes"] == 131584
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
+    assert abs(d["ms_per_step"] - 2e3 / d["value"]) <= 1e-9 * d["ms_per_step"]   # one two-solve step
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -130,3 +130,30 @@ def test_adam_first_step_is_lr_times_sign():
     opt = G.Adam(p, lr=1e-3)
     opt.step(p, {"w": np.array([0.5, -4.0, 0.0])})
     np.testing.assert_allclose(p["w"], [1.0 - 1e-3, -2.0 + 1e-3, 3.0], atol=1e-9)
+
+
+def test_magnitudes_bound_every_output_and_gradient_element(tiny):
+    """The magnitude pass is the absolute-value network: never below the value it sizes, and equal to
+    it when no term can cancel (non-negative weights, inputs and edge features, targets <= 0, no BF16
+    rounding: every ReLU is the identity and every product is non-negative)."""
+    om, g, samples = tiny
+    p = G.init_params(6, zero_decoder=False)
+    outs, mags = G.magnitudes(p, g, samples)
+    _, grads = G.loss_and_grad(p, g, samples)
+    for (f, _), m in zip(samples, outs):
+        out, _ = G.forward(p, g, f)
+        assert np.all(np.abs(out) <= m * (1 + 1e-12))
+    for k in grads:
+        assert np.all(np.abs(grads[k]) <= mags[k] * (1 + 1e-12) + 1e-300), k
+    pos = {k: np.abs(v) + 0.01 for k, v in p.items()}
+    gp = G.Graph(om.K, om.xy_c)
+    gp.efeat = np.abs(gp.efeat)
+    rng = np.random.default_rng(9)
+    psamples = [(np.abs(f), -np.abs(rng.standard_normal(om.n_c))) for f, _ in samples]
+    outs, mags = G.magnitudes(pos, gp, psamples, bf16_storage=False)
+    _, grads = G.loss_and_grad(pos, gp, psamples, bf16_storage=False)
+    for (f, _), m in zip(psamples, outs):
+        out, _ = G.forward(pos, gp, f, bf16_storage=False)
+        np.testing.assert_allclose(out, m, rtol=1e-12)
+    for k in grads:
+        np.testing.assert_allclose(np.abs(grads[k]), mags[k], rtol=1e-11, err_msg=k)

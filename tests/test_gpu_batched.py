@@ -27,7 +27,9 @@ def rel(a, r):
     return float(np.linalg.norm(np.asarray(a) - r) / np.linalg.norm(r))
 
 
-SIZES = [(8, 4), (16, 8), (33, 17), (64, 32), (128, 64), (7, 3), (96, 48)]
+# uneven sizes up to the two largest of the 64-instance workload (256x128 and 512x256: in the
+# wave schedule a 512x256 system gets the whole GPU, in the packed one a share of a single launch)
+SIZES = [(8, 4), (16, 8), (33, 17), (64, 32), (128, 64), (7, 3), (96, 48), (256, 128), (512, 256)]
 
 
 @pytest.fixture(scope="module")
@@ -42,7 +44,7 @@ def systems(cgp):
         B = (np.cos(ang), np.sin(ang), 1.0)
         Fx, Fy = O.source_field(O.POTENTIAL, om.restrict(u), om.restrict(v), B)
         b = O.rhs(om.Gx, om.Gy, Fx, Fy)
-        exact = O.pcg(om.K, om.d, b, tol=1e-14)["x"]
+        exact = O.pcg(om.K, om.d, b, tol=1e-13, max_it=8000)["x"]   # far below the tests' 1e-7
         out.append(dict(mesh=m, om=om, b=b, exact=exact))
     yield out
     for s in out:
@@ -60,9 +62,10 @@ def test_batched_instances_match_the_oracle(cgp, systems, precision, packed):
     q = batch.query()
     if packed:
         assert q["grid"] == sum(q["blocks"])
-    else:        # waves: each system gets what it would get alone (about 256 rows a block)
+    else:        # waves: each system gets what it would get alone (about 256 rows a block, one SM's worth at most)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
         assert q["grid"] <= sum(q["blocks"])
-        assert q["blocks"] == [max(1, (s["mesh"].n_c + 255) // 256) for s in systems]
+        assert q["blocks"] == [min(sms, max(1, (s["mesh"].n_c + 255) // 256)) for s in systems]
     assert min(q["blocks"]) >= 1
     batch.solve()
     infos, secs = batch.info()

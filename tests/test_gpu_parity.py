@@ -320,42 +320,168 @@ def test_potential_step_64x32_meets_the_gates(cgp):
     m.close()
 
 
+# ----------------------------------------------------------------------------
+# the full-size workload in the launch shapes the benchmark times
+# ----------------------------------------------------------------------------
+# Bounds at full size (512x256, 131,584 coarse rows), from the oracle's own
+# accuracy on this system (potential / pressure, step 7 of the vortex train):
+# its solution at tol 1e-8 lies within 0.10 / 0.17 tol max|phi| of the
+# converged one in every node, its gradient within 0.36 / 2.1 tol max|grad phi|
+# in every fine triangle (the force error is the gradient error times
+# sigma |B|^2).  A GPU solve stopped by the same rule at the same tolerance
+# has an error of the same size, so two such solves differ by at most about
+# twice that: the elementwise bounds below allow 2 tol max|phi| in phi and
+# 10 tol max|grad phi| in the gradient and the force, with tol raised to a
+# reference's own true residual where that is larger.
+C2_TOLS = (1e-8, 2e-9, 1e-12)
+
+
+def c2_references(om, u, v, B, kind, x0=None):
+    refs = {}
+    for tol in C2_TOLS:
+        refs[tol] = om.solve(u, v, kind, B=B, sigma=1.0, rho_over_dt=20.0, tol=tol, x0=x0)
+    fine = refs[1e-12]
+    conv = O.pcg(om.K, om.d, fine["b"], x0=fine["phi_c"], tol=1e-13, max_it=3000)
+    phi_f = om.prolong(conv["x"])
+    grad, force = O.lorentz(om.xy_f, om.tri_f, phi_f, u, v, B, 1.0)
+    refs["converged"] = dict(phi_c=conv["x"], phi_f=phi_f, grad=grad, force=force if kind == 0 else None,
+                             rel_res_true=conv["rel_res_true"])
+    return refs
+
+
 @pytest.fixture(scope="module")
 def c2_case(cgp):
-    """512x256 O-grid (525,312 fine nodes), vortex-train velocity, B = k, N = 1, tol 1e-8."""
+    """512x256 O-grid (525,312 fine nodes), vortex-train velocity (seed 1) at step 7, B = k, N = 1.
+
+    Oracle references for the potential and the pressure solve from x0 = 0 at
+    tol 1e-8 (the benchmark's), 2e-9 and 1e-12, a converged solution, and the
+    potential solve of step 7 warm-started from the oracle's step-6 solution
+    (the benchmark starts every solve from the previous step's)."""
     xy, tri = inputs.ogrid(512, 256)
     m = cgp.Mesh(xy, tri)
     om = O.OracleMesh(xy, tri)
     assert m.n_f == 525312
     u, v = inputs.velocity(om.xy_f, 7, 1, vortices=True)
     B = (0.0, 0.0, 1.0)
-    refs = {}
-    for kind in (0, 1):
-        ref = om.solve(u, v, kind, B=B, sigma=1.0, rho_over_dt=20.0, tol=1e-8)
-        ref["exact"] = O.pcg(om.K, om.d, ref["b"], x0=ref["phi_c"], tol=1e-13)["x"]
-        refs[kind] = ref
-    yield m, u, v, B, refs
+    refs = {kind: c2_references(om, u, v, B, kind) for kind in (0, 1)}
+    u6, v6 = inputs.velocity(om.xy_f, 6, 1, vortices=True)
+    prev = om.solve(u6, v6, 0, B=B, sigma=1.0, rho_over_dt=20.0, tol=1e-8)["phi_c"]
+    warm = om.solve(u, v, 0, B=B, sigma=1.0, rho_over_dt=20.0, tol=1e-8, x0=prev)
+    yield dict(mesh=m, u=u, v=v, B=B, refs=refs, prev=prev, warm=warm)
     m.close()
 
 
+def check_full_size_fields(out, ref, conv, tol, kind, B, sigma=1.0, gates=True):
+    """Relative L2 and elementwise agreement of phi_c, phi_f, grad phi and J x B with the oracle solve
+    at the same tolerance (ref) and with the converged solution (conv)."""
+    e = {"phi_c": rel(out["phi_c"], ref["phi_c"]), "phi_f": rel(out["phi_f"], ref["phi_f"]),
+         "grad": rel(out["grad"], ref["grad"])}
+    if kind == 0:
+        e["force"] = rel(out["force"], ref["force"])
+    if gates:    # A11(i): the same rule and tolerance from the same x0
+        assert e["phi_c"] <= 1e-8 and e["phi_f"] <= 1e-8, e
+        assert e["grad"] <= 1e-6, e
+        if kind == 0:
+            assert e["force"] <= 1e-6, e
+    phi_max = np.max(np.abs(conv["phi_c"]))
+    g_max = np.max(np.abs(conv["grad"]))
+    b2 = float(np.dot(B, B))
+    for r in (ref, conv):
+        # a reference whose own true residual is above tol (the converged pressure solution stalls
+        # near 8e-12) is only that accurate
+        t = max(tol, r.get("rel_res_true", 0.0))
+        assert np.max(np.abs(out["phi_c"] - r["phi_c"])) <= 2 * t * phi_max
+        assert np.max(np.abs(out["phi_f"] - r["phi_f"])) <= 2 * t * phi_max
+        assert np.max(np.abs(out["grad"] - r["grad"])) <= 10 * t * g_max
+        if kind == 0:
+            assert np.max(np.abs(out["force"] - r["force"])) <= 10 * t * sigma * b2 * g_max
+    return e
+
+
+# (precision, threads per block, lanes per row, blocks, tuning flags)
+FULL_SIZE_SHAPES = {
+    # the FP64 shape cgp_autotune picks here on GB300: one 512-thread block per SM,
+    # rows renumbered by coordinate bisection, reductions through tagged slots
+    "fp64-152x512-bisection-tagged": (0, 512, 1, 152, 12),
+    "fp64-152x512-mesh-order-tagged": (0, 512, 1, 152, 8),
+    "fp64-152x512-bisection-textbook": (0, 512, 1, 152, 6),
+    "fp64-default": (0, 0, 0, 0, 0),
+    # the mixed shape the autotuner picks: one 512-thread block per SM, bisection order
+    "mixed-152x512-bisection": (1, 512, 1, 152, 4),
+    "mixed-default": (1, 0, 0, 0, 0),
+}
+
+
+def set_solver_tuning(cgp, m, precision, block, lanes, blocks, flags):
+    what = cgp.CGP_TUNE_SOLVE_MIXED if precision else cgp.CGP_TUNE_SOLVE_FP64
+    cgp.cgp_set_tuning(m.handle, what, block, lanes, blocks, flags)
+
+
+@pytest.mark.parametrize("shape", list(FULL_SIZE_SHAPES))
+def test_full_size_512x256_in_the_benchmark_launch_shapes(cgp, c2_case, shape):
+    """Potential and pressure solves of the 512x256 workload in the launch shapes the benchmark
+    runs, against the oracle at the same tolerance from the same x0 (elementwise and at the gates),
+    and against the converged solution.  FP64 shapes also run at tol 1e-12, where the two solvers
+    must agree to 1e-10 in phi: a lost or stale partial sum among 152 blocks could not hide there."""
+    precision, block, lanes, blocks, flags = FULL_SIZE_SHAPES[shape]
+    m, u, v, B = c2_case["mesh"], c2_case["u"], c2_case["v"], c2_case["B"]
+    set_solver_tuning(cgp, m, precision, block, lanes, blocks, flags)
+    try:
+        for kind in (0, 1):
+            refs = c2_case["refs"][kind]
+            conv = refs["converged"]
+            out = run_step(cgp, m, u, v, B, 1.0, tol=1e-8, kind=kind, precision=precision)
+            launch = cgp.cgp_last_launch(m.handle, precision)
+            if blocks:
+                assert launch["blocks"] == blocks and launch["block"] == block, launch
+            assert out["info"]["status"] == cgp.CGP_OK, out["info"]
+            assert out["info"]["rel_res_true"] <= (1.2e-8 if flags & 2 else 1e-8), out["info"]
+            if precision == 0:
+                check_full_size_fields(out, refs[1e-8], conv, 1e-8, kind, B)
+                tight = run_step(cgp, m, u, v, B, 1.0, tol=1e-12, kind=kind)
+                assert tight["info"]["status"] == cgp.CGP_OK, tight["info"]
+                e = check_full_size_fields(tight, refs[1e-12], conv, 1e-12, kind, B)
+                assert e["phi_c"] <= 1e-10 and e["phi_f"] <= 1e-10, e
+                if kind == 0:
+                    assert e["force"] <= 1e-8, e
+            else:
+                # mixed precision follows another Krylov path than the FP64 oracle: at tol 1e-8 phi and
+                # grad phi meet the gates, J x B stays within twice the oracle's own error against the
+                # converged solution (A11(iii)); at 2e-9 every gate holds against both references
+                e = check_full_size_fields(out, refs[1e-8], conv, 1e-8, kind, B, gates=False)
+                assert e["phi_c"] <= 1e-8 and e["phi_f"] <= 1e-8 and e["grad"] <= 1e-6, e
+                if kind == 0:
+                    own = rel(refs[1e-8]["force"], conv["force"])
+                    assert rel(out["force"], conv["force"]) <= 2 * own, (rel(out["force"], conv["force"]), own)
+                acc = run_step(cgp, m, u, v, B, 1.0, tol=2e-9, kind=kind, precision=1)
+                assert acc["info"]["status"] == cgp.CGP_OK, acc["info"]
+                check_full_size_fields(acc, refs[2e-9], conv, 2e-9, kind, B)
+                if kind == 0:
+                    assert rel(acc["force"], conv["force"]) <= 1e-6
+                    assert rel(acc["phi_f"], conv["phi_f"]) <= 1e-8
+    finally:
+        set_solver_tuning(cgp, m, precision, 0, 0, 0, 0)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
-def test_full_size_512x256_potential_and_pressure(cgp, c2_case, precision):
-    """The 512x256 workload in the benchmark's launch shape, potential and pressure solves."""
-    m, u, v, B, refs = c2_case
-    for kind in (0, 1):
-        ref = refs[kind]
-        out = run_step(cgp, m, u, v, B, 1.0, tol=1e-8, kind=kind, precision=precision)
-        assert out["info"]["status"] == 0, out["info"]
-        assert out["info"]["rel_res_true"] <= 1.2e-8
-        e_gpu = rel(out["phi_c"], ref["exact"])
-        e_ref = rel(ref["phi_c"], ref["exact"])
-        # same tolerance, same accuracy: within a small factor of the oracle's own error
-        assert e_gpu <= max(4 * e_ref, 1e-10), (kind, e_gpu, e_ref)
-        if precision == 0:
-            assert rel(out["phi_f"], ref["phi_f"]) <= 1e-8
-            assert rel(out["grad"], ref["grad"]) <= 1e-6
-            if kind == 0:
-                assert rel(out["force"], ref["force"]) <= 1e-6
+def test_full_size_512x256_autotuned_warm_started_like_the_benchmark(cgp, c2_case, precision):
+    """The benchmark's own sequence: cgp_autotune on the potential right-hand side, then the
+    potential solve warm-started from the previous step's solution, against the oracle's solve
+    from its own previous-step solution at the same tolerance."""
+    m, u, v, B = c2_case["mesh"], c2_case["u"], c2_case["v"], c2_case["B"]
+    b = torch.empty(m.n_c, dtype=torch.float64, device=DEV)
+    cgp.cgp_restrict(m.handle, 0, B, 20.0, T(u), T(v), b)
+    scratch = torch.zeros(m.n_c, dtype=torch.float64, device=DEV)
+    cgp.cgp_autotune(m.handle, precision, b, scratch)
+    try:
+        out = run_step(cgp, m, u, v, B, 1.0, tol=1e-8, x0=c2_case["prev"], precision=precision)
+        assert out["info"]["status"] == cgp.CGP_OK, out["info"]
+        ref = c2_case["warm"]
+        conv = c2_case["refs"][0]["converged"]
+        e = check_full_size_fields(out, ref, conv, 1e-8, 0, B, gates=precision == 0)
+        assert e["phi_f"] <= 1e-8 and e["grad"] <= 1e-6, e
+    finally:
+        set_solver_tuning(cgp, m, precision, 0, 0, 0, 0)
 
 
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8, 32])

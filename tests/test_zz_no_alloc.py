@@ -70,3 +70,29 @@ def test_noalloc_rejects_systems_larger_than_its_scratch(cgp):
                                               None, None, None)
     assert st == cgp.CGP_ERR_INVALID_ARG
     assert b"static scratch" in cgp.load().cgp_last_error()
+
+
+def test_noalloc_solve_leaves_device_memory_untouched(cgp):
+    """After a first call on the device, a call takes no device memory: the free bytes the driver
+    reports are the same before and after it."""
+    xy, tri = inputs.ogrid(32, 16)
+    m = cgp.Mesh(xy, tri)
+    mats = m.matrices()
+    rowptr = torch.as_tensor(mats["rowptr"], dtype=torch.int32, device=DEV)
+    col = torch.as_tensor(mats["col"], dtype=torch.int32, device=DEV)
+    K = torch.as_tensor(mats["K"], dtype=torch.float64, device=DEV)
+    dinv = torch.as_tensor(mats["dinv"], dtype=torch.float64, device=DEV)
+    b = torch.randn(m.n_c, dtype=torch.float64, device=DEV, generator=torch.Generator(device=DEV).manual_seed(3))
+    b -= b.mean()
+    x = torch.zeros_like(b)
+    first = cgp.cgp_poisson_solve_noalloc(m.n_c, rowptr, col, K, dinv, b, x, tol=1e-10)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    x.zero_()
+    again = cgp.cgp_poisson_solve_noalloc(m.n_c, rowptr, col, K, dinv, b, x, tol=1e-10)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert first["status"] == again["status"] == cgp.CGP_OK
+    assert first["iterations"] == again["iterations"]
+    assert free_after == free_before
+    m.close()
