@@ -55,7 +55,8 @@ def workload_config(precision="fp64"):
 # solver launch, from one ncu capture of `bench.py --profile-case <precision>`
 # (the bench's launch shape).  They hold only for the kernel sources they were
 # taken on: when the sources' hash differs the traffic is reported as null.
-SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_sync.h", "cgp_fixed.h", "cgp_internal.h")
+SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_pcg_batch.cu", "cgp_pipe.cu", "cgp_solver.cuh", "cgp_sync.h", "cgp_fixed.h",
+                  "cgp_internal.h")
 SOLVER_TRAFFIC = {
     "sha256": "42ef0bf3a5dac1d074a5d246116bac004dc76d0907180c2e384ecfd6671164ee",
     "fp64": 13984768 + 406528,
@@ -192,6 +193,7 @@ def run_mine(args, rank, world, local_rank, refs_path=None):
 
     xy, tri = inputs.ogrid(N_THETA, N_R)
     mesh = cgp.Mesh(xy, tri)
+    cgp.cgp_mesh_set_ogrid(mesh.handle, N_THETA, N_R)   # the O-grid tiles are an autotuner choice
     xy_f, _, _ = mesh.fine_geometry()
     n, nnz = mesh.n_c, mesh.nnz
     W, K = args.warmup, args.steps
@@ -576,6 +578,7 @@ def run_levels(cgp, inputs, torch, dev, flush, steps=10, warm=3):
         nt, nr = N_THETA >> (k - 1), N_R >> (k - 1)
         xy, tri = inputs.ogrid(nt, nr)
         m = cgp.Mesh(xy, tri, k)
+        cgp.cgp_mesh_set_ogrid(m.handle, nt, nr)
         xy_f, _, _ = m.fine_geometry()
         n = m.n_c
         b = torch.empty(n, **f64)
@@ -629,6 +632,7 @@ def run_far_field(cgp, inputs, torch, dev, flush, steps=8, warm=3):
     natural condition everywhere and with phi = 0 on the outer boundary: iterations and solves/s."""
     xy, tri = inputs.ogrid(N_THETA, N_R)
     m = cgp.Mesh(xy, tri)
+    cgp.cgp_mesh_set_ogrid(m.handle, N_THETA, N_R)
     xy_f, _, _ = m.fine_geometry()
     f64 = dict(dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
@@ -677,6 +681,7 @@ def run_mixed_small(cgp, inputs, torch, dev, steps=200, check_every=10, refs_pat
     wl = configs.C3_MIXED
     xy, tri = inputs.ogrid(wl.n_theta, wl.n_r)
     m = cgp.Mesh(xy, tri)
+    cgp.cgp_mesh_set_ogrid(m.handle, wl.n_theta, wl.n_r)
     xy_f, _, _ = m.fine_geometry()
     f64 = dict(dtype=torch.float64, device=dev)
     n, nf, tf = m.n_c, m.n_f, m.t_f
@@ -705,6 +710,10 @@ def run_mixed_small(cgp, inputs, torch, dev, steps=200, check_every=10, refs_pat
     for name, prec in (("fp64", cgp.CGP_FP64), ("mixed", cgp.CGP_MIXED)):
         x = torch.zeros(n, **f64)
         phis = torch.empty((steps, n), **f64)
+        cgp.cgp_autotune(m.handle, prec, b[0], x)   # each precision in its own best launch shape
+        out.setdefault("tuned_launch", {})[name] = cgp.cgp_get_tuning(
+            m.handle, cgp.CGP_TUNE_SOLVE_MIXED if prec == cgp.CGP_MIXED else cgp.CGP_TUNE_SOLVE_FP64)
+        x.zero_()
         for t in range(3):   # warm-up on the first steps
             cgp.cgp_poisson_solve(m.handle, b[t], x, tol=wl.tol, precision=prec, inner_tol=wl.inner_tol,
                                   use_x0=t > 0, info=False)
@@ -1062,6 +1071,7 @@ def profile_case(case):
     if case in ("fp64", "mixed"):
         xy, tri = inputs.ogrid(N_THETA, N_R)
         m = cgp.Mesh(xy, tri)
+        cgp.cgp_mesh_set_ogrid(m.handle, N_THETA, N_R)
         xy_f, _, _ = m.fine_geometry()
         u, v = inputs.velocity(xy_f, 7, SEED, vortices=True)
         b = torch.empty(m.n_c, dtype=torch.float64, device=dev)
@@ -1070,8 +1080,9 @@ def profile_case(case):
         x = torch.zeros(m.n_c, dtype=torch.float64, device=dev)
         prec = cgp.CGP_MIXED if case == "mixed" else cgp.CGP_FP64
         what = cgp.CGP_TUNE_SOLVE_MIXED if case == "mixed" else cgp.CGP_TUNE_SOLVE_FP64
-        # the shape the autotuner picks on GB300 (rows renumbered by coordinate bisection; FP64: tagged reductions)
-        cgp.cgp_set_tuning(m.handle, what, 512, 1, 152, 4 if case == "mixed" else 12)
+        # the shape the autotuner picks on GB300 (FP64: O-grid tiles with the stencil product and tagged
+        # reductions; mixed: rows renumbered by coordinate bisection)
+        cgp.cgp_set_tuning(m.handle, what, 512, 1, 152, 4 if case == "mixed" else 40)
         for _ in range(2):
             x.zero_()
             info = cgp.cgp_poisson_solve(m.handle, b, x, tol=TOL, precision=prec)

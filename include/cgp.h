@@ -406,7 +406,10 @@ int cgp_spmv(cgp_mesh m, int precision, const void* x, void* y, void* stream);
  * stencil form of K: values at the fixed (angle, ring) offsets (0,0), (+-1,0),
  * (0,+-1), (+1,+1), (-1,-1), zeros where a neighbour does not exist, and no
  * column indices (9 s n bytes per product against CSR's 12 s n + 4 n; a
- * structured-stencil storage choice beside the paper's unstructured CSR).  Afterwards SpMV tuning flag bit 0 selects it for cgp_spmv.
+ * structured-stencil storage choice beside the paper's unstructured CSR).
+ * Afterwards SpMV tuning flag bit 0 selects it for cgp_spmv, and solver
+ * tuning flag bit 5 selects the O-grid tiles with the stencil product for
+ * the persistent FP64 solver (cgp_set_tuning; cgp_autotune considers it).
  * Synchronous; one allocation of 84 n_c bytes (FP64 and FP32 planes), freed
  * with the mesh.  INVALID_ARG if n_theta * (n_r + 1) != n_c or if any row's
  * CSR pattern differs from the stencil.
@@ -435,7 +438,20 @@ int cgp_mesh_set_ogrid(cgp_mesh m, int n_theta, int n_r);
  *         grid-wide reduction through tagged 128-bit slots that show by
  *         themselves when every block has stored its partial sum, instead of
  *         a barrier counter followed by a read of the slots (the same totals,
- *         bit for bit); other bits must be 0.
+ *         bit for bit); bit 4 (FP64, rows in shared memory, at least 256
+ *         threads per block and 1, 2 or 4 lanes per row; otherwise the
+ *         single-reduction form runs) runs the pipelined iteration of
+ *         Ghysels and Vanroose: four warps of every block complete the
+ *         iteration's grid reduction and fetch the next halo while the others
+ *         form the next product, at the price of three more FP64 vector
+ *         operations per row and recurrences that drift sooner (a restart
+ *         from the true residual near tight tolerances); bit 5 (FP64
+ *         single-reduction form, meshes registered with cgp_mesh_set_ogrid,
+ *         rows in shared memory) renumbers the rows into near-rectangular
+ *         tiles of the O-grid's (angle, ring) index grid, one per block, and
+ *         forms every product with the seven-point stencil on the block's
+ *         padded box (no column indices; bit 2 is then ignored); other bits
+ *         must be 0.
  *         SpMV: bit 0 uses the O-grid stencil form (cgp_mesh_set_ogrid) with
  *         one thread per row (lanes ignored).
  * Invalid shapes are rejected with INVALID_ARG.  cgp_autotune sets these.
@@ -458,7 +474,9 @@ int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks, in
  * threads per block {256, 512}, lanes per CSR row {1, 2, 4}, grid size (a
  * few counts around the SM count, and 1..16 blocks for small systems),
  * shared-memory residency, the row order (flag bit 2) and, for FP64, the
- * iteration form (flag bit 1) and the reduction form (flag bit 3),
+ * iteration form (flag bits 1 and 4), the reduction form (flag bit 3) and,
+ * on meshes registered with cgp_mesh_set_ogrid, the O-grid tiles with the
+ * stencil product (flag bit 5); only candidates that converge count,
  * and keeps the fastest with cgp_set_tuning.  Every candidate meets the
  * same tolerance on the true residual.  x
  * (device [n_c]) is overwritten.  cache_path (nullable) names a text file of

@@ -84,6 +84,18 @@ struct PermSystem {
   double* xbuf = nullptr;             // [n] x in the new order
   HaloPlan plan;                      // halo lists of the permuted pattern
   void* base = nullptr;
+  // O-grid tiles (tiles != 0): blocks own near-rectangles of the (angle, ring)
+  // index grid and the product uses the seven-point stencil on a padded box
+  int tiles = 0;
+  int box_cap = 0;                    // largest box (doubles)
+  int st_max_halo = 0;
+  double* planes = nullptr;           // [7][n] stencil coefficients in the new order
+  int* bpos = nullptr;                // [n] box position of every row in its block's box
+  int* bdim = nullptr;                // [nblk] box row length
+  int* st_hptr = nullptr;             // [nblk + 1] halo of every box (rows read from other blocks)
+  int* st_hidx = nullptr;             // [total] their global (new) row
+  int* st_hpos = nullptr;             // [total] their box position
+  void* st_base = nullptr;
 };
 
 struct cgp_mesh_impl {
@@ -127,7 +139,8 @@ struct cgp_mesh_impl {
   double* p = nullptr;
   double* p2 = nullptr;
   double* q = nullptr;
-  double* pub64 = nullptr;   // [6 n] single-reduction FP64: published R[2], W[2], S[2]
+  double* pub64 = nullptr;   // [18 n] published vectors: single-reduction R[2], W[2], S[2] (6 n doubles);
+                             // pipelined tagged W[3], Z[3], N[3] (9 n 16-byte words)
   float* f32pub = nullptr;   // [6 n] mixed: published R[2], W[2], S[2]
   float* f32own = nullptr;   // [6 n] mixed without shared-memory residency: own inner vectors
   float* fpart = nullptr;    // [8 * max_blocks] FP32 partial sums
@@ -161,7 +174,7 @@ struct cgp_mesh_impl {
   void* vinc_base = nullptr;
 
   std::vector<HaloPlan> plans;   // cached per block count
-  std::vector<PermSystem> psys;  // cached per (block count, boundary condition)
+  std::vector<PermSystem> psys;  // cached per (block count, boundary condition, tiles)
   SolverTuning tune[4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};  // by cgp_tune_target
   PlanRecord last_plan[2] = {{0, 0, 0, 0}, {0, 0, 0, 0}};                          // FP64, MIXED
 };

@@ -293,7 +293,7 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
          o_mpar = take(m->h_mid_par.size() * 4), o_xyf = take(2 * (size_t)m->n_f * 8),
          o_xyc = take(2 * n * 8), o_incp = take((n + 1) * 4), o_inc = take(3 * (size_t)t_c * 4),
          o_bp = take(n * 8), o_r = take(n * 8), o_z = take(n * 8), o_p = take(n * 8), o_p2 = take(n * 8), o_q = take(n * 8),
-         o_pub64 = take(6 * n * 8), o_f32pub = take(6 * n * 4), o_f32own = take(6 * n * 4),
+         o_pub64 = take(18 * n * 8), o_f32pub = take(6 * n * 4), o_f32own = take(6 * n * 4),
          o_fpart = take((size_t)m->max_blocks * 8 * 4), o_part = take((size_t)m->max_blocks * 32 * 8),
          o_tpart = take((size_t)m->max_blocks * 6 * 16), o_bar = take(256),
          o_res = take(sizeof(SolveResult));
@@ -521,6 +521,7 @@ extern "C" int cgp_mesh_destroy(cgp_mesh m) {
   for (auto& ps : m->psys) {
     if (ps.base) cudaFree(ps.base);
     if (ps.plan.base) cudaFree(ps.plan.base);
+    if (ps.st_base) cudaFree(ps.st_base);
   }
   if (m->st_base) cudaFree(m->st_base);
   if (m->d_base) cudaFree(m->d_base);

@@ -81,7 +81,8 @@ def test_batched_instances_match_the_oracle(cgp, systems, precision, packed):
 
 @pytest.mark.parametrize("block,lanes,per_sm,flags", [(256, 1, 1, 0), (512, 2, 2, 1), (128, 4, 0, 0), (64, 8, 1, 1),
                                                      (256, 1, 1, 4), (512, 2, 2, 5), (256, 1, 2, 2), (128, 1, 0, 6),
-                                                     (256, 1, 1, 8), (512, 1, 1, 12), (128, 2, 0, 9)])
+                                                     (256, 1, 1, 8), (512, 1, 1, 12), (128, 2, 0, 9),
+                                                     (256, 1, 1, 16), (512, 2, 1, 20), (256, 4, 1, 20)])
 def test_batched_launch_shapes(cgp, systems, block, lanes, per_sm, flags):
     bs = [T(s["b"]) for s in systems]
     xs = [torch.zeros_like(b) for b in bs]
