@@ -134,6 +134,20 @@ CGP_HD inline double to_double(I128 X, int E) {
 
 CGP_HD inline I128 add(I128 a, I128 b) { return a + b; }
 
+// 64-bit images for the tagged reductions of the solver: relative to a
+// reference exponent E >= exponent_of(v), a finite v = M 2^(e - 1075) maps to
+// X = (M << 4) >> (E - e) = v 2^(1079 - E) truncated toward zero in magnitude,
+// |X| < 2^57, so that 32 of them add within 62 bits.
+CGP_HD inline int64_t image64(double v, int E) {
+  const uint64_t b = dbits(v);
+  const int eb = (int)((b >> 52) & 0x7FF);
+  const uint64_t M = (b & ((1ull << 52) - 1)) | (eb ? (1ull << 52) : 0ull);
+  int sh = E - (eb ? eb : 1);
+  if (sh > 63) sh = 63;
+  const int64_t X = (int64_t)((M << 4) >> sh);
+  return (b >> 63) ? -X : X;
+}
+
 // Tagged slot: one block's partial X (exponent E, |X| < 2^117 for a block of
 // <= 1024 threads) of reduction `red` in one 128-bit word that says by itself
 // whether it holds that reduction:
@@ -146,8 +160,10 @@ constexpr int kTagShift = 38;
 CGP_HD inline uint64_t tag24(int red) { return 0x800000ull | ((unsigned)red & 0x7FFFFFu); }
 CGP_HD inline uint64_t tag8(int red) { return ((unsigned)red & 0xFFu) ^ 0xA5u; }
 
-CGP_HD inline void pack_tagged(I128 x, int E, int red, uint64_t& lo, uint64_t& hi) {
-  const I128 m = E < kBadExp ? sar(x, kTagShift) : (I128)0;
+// shift: bits of X dropped before packing (kTagShift for a 128-bit partial;
+// 0 for a 64-bit one, whose |X| < 2^62 fits the 80-bit field as it is).
+CGP_HD inline void pack_tagged(I128 x, int E, int red, uint64_t& lo, uint64_t& hi, int shift = kTagShift) {
+  const I128 m = E < kBadExp ? sar(x, shift) : (I128)0;
   lo = ((uint64_t)m << 8) | tag8(red);
   hi = ((uint64_t)(m >> 56) & 0xFFFFFFull) | ((uint64_t)(E & 0xFFFF) << 24) | (tag24(red) << 40);
 }

@@ -7,46 +7,6 @@
 namespace cgp {
 namespace {
 
-// ---- 64-bit fixed-point block sums ------------------------------------------
-// Relative to a reference exponent E >= e, a finite double v = M 2^(e - 1075)
-// (M < 2^53 with the implicit bit; e = 1 for zero and subnormals) has the
-// image X = (M << 4) >> (E - e) = v 2^(1079 - E) truncated, |X| < 2^57.  A
-// warp adds its images exactly in three 26/26/12-bit limbs with redux.sync.
-// The sums are deterministic (fixed assignment of rows to threads and of
-// threads to warps) and exact up to the truncation of each term 2^-54 below
-// the largest one of its warp or block.
-__device__ __forceinline__ int fx64_exponent(double v) {
-  const int e = (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF);
-  return e == 0x7FF ? fx::kBadExp : (e ? e : 1);
-}
-
-__device__ __forceinline__ long long fx64_image(double v, int E) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int eb = (int)((b >> 52) & 0x7FF);
-  const unsigned long long M = (b & ((1ull << 52) - 1)) | (eb ? (1ull << 52) : 0ull);
-  const int sh = min(E - (eb ? eb : 1), 63);
-  const long long X = (long long)((M << 4) >> sh);
-  return (b >> 63) ? -X : X;
-}
-
-// exact warp sum of |x| < 2^57 per lane (|sum| < 2^62), on every lane
-__device__ __forceinline__ long long warp_sum57(long long x) {
-  const unsigned s0 = __reduce_add_sync(0xffffffffu, (unsigned)(x & 0x3FFFFFF));
-  const unsigned s1 = __reduce_add_sync(0xffffffffu, (unsigned)((x >> 26) & 0x3FFFFFF));
-  const int s2 = __reduce_add_sync(0xffffffffu, (int)(x >> 52));
-  return (long long)s0 + ((long long)s1 << 26) + ((long long)s2 << 52);
-}
-
-// Tagged slot of a 64-bit block partial S (|S| < 2^62, value S 2^(E - 1074)):
-// the layout of fx::pack_tagged with S stored unshifted, read back by
-// tagged_total<kSlot64Shift>.
-constexpr int kSlot64Shift = 55;
-__device__ __forceinline__ void store_slot64(ulonglong2* slot, long long S, int E, int red) {
-  const uint64_t lo = ((uint64_t)S << 8) | fx::tag8(red);
-  const uint64_t hi = ((uint64_t)(S >> 56) & 0xFFFFFFull) | ((uint64_t)(E & 0xFFFF) << 24) | (fx::tag24(red) << 40);
-  st_relaxed_b128(slot, lo, hi);
-}
-
 // ---- shared-memory mbarriers (arrive with release, bounded waits with acquire) ----
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 

@@ -163,10 +163,10 @@ __device__ __forceinline__ ulonglong2* tag_slot(const Desc& d, int red, int c, i
 
 // Sum NC (<= 3) per-thread values over the block; warp c then folds
 // component c over the warps and stores it as this block's partial in bank
-// (red & 1): untagged in d.part, or TAGGED in d.tpart.  The sums are exact
-// fixed-point integer sums (cgp_fixed.h): they run on the integer pipe, cost
-// no FP64 instructions, and do not depend on the order of the terms.
-template <int NC, bool TAGGED = false>
+// (red & 1) of d.part.  The sums are exact fixed-point integer sums
+// (cgp_fixed.h): they run on the integer pipe, cost no FP64 instructions, and
+// do not depend on the order of the terms.
+template <int NC>
 __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, double (&v)[NC], Shared& sh) {
   static_assert(NC >= 1 && NC <= 3, "one to three components per reduction");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -180,7 +180,6 @@ __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, dou
       sh.wexp[c][warp] = E;
     }
   }
-  if (TAGGED && threadIdx.x == 0) sh.tflag = 1;
   __syncthreads();
   for (int c = warp; c < NC; c += nw) {
     fx::I128 x = 0;
@@ -192,16 +191,77 @@ __device__ __forceinline__ void put_partials(const Desc& d, int lb, int red, dou
     const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
     x = warp_sum_i128(E < fx::kBadExp ? fx::sar(x, E - e) : (fx::I128)0);
     if (lane == 0) {
-      if (TAGGED) {
-        uint64_t lo, hi;
-        fx::pack_tagged(x, E, red, lo, hi);
-        st_relaxed_b128(tag_slot(d, red, c, lb), lo, hi);
-      } else {
-        ulonglong2* slot = reinterpret_cast<ulonglong2*>(part_slot(d, red, c, lb));
-        slot[0] = make_ulonglong2((unsigned long long)x, (unsigned long long)(x >> 64));
-        slot[1] = make_ulonglong2((unsigned long long)E, 0ull);
-      }
+      ulonglong2* slot = reinterpret_cast<ulonglong2*>(part_slot(d, red, c, lb));
+      slot[0] = make_ulonglong2((unsigned long long)x, (unsigned long long)(x >> 64));
+      slot[1] = make_ulonglong2((unsigned long long)E, 0ull);
     }
+  }
+}
+
+// ---- 64-bit fixed-point block sums ------------------------------------------
+// Relative to a reference exponent E >= e, a finite double v = M 2^(e - 1075)
+// (M < 2^53 with the implicit bit; e = 1 for zero and subnormals) has the
+// image X = (M << 4) >> (E - e) = v 2^(1079 - E) truncated, |X| < 2^57.  A
+// warp adds its images exactly in three 26/26/12-bit limbs with redux.sync.
+// The sums are deterministic (fixed assignment of rows to threads and of
+// threads to warps) and exact up to the truncation of each term 2^-54 below
+// the largest one of its warp or block.
+__device__ __forceinline__ int fx64_exponent(double v) { return fx::exponent_of(v); }
+__device__ __forceinline__ long long fx64_image(double v, int E) { return (long long)fx::image64(v, E); }
+
+// exact warp sum of |x| < 2^57 per lane (|sum| < 2^62), on every lane
+__device__ __forceinline__ long long warp_sum57(long long x) {
+  const unsigned s0 = __reduce_add_sync(0xffffffffu, (unsigned)(x & 0x3FFFFFF));
+  const unsigned s1 = __reduce_add_sync(0xffffffffu, (unsigned)((x >> 26) & 0x3FFFFFF));
+  const int s2 = __reduce_add_sync(0xffffffffu, (int)(x >> 52));
+  return (long long)s0 + ((long long)s1 << 26) + ((long long)s2 << 52);
+}
+
+// Tagged slot of a 64-bit block partial S (|S| < 2^62, value S 2^(E - 1074)):
+// the layout of fx::pack_tagged with S stored unshifted, read back by
+// tagged_total<kSlot64Shift>.
+constexpr int kSlot64Shift = 55;
+__device__ __forceinline__ void store_slot64(ulonglong2* slot, long long S, int E, int red) {
+  uint64_t lo, hi;
+  fx::pack_tagged((fx::I128)S, E, red, lo, hi, 0);
+  st_relaxed_b128(slot, lo, hi);
+}
+
+// Tagged reductions with 64-bit fixed-point partials: every warp sums its
+// lanes' values exactly in REDUX limbs (fx64_image relative to the warp's
+// largest exponent), warp c folds the block's warp sums of component c
+// (aligned to the block's largest exponent, 5 bits of headroom for up to 32
+// warps) and stores the block's partial in its tagged slot (store_slot64;
+// read back by tagged_total<kSlot64Shift>).  Deterministic, and exact up to
+// the truncation of each term 2^-54 below the largest one of its warp or
+// block: far fewer integer instructions than the 128-bit sums of
+// put_partials, which the untagged reductions keep.
+template <int NC>
+__device__ __forceinline__ void put_partials64(const Desc& d, int lb, int red, double (&v)[NC], Shared& sh) {
+  static_assert(NC >= 1 && NC <= 3, "one to three components per reduction");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)fx64_exponent(v[c]));
+    const long long S = warp_sum57(E < fx::kBadExp ? fx64_image(v[c], E) : 0ll);
+    if (lane == 0) {
+      sh.whi[c][warp] = S;
+      sh.wexp[c][warp] = E;
+    }
+  }
+  if (threadIdx.x == 0) sh.tflag = 1;
+  __syncthreads();
+  for (int c = warp; c < NC; c += nw) {
+    long long sw = 0;
+    int ew = 1;
+    if (lane < nw) {
+      sw = sh.whi[c][lane];
+      ew = sh.wexp[c][lane];
+    }
+    const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)ew);
+    const long long y = E < fx::kBadExp ? (sw >> min(E - ew + 5, 63)) : 0ll;   // |y| < 2^57
+    const long long S = warp_sum57(y);
+    if (lane == 0) store_slot64(tag_slot(d, red, c, lb), S, E, red);
   }
 }
 
@@ -286,9 +346,9 @@ __device__ __forceinline__ void get_totals_then(const Desc& d, int red, Shared& 
 // barrier, not from these loads.)  Gives up (false on every lane) after
 // d.spin_ns of wall-clock time or when another block has given up.
 //
-// SHIFT places the slot's mantissa: a slot holds m 2^(E + SHIFT - 1129); the
-// 128-bit block partials of put_partials use fx::kTagShift.
-template <int SHIFT = fx::kTagShift>
+// SHIFT places the slot's mantissa: a slot holds m 2^(E + SHIFT - 1129)
+// (the 64-bit block partials of put_partials64: kSlot64Shift).
+template <int SHIFT>
 __device__ __forceinline__ bool tagged_total(const Desc& d, int red, int c, double& total) {
   constexpr int PRE = 8;  // slots per lane per pass (groups of up to 256 blocks per pass)
   const int lane = threadIdx.x & 31;
@@ -368,7 +428,7 @@ __device__ __forceinline__ bool tagged_total(const Desc& d, int red, int c, doub
 // when the barrier completes.
 template <int NC>
 __device__ __forceinline__ void red_start(const Desc& d, Group& grp, int lb, int red, double (&v)[NC], Shared& sh) {
-  if (d.tagged) put_partials<NC, true>(d, lb, red, v, sh);
+  if (d.tagged) put_partials64<NC>(d, lb, red, v, sh);
   else put_partials<NC>(d, lb, red, v, sh);
   grp.arrive();
 }
@@ -384,7 +444,7 @@ __device__ __forceinline__ bool red_finish(const Desc& d, Group& grp, int red, S
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int c = warp; c < NC; c += nw) {
     double t;
-    if (!tagged_total(d, red, c, t)) {
+    if (!tagged_total<kSlot64Shift>(d, red, c, t)) {
       if ((threadIdx.x & 31) == 0) sh.tflag = 0;
       break;
     }

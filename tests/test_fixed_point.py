@@ -1,10 +1,12 @@
 """The solver's integer-pipe reductions against exact rational sums (CPU only).
 
-Dot products inside the persistent CG kernel are summed as 128-bit
-fixed-point integers aligned to a common exponent (per warp, per block and
-across blocks) and converted back to the nearest double.  These tests build
-the same arithmetic on the host and compare it with the correctly rounded
-exact sum of the same doubles, computed with Python fractions.
+Dot products inside the persistent CG kernel are summed as fixed-point
+integers aligned to a common exponent (per warp, per block and across
+blocks) and converted back to the nearest double: 128-bit and exact for the
+plain reductions, 64-bit with a bounded truncation for the tagged ones of
+the iterations.  These tests build the same arithmetic on the host and
+compare it with the exact sum of the same doubles, computed with Python
+fractions.
 """
 import math
 import os
@@ -34,8 +36,10 @@ def bits(v):
     return struct.unpack("<Q", struct.pack("<d", float(v)))[0]
 
 
-def run(harness, groups, red=None):
+def run(harness, groups, red=None, warps_per_block=None):
     text = "" if red is None else f"R {red}\n"
+    if warps_per_block is not None:
+        text += f"W {warps_per_block}\n"
     text += "".join(f"G {len(g)}\n" + " ".join(f"{bits(v):x}" for v in g) + "\n" for g in groups)
     r = subprocess.run([harness], input=text, capture_output=True, text=True, check=True)
     return struct.unpack("<d", struct.pack("<Q", int(r.stdout.strip(), 16)))[0]
@@ -101,8 +105,9 @@ def test_large_sums_do_not_overflow(harness):
 
 
 # ---------------------------------------------------------------------------
-# tagged slots (tuning flag bit 3): each block's partial travels through an
-# 80-bit mantissa with its exponent and the reduction's tags
+# the tagged slot encoding: a block's partial travels through an 80-bit
+# mantissa with its exponent and the reduction's tags (here a 128-bit partial
+# shifted into the field)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("seed", range(8))
 def test_tagged_slots_keep_the_sum_correctly_rounded(harness, seed):
@@ -130,3 +135,49 @@ def test_tagged_slots_cancel_and_propagate_non_finite(harness):
     assert run(harness, [[1e16, 1.0, -1e16], [3.0, -3.0]], red=7) == 1.0
     assert run(harness, [[0.0], [-0.0]], red=9) == 0.0
     assert math.isnan(run(harness, [[1.0], [float("inf")]], red=11))
+
+
+# ---------------------------------------------------------------------------
+# the 64-bit tagged reductions of the solver's iterations: warp sums of 64-bit
+# images, block sums with 5 bits of headroom, unshifted tagged slots
+# ---------------------------------------------------------------------------
+def bound64(groups, warps_per_block, got):
+    """Truncation bound: under 2^(E - 1079) per term, 2^(E - 1074) per warp and per block, E the largest
+    biased exponent of the inputs; then the rounding of the result."""
+    vals = [float(v) for g in groups for v in g]
+    emax = max((math.frexp(v)[1] + 1022 if v != 0.0 else 1) for v in vals)
+    nblocks = (len(groups) + warps_per_block - 1) // warps_per_block
+    unit = 2.0 ** (emax - 1074)
+    return len(vals) * unit / 32 + (len(groups) + nblocks) * unit + 0.5 * math.ulp(abs(got))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_64bit_tagged_sums_stay_within_the_truncation_bound(harness, seed):
+    rng = np.random.default_rng(300 + seed)
+    wpb = int(rng.choice([1, 4, 12, 16, 32]))
+    groups = []
+    for _ in range(int(rng.integers(1, 600))):       # up to a few hundred blocks of warps
+        n = int(rng.integers(1, 33))
+        scale = 10.0 ** rng.uniform(-6, 6, size=n)
+        groups.append(list(rng.standard_normal(n) * scale))
+    got = run(harness, groups, red=int(rng.integers(2, 1 << 22)), warps_per_block=wpb)
+    want = exact(groups)
+    assert abs(got - want) <= bound64(groups, wpb, got), (got, want)
+
+
+def test_64bit_tagged_sums_are_exact_on_one_scale_and_cancel(harness):
+    # values on a common grid of the largest exponent carry no truncation
+    groups = [[1.0, 2.0, 3.5], [-0.25, 0.125], [4.0]]
+    assert run(harness, groups, red=5, warps_per_block=2) == exact(groups)
+    # a sum far below its largest term keeps only what the truncation bound allows (the 1.0 here
+    # sits 2^-53 below 1e16, under the block level's unit)
+    groups = [[1e16, 1.0, -1e16], [3.0, -3.0]]
+    got = run(harness, groups, red=7, warps_per_block=16)
+    assert abs(got - 1.0) <= bound64(groups, 16, got)
+    assert run(harness, [[0.0], [-0.0]], red=9, warps_per_block=1) == 0.0
+    assert math.isnan(run(harness, [[1.0], [float("inf")]], red=11, warps_per_block=1))
+    # every slot checked against stale, torn and empty words (exit status otherwise)
+    for red in (2, 255, 256, (1 << 23) + 5):
+        groups = [[1.0, -3.5e-7], [-2.0 ** 60, 5.0], [1e-300], [-7.25e12, 1.0 / 3.0]]
+        got = run(harness, groups, red=red, warps_per_block=2)
+        assert abs(got - exact(groups)) <= bound64(groups, 2, got)
