@@ -248,8 +248,11 @@ int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* col, const do
  *     use (about 256 rows per block, at most blocks_per_sm x SMs), so that its
  *     rows fit in shared memory; systems are packed largest first into waves
  *     of at most blocks_per_sm x SMs blocks, and the waves run as consecutive
- *     cooperative launches: small systems share the GPU, large ones get all
- *     of it;
+ *     cooperative launches, the wave of the smallest systems first: small
+ *     systems share the GPU, large ones get all of it.  Tuning flag bits 5-6
+ *     ask for 256 << k rows per block instead (k = 1..3; a system still gets
+ *     at least the blocks that keep its chunk in shared memory), so that
+ *     large systems share the GPU too;
  *   - packed (tuning flag bit 2): ONE cooperative launch holds every system,
  *     block groups sized in proportion to each system's work (nnz sqrt(n)).
  * Neither needs host work between launches, so a solve can be captured in a
@@ -274,7 +277,10 @@ int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* col, const do
  *                     fit on an SM) and flags (bit 0: rows in global
  *                     memory; bit 1: FP64 textbook iteration, as for
  *                     cgp_set_tuning; bit 2: one packed launch, not waves;
- *                     bit 3: tagged reductions, as for cgp_set_tuning).
+ *                     bit 3: tagged reductions and bit 4: pipelined FP64
+ *                     iteration, as for cgp_set_tuning; bits 5-6: waves
+ *                     with 256 << k rows per block).  INVALID_ARG for other
+ *                     bits.
  * cgp_batch_autotune  times a set of launch shapes on the batch's own
  *                     systems (from x = 0) and keeps the fastest; writes the
  *                     best time in ms to best_ms (nullable).  Synchronous;

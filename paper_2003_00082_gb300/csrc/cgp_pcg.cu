@@ -487,6 +487,14 @@ size_t res_smem_bytes(SolverKind kind, int chunk, const HaloPlan& hp) {
   return (s + 15) / 16 * 16;
 }
 
+// Shared memory a resident block needs for its chunk and CSR slice, before
+// the halo is known (the lower bound the planners size chunks by).
+size_t res_smem_rows(SolverKind kind, int chunk, int nnz) {
+  HaloPlan none;
+  none.max_nnz = nnz;
+  return res_smem_bytes(kind, chunk, none);
+}
+
 // Dynamic shared memory of a resident single-reduction FP64 block on O-grid
 // tiles: nine vectors, the padded box, D^-1 of the halo, seven coefficient
 // planes, three staging buffers of the halo; box positions of the rows and
@@ -576,8 +584,7 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
     return CGP_OK;
   }
   const size_t limit = (size_t)std::max(0, optin_smem(device) - (int)fa.sharedSizeBytes - 1024);
-  if ((size_t)chunk * (kind == KIND_FP64_PIPE ? 96 : kind == KIND_FP64_SR ? 80 : 56) + (size_t)rough_nnz * 12 > limit)
-    return CGP_OK;
+  if (res_smem_rows(kind, chunk, rough_nnz) > limit) return CGP_OK;
   HaloPlan hp;
   if (ps) {
     hp = ps->plan;
@@ -944,8 +951,7 @@ int batch_plan(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
     cgp_mesh_impl* m = B->meshes[i];
     const int chunk = (m->n_c + nb[i] - 1) / nb[i];
     const int rough_nnz = m->h_rowptr[std::min(m->n_c, chunk)] - m->h_rowptr[0];
-    if ((size_t)chunk * (kind == KIND_FP64_PIPE ? 96 : kind == KIND_FP64_SR ? 80 : 56) + (size_t)rough_nnz * 12 >
-        limit) {
+    if (res_smem_rows(kind, chunk, rough_nnz) > limit) {
       res = false;
       break;
     }
@@ -1004,12 +1010,15 @@ int batch_plan(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
   return CGP_OK;
 }
 
-// Wave schedule: every instance gets the block count a solve of it alone
-// would use (about 256 rows per block, at most one SM's worth of blocks
-// each), so that it can keep its rows in shared memory; instances are packed
-// largest first into waves of at most blocks_per_sm x SMs blocks, and the
-// waves run as consecutive cooperative launches.  Small instances then share
-// the GPU while each large one gets all of it.
+// Wave schedule: every instance gets about rows_per_block rows per block
+// (256 << (flags bits 5-6): 256 as a solve of it alone would use, up to 2048),
+// at most one SM's worth of blocks and at least as many blocks as keep its
+// chunk in shared memory; instances are packed largest first into waves of
+// at most blocks_per_sm x SMs blocks, and the waves run as consecutive
+// cooperative launches, the wave of the smallest instances first.  Small
+// instances then share the GPU, and a large one gets all of it (256 rows a
+// block) or shares it with others of its size (more rows a block: the
+// iteration is bound by the latency of its reductions, not by its rows).
 int batch_plan_waves(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts& o) {
   const int lanes = sh.lanes > 0 ? sh.lanes : 1;
   const int block = sh.block > 0 ? sh.block : 512;
@@ -1029,10 +1038,24 @@ int batch_plan_waves(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts&
   const int count = B->count;
   SolverKind kind = solver_kind(mixed, sh.flags);
   BatchFn fnr = resident_batched_kernel_for(kind, lanes, block);
+  cudaFuncAttributes fa{};
+  bool can_res = !(sh.flags & 1) && cudaFuncGetAttributes(&fa, (const void*)fnr) == cudaSuccess;
+  if (!can_res) cudaGetLastError();
+  const size_t limit = can_res ? (size_t)std::max(0, optin_smem(B->device) - (int)fa.sharedSizeBytes - 1024) : 0;
+  const int rows = 256 << ((sh.flags >> 5) & 3);
   std::vector<int> nb(count), order(count);
   for (int i = 0; i < count; ++i) {
-    const int n = B->meshes[i]->n_c;
-    nb[i] = std::max(1, std::min(std::min(cap, B->meshes[i]->max_blocks), (n + 255) / 256));
+    const cgp_mesh_impl* m = B->meshes[i];
+    const int n = m->n_c;
+    int want = (n + rows - 1) / rows;
+    if (can_res && rows > 256) {
+      // the largest chunk whose rows leave a quarter of the shared memory to the halo
+      const int per_row = std::max(1, (m->nnz + n - 1) / std::max(1, n));
+      int c = std::min(n, rows);
+      while (c > 256 && res_smem_rows(kind, c, c * per_row) * 5 > limit * 4) c -= 64;
+      want = std::max(want, (n + c - 1) / c);
+    }
+    nb[i] = std::max(1, std::min(std::min(cap, m->max_blocks), want));
     order[i] = i;
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nb[a] > nb[b]; });
@@ -1048,10 +1071,18 @@ int batch_plan_waves(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts&
     groups[g].push_back(i);
     used[g] += nb[i];
   }
-  cudaFuncAttributes fa{};
-  bool can_res = !(sh.flags & 1) && cudaFuncGetAttributes(&fa, (const void*)fnr) == cudaSuccess;
-  if (!can_res) cudaGetLastError();
-  const size_t limit = can_res ? (size_t)std::max(0, optin_smem(B->device) - (int)fa.sharedSizeBytes - 1024) : 0;
+  // the wave whose largest instance is smallest runs first, so the small
+  // instances finish early (the order changes the latencies, not the total)
+  auto span = [&](const std::vector<int>& grp) {
+    double w = 0.0;
+    for (int i : grp) {
+      const cgp_mesh_impl* m = B->meshes[i];
+      w = std::max(w, (double)m->nnz * std::sqrt((double)m->n_c) / nb[i]);
+    }
+    return w;
+  };
+  std::stable_sort(groups.begin(), groups.end(),
+                   [&](const std::vector<int>& a, const std::vector<int>& b) { return span(a) < span(b); });
   std::vector<Desc> desc(count);
   std::vector<int> blk_inst;
   std::vector<cgp_batch_s::Wave> waves;
@@ -1067,8 +1098,7 @@ int batch_plan_waves(cgp_batch_s* B, const BatchShape& sh, const cgp_solve_opts&
       cgp_mesh_impl* m = B->meshes[i];
       const int chunk = (m->n_c + nb[i] - 1) / nb[i];
       const int rough_nnz = m->h_rowptr[std::min(m->n_c, chunk)] - m->h_rowptr[0];
-      if ((size_t)chunk * (kind == KIND_FP64_PIPE ? 96 : kind == KIND_FP64_SR ? 80 : 56) + (size_t)rough_nnz * 12 >
-          limit) {
+      if (res_smem_rows(kind, chunk, rough_nnz) > limit) {
         res = false;
         break;
       }
@@ -1340,7 +1370,7 @@ extern "C" int cgp_batch_create(const cgp_mesh* meshes, int count, const double*
 
 extern "C" int cgp_batch_set_tuning(cgp_batch batch, int block, int lanes, int blocks_per_sm, int flags) {
   if (!batch) return fail(CGP_ERR_INVALID_ARG, "cgp_batch_set_tuning: NULL batch");
-  if (!valid_shape(CGP_TUNE_SOLVE_FP64, block, lanes) || blocks_per_sm < 0 || (flags & ~31))
+  if (!valid_shape(CGP_TUNE_SOLVE_FP64, block, lanes) || blocks_per_sm < 0 || (flags & ~127))
     return fail(CGP_ERR_INVALID_ARG, "cgp_batch_set_tuning: bad shape");
   return batch_plan_any(batch, BatchShape{block, lanes, blocks_per_sm, flags}, batch->opts);
 }
@@ -1400,27 +1430,30 @@ extern "C" int cgp_batch_autotune(cgp_batch batch, void* stream, double* best_ms
   const int blocks[2] = {256, 512};
   const int lanes[2] = {1, 2};
   const int per_sm[2] = {1, 2};
+  const int rows[3] = {0, 2, 3};   // waves: 256, 1024 or 2048 rows a block (flags bits 5-6)
   const int nflags = batch->opts.precision == CGP_MIXED ? 2 : 4;
   for (int fl = 0; fl < 2 * nflags; ++fl)   // bit 2 (one packed launch instead of waves) on top
-    for (int bk : blocks)
-      for (int ln : lanes)
-        for (int ps : per_sm) {
-          BatchShape cand{bk, ln, ps, (fl % nflags) | (fl >= nflags ? 4 : 0)};
-          if (batch_plan_any(batch, cand, o) != CGP_OK) continue;
-          float t = 1e30f;
-          for (int rep = 0; rep < 2; ++rep) {
-            if (cudaEventRecord(e0, s) != cudaSuccess || batch_launch(batch, s) != CGP_OK ||
-                cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
-              break;
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            t = std::min(t, ms);
+    for (int rw : rows)
+      for (int bk : blocks)
+        for (int ln : lanes)
+          for (int ps : per_sm) {
+            if (rw && (fl >= nflags || ps > 1)) continue;   // more rows a block: waves, one block per SM
+            BatchShape cand{bk, ln, ps, (fl % nflags) | (fl >= nflags ? 4 : 0) | (rw << 5)};
+            if (batch_plan_any(batch, cand, o) != CGP_OK) continue;
+            float t = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+              if (cudaEventRecord(e0, s) != cudaSuccess || batch_launch(batch, s) != CGP_OK ||
+                  cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                break;
+              float ms = 0.0f;
+              cudaEventElapsedTime(&ms, e0, e1);
+              t = std::min(t, ms);
+            }
+            if (t < best_t) {
+              best_t = t;
+              best = cand;
+            }
           }
-          if (t < best_t) {
-            best_t = t;
-            best = cand;
-          }
-        }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best_t >= 1e29f) return fail(CGP_ERR_CUDA, "cgp_batch_autotune: no candidate ran");
