@@ -39,7 +39,13 @@ RHO_OVER_DT = 20.0
 L2_FLUSH_BYTES = 512 << 20
 SPMV_MESH = (3072, 1536)       # matrix + vectors: 490 MB FP64, 320 MB FP32 (L2 is 129 MB)
 KERNELS_PER_STEP = 8           # 2 x (restrict_rhs, persistent PCG, prolong, lorentz)
-PERM_KERNELS_PER_SOLVE = 2     # gather and scatter around a solve in the bisection row order (tuning flag bit 2)
+PERM_KERNELS_PER_SOLVE = 2     # gather and scatter around a solve in a renumbered row order
+
+
+def renumbered(flags, precision):
+    """Whether a solve with these tuning flags runs on renumbered rows: coordinate bisection (bit 2), or
+    the O-grid tiles of the FP64 single-reduction form (bit 5, the O-grid registered as here)."""
+    return bool(flags & 4) or (precision == "fp64" and bool(flags & 32) and not flags & 18)
 FP64_PEAK_TFLOPS = 1.25        # nominal dense FP64 of a GB300
 
 
@@ -227,8 +233,13 @@ def run_mine(args, rank, world, local_rank, refs_path=None):
     tune_x = torch.zeros(n, **f64)
     tuned = {}
     for prec in (cgp.CGP_FP64, cgp.CGP_MIXED):
-        best_ms = cgp.cgp_autotune(mesh.handle, prec, b, tune_x)
         what = cgp.CGP_TUNE_SOLVE_MIXED if prec == cgp.CGP_MIXED else cgp.CGP_TUNE_SOLVE_FP64
+        if args.tuning:   # a fixed launch shape for the benchmarked precision (profiler runs), no autotuning
+            if prec == precision:
+                cgp.cgp_set_tuning(mesh.handle, what, *args.tuning)
+                tuned["mixed" if prec else "fp64"] = dict(cgp.cgp_get_tuning(mesh.handle, what), ms=None)
+            continue
+        best_ms = cgp.cgp_autotune(mesh.handle, prec, b, tune_x)
         tuned["mixed" if prec else "fp64"] = dict(cgp.cgp_get_tuning(mesh.handle, what), ms=best_ms)
     del tune_x
 
@@ -1126,6 +1137,8 @@ def main():
     ap.add_argument("--no-spmv", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the other-precision and batched passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", type=lambda v: tuple(int(t) for t in v.split(",")), default=None,
+                    help="block,lanes,blocks,flags of the benchmarked precision's solves instead of autotuning")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-refs", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--ref-procs", type=int, default=0,
@@ -1203,8 +1216,8 @@ def main():
                     "timing": "one interval over all steps, from the first host-to-device copy to the last "
                               "device-to-host copy; step j+1's velocity in and step j's force and grad p out "
                               "on copy streams while steps compute (pinned host buffers)"},
-            "gpu_launches": (KERNELS_PER_STEP + (2 * PERM_KERNELS_PER_SOLVE if res["tuned"][args.precision]["flags"] & 4
-                                                 else 0)) * args.steps,
+            "gpu_launches": (KERNELS_PER_STEP + (2 * PERM_KERNELS_PER_SOLVE if renumbered(res["tuned"][args.precision]["flags"],
+                                                                                     args.precision) else 0)) * args.steps,
             "clocks": res["clocks"],
             "iterations": {"per_solve_mean": statistics.mean(res["its"]), "min": min(res["its"]),
                            "max": max(res["its"]), "rel_res_true_max": res["rel_res_true_max"]},

@@ -8,15 +8,21 @@
 //   h_i  = h_i + relu(Wu_l [h_i ; a_i] + bu_l)
 //   out  = Wd h + bd,   x0 = phi1 + s_d out         (the solver projects x0 to mean zero)
 //
-// The two dense layers of every message-passing step run on the tensor
-// cores as BF16 x BF16 -> FP32 mma.sync tiles (16 rows x 64 outputs per
-// warp), with the edge gather in the prologue and bias + ReLU + BF16
-// rounding in the epilogue.  Activations h, messages m, aggregates a and
-// the dense weights are stored in BF16; master weights, Adam moments,
-// gradients and every sum are FP32.  Aggregations and all gradient sums run
-// in a fixed order (no atomics), so training is deterministic.  Inference of
-// one sample (cgp_gnn_predict) is a single cooperative kernel with four grid
-// barriers instead of the dozen launches of the batched forward.
+// The message layer is linear in its three inputs, so with Wm_l = [A | B | C]
+// it is formed per node, not per edge: [P | Q] = h [A | B]^T on the tensor
+// cores (BF16 x BF16 -> FP32 mma.sync tiles), then m_ij = relu(P_i + Q_j +
+// C e_ij + bm) costs three FMAs per channel and is summed into a_i at once.
+// The update [h | a] Wu^T runs on the tensor cores the same way.  Its
+// backward is per node as well: dP_i is da_i times the count of the ReLU's
+// open in-edges, dQ_j a sum over the out-edges, and the weight gradients of
+// A and B are sums over node rows; only C's gradient visits the edges.
+// Activations h, messages m, aggregates a and the dense weights are stored
+// in BF16 (the messages only as they are summed); projections, master
+// weights, Adam moments, gradients and every sum are FP32.  Aggregations and
+// all gradient sums run in a fixed order (no atomics), so training is
+// deterministic.  Inference of one sample (cgp_gnn_predict) is a single
+// cooperative kernel with four grid barriers instead of the launches of the
+// batched forward.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -37,8 +43,8 @@ constexpr int FIN = 5;
 constexpr int KM = 2 * H + 3;       // message input width
 constexpr int KMP = 144;            // padded to a multiple of 16
 constexpr int KU = 2 * H;           // update input width
-constexpr int LDM = KMP + 8;        // smem row strides (bank spread)
-constexpr int LDU = KU + 8;
+constexpr int LDU = KU + 8;         // smem row strides (bank spread): update operands
+constexpr int LDP = H + 8;          // node-projection operands
 constexpr int TILE = 128;           // rows per tensor-core block (8 warps x 16)
 
 // parameter layout (FP32, row-major), identical to the oracle's order
@@ -271,71 +277,99 @@ __global__ void encode_kernel(int rows, const float* __restrict__ P, const float
   h0[t] = __float2bfloat16_rn(fmaxf(z, 0.0f));
 }
 
-// Messages of layer l for TILE directed edges (all samples stacked): gather
-// [h_dst | h_src | e | 0] into shared memory, tensor-core product with Wm,
-// bias, ReLU, BF16.
-__global__ void __launch_bounds__(256) message_fwd_kernel(int n, int E, int rows, const int* __restrict__ dst,
-                                                          const int* __restrict__ src, const bf16* __restrict__ ef,
-                                                          const bf16* __restrict__ h, const bf16* __restrict__ Wb,
-                                                          const float* __restrict__ bias, bf16* __restrict__ m) {
+// The message layer's product split by its inputs.  With Wm = [A | B | C]
+// (the columns that multiply h_i, h_j and e_ij), z_ij = P_i + Q_j + C e_ij + bm
+// where [P | Q] = h [A | B]^T is formed once per node instead of once per
+// edge; every message then costs three FMAs per channel.  Both forward paths
+// add the terms in this order.
+__device__ __forceinline__ float message_z(float p, float q, float e0, float e1, float e2, float c0, float c1,
+                                           float c2, float b) {
+  float z = p + q;
+  z = fmaf(c0, e0, z);
+  z = fmaf(c1, e1, z);
+  z = fmaf(c2, e2, z);
+  return z + b;
+}
+
+// Row o of [A; B] inside one layer's BF16 Wm ([H][KMP]): A's row o for o < H,
+// B's row o - H otherwise (K contiguous; the node projection's B operand).
+__device__ __forceinline__ const bf16* ab_row(const bf16* Wl, int o) { return Wl + (o % H) * KMP + (o / H) * H; }
+
+// [P | Q] = h [A | B]^T for TILE node rows (all samples stacked), FP32.
+__global__ void __launch_bounds__(256) project_kernel(int rows, const bf16* __restrict__ h, const bf16* __restrict__ Wb,
+                                                      float* __restrict__ pq) {
   extern __shared__ __align__(16) unsigned char smem[];
-  bf16* W = reinterpret_cast<bf16*>(smem);            // [H][LDM]
-  bf16* X = W + H * LDM;                              // [TILE][LDM]
+  bf16* W = reinterpret_cast<bf16*>(smem);            // [2H][LDP]
+  bf16* X = W + 2 * H * LDP;                          // [TILE][LDP]
   const int tid = threadIdx.x;
-  for (int i = tid; i < H * KMP / 8; i += blockDim.x) {
-    const int o = i / (KMP / 8), k8 = i % (KMP / 8);
-    *reinterpret_cast<uint4*>(W + o * LDM + k8 * 8) = *reinterpret_cast<const uint4*>(Wb + o * KMP + k8 * 8);
+  for (int i = tid; i < 2 * H * (H / 8); i += blockDim.x) {
+    const int o = i / (H / 8), k8 = i % (H / 8);
+    *reinterpret_cast<uint4*>(W + o * LDP + k8 * 8) = *reinterpret_cast<const uint4*>(ab_row(Wb, o) + k8 * 8);
   }
   const int r0 = blockIdx.x * TILE;
-  // 18 16-byte pieces per row: 8 of h_dst, 8 of h_src, 1 of edge features, 1 of zeros
-  for (int i = tid; i < TILE * 18; i += blockDim.x) {
-    const int rr = i / 18, piece = i % 18, r = r0 + rr;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (r < rows) {
-      const int s = r / E, e = r % E;
-      if (piece < 8) {
-        v = *reinterpret_cast<const uint4*>(h + ((size_t)s * n + dst[e]) * H + piece * 8);
-      } else if (piece < 16) {
-        v = *reinterpret_cast<const uint4*>(h + ((size_t)s * n + src[e]) * H + (piece - 8) * 8);
-      } else if (piece == 16) {
-        const uint2 q = *reinterpret_cast<const uint2*>(ef + 4 * (size_t)e);
-        v = make_uint4(q.x, q.y & 0xffffu, 0u, 0u);   // keep the three features, zero the pad
-      }
-    }
-    *reinterpret_cast<uint4*>(X + rr * LDM + piece * 8) = v;
+  for (int i = tid; i < TILE * (H / 8); i += blockDim.x) {
+    const int rr = i / (H / 8), piece = i % (H / 8), r = r0 + rr;
+    *reinterpret_cast<uint4*>(X + rr * LDP + piece * 8) =
+        r < rows ? *reinterpret_cast<const uint4*>(h + (size_t)r * H + piece * 8) : make_uint4(0u, 0u, 0u, 0u);
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
-  float acc[8][4];
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-  warp_tile_mma<KMP>(X + warp * 16 * LDM, LDM, W, LDM, acc);
+  for (int half_n = 0; half_n < 2; ++half_n) {   // P (outputs 0 .. H-1), then Q
+    float acc[8][4];
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int c = nt * 8 + tig * 2;
-    const float b0 = bias[c], b1 = bias[c + 1];
+    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+    warp_tile_mma<H>(X + warp * 16 * LDP, LDP, W + half_n * H * LDP, LDP, acc);
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int r = r0 + warp * 16 + gid + half * 8;
-      if (r < rows) {
-        __nv_bfloat162 v;
-        v.x = __float2bfloat16_rn(fmaxf(acc[nt][2 * half] + b0, 0.0f));
-        v.y = __float2bfloat16_rn(fmaxf(acc[nt][2 * half + 1] + b1, 0.0f));
-        *reinterpret_cast<__nv_bfloat162*>(m + (size_t)r * H + c) = v;
+    for (int nt = 0; nt < 8; ++nt) {
+      const int c = half_n * H + nt * 8 + tig * 2;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int r = r0 + warp * 16 + gid + half * 8;
+        if (r < rows) *reinterpret_cast<float2*>(pq + (size_t)r * 2 * H + c) = make_float2(acc[nt][2 * half], acc[nt][2 * half + 1]);
       }
     }
   }
 }
 
-// a_i = sum over the in-edges of i, in edge order (FP32 sum of BF16 messages), stored in BF16.
-__global__ void aggregate_kernel(int n, int E, int B, const int* __restrict__ in_ptr, const bf16* __restrict__ m,
-                                 bf16* __restrict__ a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= B * n * H) return;
-  const int c = t % H, node = (t / H) % n, s = t / (H * n);
-  float acc = 0.0f;
-  for (int e = in_ptr[node]; e < in_ptr[node + 1]; ++e) acc += __bfloat162float(m[((size_t)s * E + e) * H + c]);
-  a[t] = __float2bfloat16_rn(acc);
+// a_i = bf16(sum over the in-edges e = (i <- j), in edge order, of
+// bf16(relu(z_e))), z_e from message_z (FP32 sum of BF16 messages).  One warp
+// per node row, lanes on channels lane and lane + 32.  mask[e] keeps bit c
+// set where z_e[c] > 0 (the ReLU's derivative, for the backward).
+__global__ void message_agg_kernel(int n, int E, int rows, const int* __restrict__ in_ptr, const int* __restrict__ src,
+                                   const bf16* __restrict__ ef, const float* __restrict__ pq, const bf16* __restrict__ Wb,
+                                   const float* __restrict__ bias, bf16* __restrict__ a,
+                                   unsigned long long* __restrict__ mask) {
+  const int lane = threadIdx.x & 31;
+  const int r = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (r >= rows) return;
+  const int s = r / n, i = r % n;
+  float c[2][3], bm[2], p[2], acc[2] = {0.0f, 0.0f};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int ch = lane + 32 * q;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[q][k] = __bfloat162float(Wb[ch * KMP + 2 * H + k]);
+    bm[q] = bias[ch];
+    p[q] = pq[(size_t)r * 2 * H + ch];
+  }
+  const size_t nb = (size_t)s * n, eb = (size_t)s * E;
+  for (int e = in_ptr[i]; e < in_ptr[i + 1]; ++e) {
+    const float* qr = pq + (nb + src[e]) * 2 * H + H;
+    const float e0 = __bfloat162float(ef[4 * (size_t)e]), e1 = __bfloat162float(ef[4 * (size_t)e + 1]),
+                e2 = __bfloat162float(ef[4 * (size_t)e + 2]);
+    bool pos[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float z = message_z(p[q], qr[lane + 32 * q], e0, e1, e2, c[q][0], c[q][1], c[q][2], bm[q]);
+      pos[q] = z > 0.0f;
+      acc[q] += __bfloat162float(__float2bfloat16_rn(fmaxf(z, 0.0f)));
+    }
+    const unsigned lo = __ballot_sync(0xffffffffu, pos[0]), hi = __ballot_sync(0xffffffffu, pos[1]);
+    if (lane == 0) mask[eb + e] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) a[(size_t)r * H + lane + 32 * q] = __float2bfloat16_rn(acc[q]);
 }
 
 // Node update of layer l for TILE nodes: [h | a] x Wu on the tensor cores,
@@ -413,7 +447,6 @@ struct InferArgs {
   const double* phi1;
   const double* phi2;
   const double2* xy;
-  const int* dst;
   const int* src;
   const int* in_ptr;
   const bf16* ef;
@@ -421,8 +454,7 @@ struct InferArgs {
   const bf16* Wm;
   const bf16* Wu;
   bf16* h;        // [NL + 1][n][H]
-  bf16* msg;      // [E][H]
-  float* f;       // [n][FIN]
+  float* pq;      // [2][n][2H] node projections [P | Q], by layer parity
   double* part;   // [C][3]
   double* res;    // [n] residual b - K phi1 of the first phase
   double* scale;  // [1]
@@ -434,36 +466,53 @@ struct InferArgs {
 };
 
 // Layers and decoder work on node chunks of NT nodes (block b takes chunks b,
-// b + grid, ...); a chunk's in-edges are contiguous in CSR order and run
-// through the message tile 128 at a time, each message tile's rows added in
-// edge order into FP32 aggregates in shared memory.  The input scales use
-// the 128-row chunks of the shared reduction order.  Four grid barriers:
+// b + grid, ...).  The input scales use the 128-row chunks of the shared
+// reduction order.  Each phase ends with the node projections [P | Q] of the
+// layer that follows, so a layer reads only Q of its in-edges' sources (the
+// one value other chunks contribute) and its own P.  Four grid barriers:
 // after the scale partials, after the encoder and after each of the first
-// two layers (a layer reads the previous layer's h of neighbouring chunks;
-// the decoder only its own).  Every step runs the same arithmetic in the
-// same order as the batched kernels (features, encode, message_fwd,
-// aggregate, update_fwd, decode), so the result is the same bits.  A
-// barrier that gives up writes NaN to the block's x0 rows.
-constexpr int NT = 16;    // nodes per inference chunk (one 16-row update tile)
-constexpr int EIC = 256;  // in-edge indices of a chunk kept in shared memory (more are read from global)
-constexpr size_t kInferSmem = (size_t)NL * H * (LDM + LDU) * sizeof(bf16)   // all dense weights
-                              + (size_t)TILE * LDM * sizeof(bf16)         // message / update tile
-                              + (size_t)NT * H * sizeof(bf16)             // the chunk's own h
-                              + (size_t)NT * H * sizeof(float)            // FP32 aggregates
-                              + (size_t)2 * EIC * sizeof(int);            // dst, src of the chunk's in-edges
+// two layers.  Every step runs the same arithmetic in the same order as the
+// batched kernels (features, encode, project, message_agg, update_fwd,
+// decode), so the result is the same bits.  A barrier that gives up writes
+// NaN to the block's x0 rows.
+constexpr int NT = 16;    // nodes per inference chunk (one 16-row MMA tile)
+constexpr int EIC = 256;  // in-edge sources of a chunk kept in shared memory (more are read from global)
+constexpr size_t kInferSmem = (size_t)NL * 2 * H * LDP * sizeof(bf16)       // [A; B] of every layer
+                              + (size_t)NL * H * LDU * sizeof(bf16)         // Wu of every layer
+                              + (size_t)NT * LDU * sizeof(bf16)             // update tile [h | a]
+                              + (size_t)NT * LDP * sizeof(bf16)             // projection tile h
+                              + (size_t)EIC * sizeof(int);                  // sources of the chunk's in-edges
+
+// [P | Q] of the NT rows in Xh (stride LDP) with [A; B] at W: warp w forms
+// outputs 16w .. 16w + 15 (n-tiles 2w, 2w + 1 of project_kernel, same bits).
+__device__ __forceinline__ void chunk_project(const bf16* Xh, const bf16* W, int n0, int n1, float* __restrict__ pq) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int nt = 2 * warp + t;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    warp_tile_mma_nt<H>(Xh, LDP, W, LDP, nt, acc);
+    const int c = nt * 8 + tig * 2;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int node = n0 + gid + half * 8;
+      if (node < n1) *reinterpret_cast<float2*>(pq + (size_t)node * 2 * H + c) = make_float2(acc[2 * half], acc[2 * half + 1]);
+    }
+  }
+}
 
 __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
+  static_assert(2 * H / 16 == 8, "eight warps, two projection n-tiles each");
   extern __shared__ __align__(16) unsigned char smem[];
-  bf16* Wms = reinterpret_cast<bf16*>(smem);               // [NL][H][LDM]
-  bf16* Wus = Wms + NL * H * LDM;                          // [NL][H][LDU]
-  bf16* X = Wus + NL * H * LDU;                            // [TILE][LDM] or [NT][LDU]
-  bf16* Hs = X + TILE * LDM;                               // [NT][H]
-  float* agg = reinterpret_cast<float*>(Hs + NT * H);      // [NT][H]
-  int* dsts = reinterpret_cast<int*>(agg + NT * H);        // [EIC]
-  int* srcs = dsts + EIC;                                  // [EIC]
+  bf16* Wab = reinterpret_cast<bf16*>(smem);               // [NL][2H][LDP]
+  bf16* Wus = Wab + NL * 2 * H * LDP;                      // [NL][H][LDU]
+  bf16* X = Wus + NL * H * LDU;                            // [NT][LDU]: h | a of the update
+  bf16* Xh = X + NT * LDU;                                 // [NT][LDP]: h of the projection
+  int* srcs = reinterpret_cast<int*>(Xh + NT * LDP);       // [EIC]
   __shared__ double red[3 * 32];
   __shared__ double sc[3], isc[3];
   __shared__ float bias[NL][2][H];   // bm, bu of every layer
+  __shared__ float cm[NL][3][H];     // C of every layer (as its BF16 values)
   __shared__ int iptr[NT + 1];       // in-edge offsets of the (single) chunk
   __shared__ int ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
@@ -483,28 +532,32 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
     }
   };
   // all dense weights to shared memory once, by asynchronous 16-byte copies
-  // that complete while the first two phases run (waited for before layer 0)
+  // that complete while the first phase runs (waited for before the encoder's projection)
   {
-    constexpr int NM = NL * H * KMP / 8, NU = NL * H * KU / 8;
-    for (int i = tid; i < NM + NU; i += blockDim.x) {
-      const bf16* src;
+    constexpr int NP = NL * 2 * H * (H / 8), NU = NL * H * KU / 8;
+    for (int i = tid; i < NP + NU; i += blockDim.x) {
+      const bf16* srcp;
       bf16* dstp;
-      if (i < NM) {
-        const int lo = i / (KMP / 8), k8 = i % (KMP / 8);   // lo = layer * H + output
-        src = a.Wm + (size_t)i * 8;
-        dstp = Wms + lo * LDM + k8 * 8;
+      if (i < NP) {
+        const int lo = i / (H / 8), k8 = i % (H / 8);   // lo = layer * 2H + output
+        srcp = ab_row(a.Wm + (size_t)(lo / (2 * H)) * H * KMP, lo % (2 * H)) + k8 * 8;
+        dstp = Wab + lo * LDP + k8 * 8;
       } else {
-        const int j = i - NM, lo = j / (KU / 8), k8 = j % (KU / 8);
-        src = a.Wu + (size_t)j * 8;
+        const int j = i - NP, lo = j / (KU / 8), k8 = j % (KU / 8);
+        srcp = a.Wu + (size_t)j * 8;
         dstp = Wus + lo * LDU + k8 * 8;
       }
       const unsigned sa = (unsigned)__cvta_generic_to_shared(dstp);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(srcp) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     for (int i = tid; i < NL * 2 * H; i += blockDim.x) {
       const int l = i / (2 * H), w = (i / H) % 2, ch = i % H;
       bias[l][w][ch] = a.P[layer_off(l) + (w == 0 ? L_BM : L_BU) + ch];
+    }
+    for (int i = tid; i < NL * 3 * H; i += blockDim.x) {
+      const int l = i / (3 * H), k = (i / H) % 3, ch = i % H;
+      cm[l][k][ch] = __bfloat162float(a.Wm[(size_t)l * H * KMP + ch * KMP + 2 * H + k]);
     }
   }
   // ---- scale partials (128-row chunks) ----
@@ -513,51 +566,56 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
     if (tid < 3) a.part[c * 3 + tid] = sc[tid];
     __syncthreads();
   }
-  // a block with a single node chunk keeps its in-edge indices for all layers
+  // a block with a single node chunk keeps its in-edge sources for all layers
   const bool one_chunk = CN <= (int)gridDim.x;
   auto load_edges = [&](int c) {
     const int n0 = c * NT, cnt = min(NT, n - n0);
     if (tid <= cnt) iptr[tid] = a.in_ptr[n0 + tid];
     const int e0 = a.in_ptr[n0], e1 = a.in_ptr[n0 + cnt];
-    for (int e = e0 + tid; e < min(e1, e0 + EIC); e += blockDim.x) {
-      dsts[e - e0] = a.dst[e];
-      srcs[e - e0] = a.src[e];
-    }
+    for (int e = e0 + tid; e < min(e1, e0 + EIC); e += blockDim.x) srcs[e - e0] = a.src[e];
   };
   if (one_chunk && (int)blockIdx.x < CN) load_edges(blockIdx.x);
   if (!gsync()) { give_up(); return; }
   sample_scales(n, C, a.part, sc, isc);
   if (blockIdx.x == 0 && tid == 0) a.scale[0] = sc[1];
-  // ---- features and encoder of the block's node chunks ----
+  // ---- features, encoder and the first layer's projections of the block's node chunks ----
+  asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's weight copies; the barrier below shows all
   {
     const double ir = isc[0], id = isc[1], ib = isc[2];
     __shared__ float fs[NT * FIN];
     for (int c = blockIdx.x; c < CN; c += gridDim.x) {
-      const int i = c * NT + tid;
+      const int n0 = c * NT, n1 = min(n, n0 + NT), cnt = n1 - n0;
+      const int i = n0 + tid;
       if (tid < NT && i < n)
         features_row(i, __ldcg(a.res + i), a.b, a.phi1, a.phi2, nullptr, a.xy, ir, id, ib, fs + tid * FIN, nullptr);
-      __syncthreads();
-      const int cnt = min(NT, n - c * NT);
-      for (int t = tid; t < cnt * H; t += blockDim.x) {
+      __syncthreads();   // also orders every thread's weight copies before the projection
+      for (int t = tid; t < NT * H; t += blockDim.x) {
         const int rr = t / H, ch = t % H;
-        const float* w = a.P + OFF_WE + ch * FIN;
-        float z = a.P[OFF_BE + ch];
+        bf16 hv = __float2bfloat16_rn(0.0f);
+        if (rr < cnt) {
+          const float* w = a.P + OFF_WE + ch * FIN;
+          float z = a.P[OFF_BE + ch];
 #pragma unroll
-        for (int k = 0; k < FIN; ++k) z = fmaf(w[k], fs[rr * FIN + k], z);
-        a.h[(size_t)(c * NT + rr) * H + ch] = __float2bfloat16_rn(fmaxf(z, 0.0f));
+          for (int k = 0; k < FIN; ++k) z = fmaf(w[k], fs[rr * FIN + k], z);
+          hv = __float2bfloat16_rn(fmaxf(z, 0.0f));
+          a.h[(size_t)(n0 + rr) * H + ch] = hv;
+        }
+        Xh[rr * LDP + ch] = hv;
       }
+      __syncthreads();
+      chunk_project(Xh, Wab, n0, n1, a.pq);
       __syncthreads();
     }
   }
-  asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's weight copies; gsync makes all visible
   if (!gsync()) { give_up(); return; }
   // ---- message-passing layers ----
   for (int l = 0; l < NL; ++l) {
     const bf16* hin = a.h + (size_t)l * n * H;
     bf16* hout = a.h + (size_t)(l + 1) * n * H;
+    const float* pin = a.pq + (size_t)(l & 1) * n * 2 * H;
+    float* pout = a.pq + (size_t)((l + 1) & 1) * n * 2 * H;
     const float* bm = bias[l][0];
     const float* bu = bias[l][1];
-    const bf16* W = Wms + l * H * LDM;
     const bf16* Wu = Wus + l * H * LDU;
     for (int c = blockIdx.x; c < CN; c += gridDim.x) {
       const int n0 = c * NT, n1 = min(n, n0 + NT);
@@ -565,88 +623,31 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
         load_edges(c);
         __syncthreads();
       }
-      const int e0 = iptr[0], e1 = iptr[n1 - n0];
-      for (int i = tid; i < NT * H; i += blockDim.x) agg[i] = 0.0f;
-      // the chunk's own h rows, for the update: loaded now, stored with the first message tile
-      static_assert(NT * 8 <= 256, "one 16-byte piece of the chunk's rows per thread");
-      uint4 hsv = make_uint4(0u, 0u, 0u, 0u);
-      if (tid < NT * 8 && n0 + tid / 8 < n1) hsv = *reinterpret_cast<const uint4*>(hin + (size_t)(n0 + tid / 8) * H + (tid % 8) * 8);
-      bool hs_done = false;
-      // messages of the chunk's in-edges, TILE at a time, summed in edge order
-      for (int t0 = e0; t0 < e1; t0 += TILE) {
-        const int rows = min(TILE, e1 - t0);
-        {
-          constexpr int PER = TILE * 18 / 256;   // 16-byte pieces per thread, all loads in flight at once
-          uint4 v[PER];
-#pragma unroll
-          for (int q = 0; q < PER; ++q) {
-            const int i = q * 256 + tid, rr = i / 18, piece = i % 18, e = t0 + rr;
-            v[q] = make_uint4(0u, 0u, 0u, 0u);
-            if (rr < rows) {
-              const int el = e - e0;
-              if (piece < 8) {
-                const int j = el < EIC ? dsts[el] : a.dst[e];
-                v[q] = *reinterpret_cast<const uint4*>(hin + (size_t)j * H + piece * 8);
-              } else if (piece < 16) {
-                const int j = el < EIC ? srcs[el] : a.src[e];
-                v[q] = *reinterpret_cast<const uint4*>(hin + (size_t)j * H + (piece - 8) * 8);
-              } else if (piece == 16) {
-                const uint2 w2 = *reinterpret_cast<const uint2*>(a.ef + 4 * (size_t)e);
-                v[q] = make_uint4(w2.x, w2.y & 0xffffu, 0u, 0u);
-              }
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < PER; ++q) {
-            const int i = q * 256 + tid, rr = i / 18, piece = i % 18;
-            *reinterpret_cast<uint4*>(X + rr * LDM + piece * 8) = v[q];
-          }
-          if (!hs_done && tid < NT * 8) *reinterpret_cast<uint4*>(Hs + (tid / 8) * H + (tid % 8) * 8) = hsv;
-          hs_done = true;
-        }
-        __syncthreads();
-        if (warp * 16 < rows) {   // each warp reads and then overwrites only its own 16 rows
-          float acc[8][4];
-#pragma unroll
-          for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-          warp_tile_mma<KMP>(X + warp * 16 * LDM, LDM, W, LDM, acc);
-          __syncwarp();
-#pragma unroll
-          for (int nt = 0; nt < 8; ++nt) {
-            const int ch = nt * 8 + tig * 2;
-            const float b0 = bm[ch], b1 = bm[ch + 1];
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-              const int rr = warp * 16 + gid + half * 8;
-              __nv_bfloat162 v;
-              v.x = __float2bfloat16_rn(fmaxf(acc[nt][2 * half] + b0, 0.0f));
-              v.y = __float2bfloat16_rn(fmaxf(acc[nt][2 * half + 1] + b1, 0.0f));
-              *reinterpret_cast<__nv_bfloat162*>(X + rr * LDM + ch) = v;
-            }
-          }
-        }
-        __syncthreads();
-        // add this tile's messages into the aggregates of their destinations, in edge order
-        for (int i = tid; i < NT * H; i += blockDim.x) {
-          const int rr = i / H, ch = i % H, node = n0 + rr;
-          if (node < n1) {
-            const int lo = max(iptr[rr], t0), hi = min(iptr[rr + 1], t0 + rows);
-            float s = agg[i];
-            for (int e = lo; e < hi; ++e) s += __bfloat162float(X[(e - t0) * LDM + ch]);
-            agg[i] = s;
-          }
-        }
-        __syncthreads();
-      }
-      // update of the chunk's nodes: [h | bf16(a)] x Wu, warp w computing outputs 8w .. 8w+7
-      if (!hs_done && tid < NT * 8) *reinterpret_cast<uint4*>(Hs + (tid / 8) * H + (tid % 8) * 8) = hsv;
-      __syncthreads();   // Hs and agg complete (also when the chunk has no in-edges)
+      const int e0 = iptr[0];
+      // the chunk's own h rows (the update's first half) and the messages summed into a (second half)
       for (int i = tid; i < NT * 8; i += blockDim.x) {
         const int rr = i / 8, piece = i % 8;
-        *reinterpret_cast<uint4*>(X + rr * LDU + piece * 8) = *reinterpret_cast<const uint4*>(Hs + rr * H + piece * 8);
+        *reinterpret_cast<uint4*>(X + rr * LDU + piece * 8) =
+            n0 + rr < n1 ? *reinterpret_cast<const uint4*>(hin + (size_t)(n0 + rr) * H + piece * 8) : make_uint4(0u, 0u, 0u, 0u);
       }
-      for (int i = tid; i < NT * H; i += blockDim.x) X[(i / H) * LDU + H + (i % H)] = __float2bfloat16_rn(agg[i]);
+      for (int t = tid; t < NT * H; t += blockDim.x) {
+        const int rr = t / H, ch = t % H, node = n0 + rr;
+        float acc = 0.0f;
+        if (node < n1) {
+          const float p = pin[(size_t)node * 2 * H + ch], c0 = cm[l][0][ch], c1 = cm[l][1][ch], c2 = cm[l][2][ch];
+          for (int e = iptr[rr]; e < iptr[rr + 1]; ++e) {
+            const int el = e - e0;
+            const int j = el < EIC ? srcs[el] : a.src[e];
+            const float z = message_z(p, pin[(size_t)j * 2 * H + H + ch], __bfloat162float(a.ef[4 * (size_t)e]),
+                                      __bfloat162float(a.ef[4 * (size_t)e + 1]), __bfloat162float(a.ef[4 * (size_t)e + 2]),
+                                      c0, c1, c2, bm[ch]);
+            acc += __bfloat162float(__float2bfloat16_rn(fmaxf(z, 0.0f)));
+          }
+        }
+        X[rr * LDU + H + ch] = __float2bfloat16_rn(acc);
+      }
       __syncthreads();
+      // update of the chunk's nodes: [h | a] x Wu, warp w computing outputs 8w .. 8w+7
       {
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         warp_tile_mma_nt<KU>(X, LDU, Wu, LDU, warp, acc);
@@ -655,17 +656,20 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
           const int rr = gid + half * 8, node = n0 + rr;
-          if (node < n1) {
-            const float u0 = acc[2 * half] + b0, u1 = acc[2 * half + 1] + b1;
-            const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162*>(Hs + rr * H + ch);
-            __nv_bfloat162 o;
-            o.x = __float2bfloat16_rn(__bfloat162float(hv.x) + fmaxf(u0, 0.0f));
-            o.y = __float2bfloat16_rn(__bfloat162float(hv.y) + fmaxf(u1, 0.0f));
-            *reinterpret_cast<__nv_bfloat162*>(hout + (size_t)node * H + ch) = o;
-          }
+          const float u0 = acc[2 * half] + b0, u1 = acc[2 * half + 1] + b1;
+          const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162*>(X + rr * LDU + ch);
+          __nv_bfloat162 o;
+          o.x = __float2bfloat16_rn(__bfloat162float(hv.x) + fmaxf(u0, 0.0f));
+          o.y = __float2bfloat16_rn(__bfloat162float(hv.y) + fmaxf(u1, 0.0f));
+          if (node < n1) *reinterpret_cast<__nv_bfloat162*>(hout + (size_t)node * H + ch) = o;
+          *reinterpret_cast<__nv_bfloat162*>(Xh + rr * LDP + ch) = node < n1 ? o : __floats2bfloat162_rn(0.0f, 0.0f);
         }
       }
       __syncthreads();
+      if (l + 1 < NL) {   // the next layer's projections of the new h
+        chunk_project(Xh, Wab + (l + 1) * 2 * H * LDP, n0, n1, pout);
+        __syncthreads();
+      }
     }
     if (l + 1 < NL && !gsync()) { give_up(); return; }
   }
@@ -761,52 +765,70 @@ __global__ void update_bwd_kernel(int rows, const float* __restrict__ dh, const 
   }
 }
 
-// dz_e = da[dst] * [m_e > 0];  dx_e = dz_e Wm (first 2H inputs) for the node gathers.
-// One warp per edge row (grid-stride), four outputs per lane as in
-// update_bwd_kernel; Wm expanded once per block.
-__global__ void message_bwd_kernel(int n, int E, int rows, const int* __restrict__ dst, const float* __restrict__ da,
-                                   const bf16* __restrict__ m, const bf16* __restrict__ Wb, float* __restrict__ dz,
-                                   float* __restrict__ dxe) {
-  static_assert(KU == 4 * 32 && H == 2 * 32, "one warp per row, four outputs per lane");
+// Backward of the split message layer for one node row r = (s, i), one warp
+// per row (grid-stride), lanes on channels lane and lane + 32.  With
+// dz_e = da_dst(e) * [z_e > 0]:
+//   dP_i = sum over the in-edges of i of dz_e = da_i * (in-edges with z_e > 0),
+//   dQ_i = sum over the out-edges e of i, in edge order, of dz_e,
+//   dh_prev_i += dP_i A + dQ_i B  (A, B as their BF16 values),
+// and [dP | dQ] is kept for the weight gradients of A, B and bm.  A block
+// expands A and B to FP32 in shared memory once for all the rows it visits.
+constexpr size_t kMsgBwdSmem = (size_t)(H * 2 * H + 8 * 2 * H) * sizeof(float);   // A, B in FP32; 8 warps' dP | dQ
+__global__ void message_bwd_kernel(int n, int E, int rows, const int* __restrict__ in_ptr,
+                                   const int* __restrict__ out_ptr, const int* __restrict__ out_edge,
+                                   const int* __restrict__ dst, const unsigned long long* __restrict__ mask,
+                                   const float* __restrict__ da, const bf16* __restrict__ Wb, float* __restrict__ dpq,
+                                   float* __restrict__ dh_prev) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* Wf = reinterpret_cast<float*>(smem);          // [H][2H] (the h_i, h_j inputs)
-  for (int i = threadIdx.x; i < H * KU; i += blockDim.x) Wf[i] = __bfloat162float(Wb[(i / KU) * KMP + i % KU]);
+  float* Wf = reinterpret_cast<float*>(smem);            // [H][2H]: A's row o, then B's row o
+  float* sd = Wf + H * 2 * H;                            // [warps][2H]: the warp's dP | dQ
+  for (int i = threadIdx.x; i < H * 2 * H; i += blockDim.x) Wf[i] = __bfloat162float(Wb[(i / (2 * H)) * KMP + i % (2 * H)]);
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  float* mine = sd + (threadIdx.x >> 5) * 2 * H;
   const size_t total = (size_t)rows * 32;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(t / 32);
-    const int s = r / E, e = r % E;
-    const float* dar = da + ((size_t)s * n + dst[e]) * H;
-    const bf16* mr = m + (size_t)r * H;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int o = 0; o < H; ++o) {
-      const float g = __bfloat162float(mr[o]) > 0.0f ? dar[o] : 0.0f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(g, Wf[o * KU + lane + 32 * q], acc[q]);
+    const int s = r / n, i = r % n;
+    const size_t nb = (size_t)s * n, eb = (size_t)s * E;
+    float dp[2], dq[2] = {0.0f, 0.0f};
+    int cnt[2] = {0, 0};
+    for (int e = in_ptr[i]; e < in_ptr[i + 1]; ++e) {
+      const unsigned long long mk = mask[eb + e];
+      cnt[0] += (int)((mk >> lane) & 1ull);
+      cnt[1] += (int)((mk >> (lane + 32)) & 1ull);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dxe[(size_t)r * KU + lane + 32 * q] = acc[q];
+    for (int q = 0; q < 2; ++q) dp[q] = da[((size_t)r) * H + lane + 32 * q] * (float)cnt[q];
+    for (int k = out_ptr[i]; k < out_ptr[i + 1]; ++k) {
+      const int e = out_edge[k];
+      const unsigned long long mk = mask[eb + e];
+      const float* dar = da + (nb + dst[e]) * H;
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if ((mk >> (lane + 32 * q)) & 1ull) dq[q] += dar[lane + 32 * q];
+    }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const int k = lane + 32 * q;
-      dz[(size_t)r * H + k] = __bfloat162float(mr[k]) > 0.0f ? dar[k] : 0.0f;
+      mine[lane + 32 * q] = dp[q];
+      mine[H + lane + 32 * q] = dq[q];
+      dpq[(size_t)r * 2 * H + lane + 32 * q] = dp[q];
+      dpq[(size_t)r * 2 * H + H + lane + 32 * q] = dq[q];
     }
+    __syncwarp();
+    float acc[2] = {0.0f, 0.0f};
+    for (int o = 0; o < H; ++o) {
+      const float gp = mine[o], gq = mine[H + o];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        acc[q] = fmaf(gp, Wf[o * 2 * H + lane + 32 * q], acc[q]);
+        acc[q] = fmaf(gq, Wf[o * 2 * H + H + lane + 32 * q], acc[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) dh_prev[(size_t)r * H + lane + 32 * q] += acc[q];
+    __syncwarp();
   }
-}
-
-// dh_prev[i] += sum over in-edges of dx_e[:, 0:H] + sum over out-edges of dx_e[:, H:2H]
-__global__ void message_gather_kernel(int n, int E, int B, const int* __restrict__ in_ptr,
-                                      const int* __restrict__ out_ptr, const int* __restrict__ out_edge,
-                                      const float* __restrict__ dxe, float* __restrict__ dh_prev) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= B * n * H) return;
-  const int c = t % H, node = (t / H) % n, s = t / (H * n);
-  const size_t eb = (size_t)s * E;
-  float acc = dh_prev[t];
-  for (int e = in_ptr[node]; e < in_ptr[node + 1]; ++e) acc += dxe[(eb + e) * KU + c];
-  for (int q = out_ptr[node]; q < out_ptr[node + 1]; ++q) acc += dxe[(eb + out_edge[q]) * KU + H + c];
-  dh_prev[t] = acc;
 }
 
 __global__ void encode_bwd_kernel(int rows, const float* __restrict__ dh, const float* __restrict__ z0,
@@ -817,15 +839,16 @@ __global__ void encode_bwd_kernel(int rows, const float* __restrict__ dh, const 
 }
 
 // Weight gradient partials: for a chunk of ROWS rows, G[o][k] = sum_r D[r][o] X[r][k]
-// and G[o][K] = sum_r D[r][o] (the bias); X rows come from `load_x`.
+// and G[o][K] = sum_r D[r][o] (the bias); D and X entries come from `load_d`
+// and `load_x`.
 constexpr int WG_ROWS = 128;
 // shared-memory row stride of the inputs of a weight-gradient chunk (KX
 // inputs and the bias column, padded to 16-byte rows) and the chunk's bytes
 __host__ __device__ constexpr int wg_xs(int KX) { return (KX + 1 + 3) / 4 * 4; }
 constexpr size_t wg_smem(int KX, int NO) { return (size_t)WG_ROWS * (NO + wg_xs(KX)) * sizeof(float); }
 
-template <int KX, int NO, typename LoadX>
-__device__ void wgrad_chunk(int rows, const float* __restrict__ D, LoadX load_x, float* __restrict__ part) {
+template <int KX, int NO, typename LoadD, typename LoadX>
+__device__ void wgrad_chunk(int rows, LoadD load_d, LoadX load_x, float* __restrict__ part) {
   constexpr int XS = wg_xs(KX);
   extern __shared__ __align__(16) unsigned char smem[];
   float* Ds = reinterpret_cast<float*>(smem);          // [WG_ROWS][NO]
@@ -833,7 +856,7 @@ __device__ void wgrad_chunk(int rows, const float* __restrict__ D, LoadX load_x,
   const int r0 = blockIdx.x * WG_ROWS;
   for (int i = threadIdx.x; i < WG_ROWS * NO; i += blockDim.x) {
     const int rr = i / NO, o = i % NO, r = r0 + rr;
-    Ds[i] = r < rows ? D[(size_t)r * NO + o] : 0.0f;
+    Ds[i] = r < rows ? load_d(r, o) : 0.0f;
   }
   for (int i = threadIdx.x; i < WG_ROWS * XS; i += blockDim.x) {
     const int rr = i / XS, k = i % XS, r = r0 + rr;
@@ -880,22 +903,28 @@ __device__ void wgrad_chunk(int rows, const float* __restrict__ D, LoadX load_x,
   }
 }
 
-__global__ void wgrad_message_kernel(int n, int E, int rows, const int* __restrict__ dst, const int* __restrict__ src,
-                                     const bf16* __restrict__ ef, const bf16* __restrict__ h,
-                                     const float* __restrict__ dz, float* __restrict__ part) {
-  wgrad_chunk<KM, H>(rows, dz,
-                     [&](int r, int k) -> float {
-                       const int s = r / E, e = r % E;
-                       if (k < H) return __bfloat162float(h[((size_t)s * n + dst[e]) * H + k]);
-                       if (k < 2 * H) return __bfloat162float(h[((size_t)s * n + src[e]) * H + k - H]);
-                       return __bfloat162float(ef[4 * (size_t)e + (k - 2 * H)]);
-                     },
-                     part);
+// Gradients of A, B and bm over node rows: D = [dP | dQ], X = h.
+__global__ void wgrad_project_kernel(int rows, const bf16* __restrict__ h, const float* __restrict__ dpq,
+                                     float* __restrict__ part) {
+  wgrad_chunk<H, 2 * H>(rows, [&](int r, int o) -> float { return dpq[(size_t)r * 2 * H + o]; },
+                        [&](int r, int k) -> float { return __bfloat162float(h[(size_t)r * H + k]); }, part);
+}
+
+// Gradient of C over edge rows: D = dz_e = da_dst(e) * [z_e > 0], X = e_ij.
+__global__ void wgrad_edge_kernel(int n, int E, int rows, const int* __restrict__ dst, const bf16* __restrict__ ef,
+                                  const unsigned long long* __restrict__ mask, const float* __restrict__ da,
+                                  float* __restrict__ part) {
+  wgrad_chunk<3, H>(rows,
+                    [&](int r, int o) -> float {
+                      const int s = r / E, e = r % E;
+                      return ((mask[r] >> o) & 1ull) ? da[((size_t)s * n + dst[e]) * H + o] : 0.0f;
+                    },
+                    [&](int r, int k) -> float { return __bfloat162float(ef[4 * (size_t)(r % E) + k]); }, part);
 }
 
 __global__ void wgrad_update_kernel(int rows, const bf16* __restrict__ h, const bf16* __restrict__ a,
                                     const float* __restrict__ du, float* __restrict__ part) {
-  wgrad_chunk<KU, H>(rows, du,
+  wgrad_chunk<KU, H>(rows, [&](int r, int o) -> float { return du[(size_t)r * H + o]; },
                      [&](int r, int k) -> float {
                        return k < H ? __bfloat162float(h[(size_t)r * H + k]) : __bfloat162float(a[(size_t)r * H + k - H]);
                      },
@@ -904,19 +933,20 @@ __global__ void wgrad_update_kernel(int rows, const bf16* __restrict__ h, const 
 
 __global__ void wgrad_encode_kernel(int rows, const float* __restrict__ f, const float* __restrict__ dz0,
                                     float* __restrict__ part) {
-  wgrad_chunk<FIN, H>(rows, dz0, [&](int r, int k) -> float { return f[(size_t)r * FIN + k]; }, part);
+  wgrad_chunk<FIN, H>(rows, [&](int r, int o) -> float { return dz0[(size_t)r * H + o]; },
+                      [&](int r, int k) -> float { return f[(size_t)r * FIN + k]; }, part);
 }
 
 __global__ void wgrad_decode_kernel(int rows, const bf16* __restrict__ h, const float* __restrict__ dout,
                                     float* __restrict__ part) {
-  wgrad_chunk<H, 1>(rows, dout, [&](int r, int k) -> float { return __bfloat162float(h[(size_t)r * H + k]); },
-                    part);
+  wgrad_chunk<H, 1>(rows, [&](int r, int) -> float { return dout[r]; },
+                    [&](int r, int k) -> float { return __bfloat162float(h[(size_t)r * H + k]); }, part);
 }
 
 // Sum the chunk partials in chunk order into the gradient vector: G[o][k] at
-// gw + o*KX + k for k < KX, the bias column at gb + o.
+// gw + o*ldg + k for k < KX, the bias column at gb + o (dropped when gb < 0).
 __global__ void wgrad_reduce_kernel(int chunks, int NO, int KX, const float* __restrict__ part, float* __restrict__ G,
-                                    int gw, int gb) {
+                                    int gw, int ldg, int gb) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int per = NO * (KX + 1);
   if (j >= per) return;
@@ -924,9 +954,27 @@ __global__ void wgrad_reduce_kernel(int chunks, int NO, int KX, const float* __r
   for (int c = 0; c < chunks; ++c) s += part[(size_t)c * per + j];
   const int o = j / (KX + 1), k = j % (KX + 1);
   if (k < KX)
-    G[gw + o * KX + k] = s;
-  else
+    G[gw + o * ldg + k] = s;
+  else if (gb >= 0)
     G[gb + o] = s;
+}
+
+// The partials of wgrad_project_kernel into layer `off`'s Wm (columns 0 .. H-1
+// from dP, H .. 2H-1 from dQ) and bm (the bias column of dP: every edge is the
+// in-edge of one node, so sum_i dP_i = sum_e dz_e).
+__global__ void wgrad_reduce_project_kernel(int chunks, const float* __restrict__ part, float* __restrict__ G, int off) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = 2 * H * (H + 1);
+  if (j >= per) return;
+  float s = 0.0f;
+  for (int c = 0; c < chunks; ++c) s += part[(size_t)c * per + j];
+  const int o = j / (H + 1), k = j % (H + 1);
+  if (o < H) {
+    if (k < H) G[off + L_WM + o * KM + k] = s;
+    else G[off + L_BM + o] = s;
+  } else if (k < H) {
+    G[off + L_WM + (o - H) * KM + H + k] = s;
+  }
 }
 
 // Adam on the FP32 master weights (bias-corrected moments).
@@ -979,8 +1027,10 @@ struct cgp_gnn_s {
   // activations and gradients (max_batch samples)
   float *f = nullptr, *z0 = nullptr, *u = nullptr, *out = nullptr, *target = nullptr, *dout = nullptr, *loss = nullptr;
   double* scale = nullptr;
-  bf16 *h = nullptr, *msg = nullptr, *agg = nullptr;
-  float *dh = nullptr, *dh2 = nullptr, *du = nullptr, *da = nullptr, *dz = nullptr, *dxe = nullptr, *part = nullptr;
+  bf16 *h = nullptr, *agg = nullptr;
+  unsigned long long* mask = nullptr;  // [NL][batch][E] ReLU masks of the messages
+  float* pq = nullptr;                 // [max(batch, 2)][n][2H] node projections [P | Q]
+  float *dh = nullptr, *dh2 = nullptr, *du = nullptr, *da = nullptr, *dpq = nullptr, *part = nullptr;
   size_t part_floats = 0;
   double* fpart = nullptr;        // [max_batch][C][3] partial sums of the input scales
   double* rres = nullptr;         // [n] fused inference: residual b - K phi1
@@ -1007,15 +1057,14 @@ int gnn_forward(cgp_gnn_s* g, int B, const double* b, const double* phi1, const 
   features_rows_kernel<<<B * C, 256, 0, s>>>(n, C, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, phi_t, xy,
                                              g->fpart, g->f, g->scale, g->target);
   encode_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, g->P, g->f, g->z0, g->h);
-  const size_t smem_m = (size_t)(H + TILE) * LDM * sizeof(bf16), smem_u = (size_t)(H + TILE) * LDU * sizeof(bf16);
+  const size_t smem_p = (size_t)(2 * H + TILE) * LDP * sizeof(bf16), smem_u = (size_t)(H + TILE) * LDU * sizeof(bf16);
   for (int l = 0; l < NL; ++l) {
     const bf16* hl = g->h + (size_t)l * rn * H;
-    bf16* ml = g->msg + (size_t)l * re * H;
+    const bf16* Wl = g->Wm + (size_t)l * H * KMP;
     bf16* al_ = g->agg + (size_t)l * rn * H;
-    message_fwd_kernel<<<(re + TILE - 1) / TILE, 256, smem_m, s>>>(n, E, re, g->dst, g->src, g->ef, hl,
-                                                                   g->Wm + (size_t)l * H * KMP,
-                                                                   g->P + layer_off(l) + L_BM, ml);
-    aggregate_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(n, E, B, g->in_ptr, ml, al_);
+    project_kernel<<<(rn + TILE - 1) / TILE, 256, smem_p, s>>>(rn, hl, Wl, g->pq);
+    message_agg_kernel<<<(unsigned)(((size_t)rn * 32 + 255) / 256), 256, 0, s>>>(
+        n, E, rn, g->in_ptr, g->src, g->ef, g->pq, Wl, g->P + layer_off(l) + L_BM, al_, g->mask + (size_t)l * re);
     update_fwd_kernel<<<(rn + TILE - 1) / TILE, 256, smem_u, s>>>(rn, hl, al_, g->Wu + (size_t)l * H * KU,
                                                                   g->P + layer_off(l) + L_BU,
                                                                   g->u + (size_t)l * rn * H,
@@ -1034,7 +1083,7 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
     const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
     const size_t sm = wg_smem(H, 1);
     wgrad_decode_kernel<<<chunks, 256, sm, s>>>(rn, g->h + (size_t)NL * rn * H, g->dout, g->part);
-    wgrad_reduce_kernel<<<1, 128, 0, s>>>(chunks, 1, H, g->part, g->G, OFF_WD, OFF_BD);
+    wgrad_reduce_kernel<<<1, 128, 0, s>>>(chunks, 1, H, g->part, g->G, OFF_WD, H, OFF_BD);
     decode_bwd_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, g->P, g->dout, g->dh);
   }
   float* dh = g->dh;
@@ -1042,7 +1091,8 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
   for (int l = NL - 1; l >= 0; --l) {
     const bf16* hl = g->h + (size_t)l * rn * H;
     const bf16* al_ = g->agg + (size_t)l * rn * H;
-    const bf16* ml = g->msg + (size_t)l * re * H;
+    const unsigned long long* mk = g->mask + (size_t)l * re;
+    const bf16* Wl = g->Wm + (size_t)l * H * KMP;
     const float* ul = g->u + (size_t)l * rn * H;
     const int off = layer_off(l);
     // node update
@@ -1052,21 +1102,22 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
       const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
       const size_t sm = wg_smem(KU, H);
       wgrad_update_kernel<<<chunks, 256, sm, s>>>(rn, hl, al_, g->du, g->part);
-      wgrad_reduce_kernel<<<(H * (KU + 1) + 255) / 256, 256, 0, s>>>(chunks, H, KU, g->part, g->G, off + L_WU,
+      wgrad_reduce_kernel<<<(H * (KU + 1) + 255) / 256, 256, 0, s>>>(chunks, H, KU, g->part, g->G, off + L_WU, KU,
                                                                     off + L_BU);
     }
-    // messages
-    message_bwd_kernel<<<bwd_grid((size_t)re * 32), 256, (size_t)H * KU * sizeof(float), s>>>(
-        n, E, re, g->dst, g->da, ml, g->Wm + (size_t)l * H * KMP, g->dz, g->dxe);
+    // messages: dP, dQ and dh_prev += dP A + dQ B per node, then the gradients of A, B, bm (node rows) and C (edge rows)
+    message_bwd_kernel<<<bwd_grid((size_t)rn * 32), 256, kMsgBwdSmem, s>>>(n, E, rn, g->in_ptr, g->out_ptr, g->out_edge,
+                                                                         g->dst, mk, g->da, Wl, g->dpq, dh_prev);
+    {
+      const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
+      wgrad_project_kernel<<<chunks, 256, wg_smem(H, 2 * H), s>>>(rn, hl, g->dpq, g->part);
+      wgrad_reduce_project_kernel<<<(2 * H * (H + 1) + 255) / 256, 256, 0, s>>>(chunks, g->part, g->G, off);
+    }
     {
       const int chunks = (re + WG_ROWS - 1) / WG_ROWS;
-      const size_t sm = wg_smem(KM, H);
-      wgrad_message_kernel<<<chunks, 256, sm, s>>>(n, E, re, g->dst, g->src, g->ef, hl, g->dz, g->part);
-      wgrad_reduce_kernel<<<(H * (KM + 1) + 255) / 256, 256, 0, s>>>(chunks, H, KM, g->part, g->G, off + L_WM,
-                                                                    off + L_BM);
+      wgrad_edge_kernel<<<chunks, 256, wg_smem(3, H), s>>>(n, E, re, g->dst, g->ef, mk, g->da, g->part);
+      wgrad_reduce_kernel<<<(H * 4 + 255) / 256, 256, 0, s>>>(chunks, H, 3, g->part, g->G, off + L_WM + 2 * H, KM, -1);
     }
-    message_gather_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(n, E, B, g->in_ptr, g->out_ptr, g->out_edge, g->dxe,
-                                                               dh_prev);
     std::swap(dh, dh_prev);
   }
   // encoder
@@ -1075,7 +1126,8 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
     const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
     const size_t sm = wg_smem(FIN, H);
     wgrad_encode_kernel<<<chunks, 256, sm, s>>>(rn, g->f, g->du, g->part);
-    wgrad_reduce_kernel<<<(H * (FIN + 1) + 255) / 256, 256, 0, s>>>(chunks, H, FIN, g->part, g->G, OFF_WE, OFF_BE);
+    wgrad_reduce_kernel<<<(H * (FIN + 1) + 255) / 256, 256, 0, s>>>(chunks, H, FIN, g->part, g->G, OFF_WE, FIN,
+                                                                     OFF_BE);
   }
   CGP_CUDA(cudaGetLastError());
   return CGP_OK;
@@ -1137,9 +1189,10 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
                o_Wm = take((size_t)NL * H * KMP * 2), o_Wu = take((size_t)NL * H * KU * 2), o_f = take(rn * FIN * 4),
                o_z0 = take(rn * H * 4), o_u = take((size_t)NL * rn * H * 4), o_out = take(rn * 4),
                o_t = take(rn * 4), o_do = take(rn * 4), o_loss = take(8), o_sc = take(B * 8),
-               o_h = take((size_t)(NL + 1) * rn * H * 2), o_msg = take((size_t)NL * re * H * 2),
-               o_agg = take((size_t)NL * rn * H * 2), o_dh = take(rn * H * 4), o_dh2 = take(rn * H * 4),
-               o_du = take(rn * H * 4), o_da = take(rn * H * 4), o_dz = take(re * H * 4), o_dxe = take(re * KU * 4),
+               o_h = take((size_t)(NL + 1) * rn * H * 2), o_mask = take((size_t)NL * re * 8),
+               o_pq = take(std::max<size_t>(B, 2) * n * 2 * H * 4), o_agg = take((size_t)NL * rn * H * 2),
+               o_dh = take(rn * H * 4), o_dh2 = take(rn * H * 4), o_du = take(rn * H * 4), o_da = take(rn * H * 4),
+               o_dpq = take(rn * 2 * H * 4),
                o_part = take(g->part_floats * 4), o_fpart = take(B * (size_t)((n + TILE - 1) / TILE) * 3 * 8),
                o_ictrl = take(256), o_rres = take((size_t)n * 8);
   g->bytes = off;
@@ -1171,14 +1224,14 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   g->loss = (float*)(bs + o_loss);
   g->scale = (double*)(bs + o_sc);
   g->h = (bf16*)(bs + o_h);
-  g->msg = (bf16*)(bs + o_msg);
+  g->mask = (unsigned long long*)(bs + o_mask);
+  g->pq = (float*)(bs + o_pq);
   g->agg = (bf16*)(bs + o_agg);
   g->dh = (float*)(bs + o_dh);
   g->dh2 = (float*)(bs + o_dh2);
   g->du = (float*)(bs + o_du);
   g->da = (float*)(bs + o_da);
-  g->dz = (float*)(bs + o_dz);
-  g->dxe = (float*)(bs + o_dxe);
+  g->dpq = (float*)(bs + o_dpq);
   g->part = (float*)(bs + o_part);
   g->fpart = (double*)(bs + o_fpart);
   g->ictrl = (unsigned char*)(bs + o_ictrl);
@@ -1201,12 +1254,13 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   edge_length_kernel<<<1, 1024>>>(E, g->dst, g->src, xy, g->ell);
   edge_feature_kernel<<<(E + 255) / 256, 256>>>(E, g->dst, g->src, xy, g->ell, g->ef);
   st = refresh(g, 0);
-  if (st == CGP_OK) st = smem_optin((const void*)message_fwd_kernel, (size_t)(H + TILE) * LDM * sizeof(bf16));
+  if (st == CGP_OK) st = smem_optin((const void*)project_kernel, (size_t)(2 * H + TILE) * LDP * sizeof(bf16));
   if (st == CGP_OK) st = smem_optin((const void*)update_fwd_kernel, (size_t)(H + TILE) * LDU * sizeof(bf16));
-  if (st == CGP_OK) st = smem_optin((const void*)wgrad_message_kernel, wg_smem(KM, H));
+  if (st == CGP_OK) st = smem_optin((const void*)wgrad_project_kernel, wg_smem(H, 2 * H));
+  if (st == CGP_OK) st = smem_optin((const void*)wgrad_edge_kernel, wg_smem(3, H));
   if (st == CGP_OK) st = smem_optin((const void*)wgrad_update_kernel, wg_smem(KU, H));
   if (st == CGP_OK) st = smem_optin((const void*)update_bwd_kernel, (size_t)H * KU * sizeof(float));
-  if (st == CGP_OK) st = smem_optin((const void*)message_bwd_kernel, (size_t)H * KU * sizeof(float));
+  if (st == CGP_OK) st = smem_optin((const void*)message_bwd_kernel, kMsgBwdSmem);
   if (st == CGP_OK) st = smem_optin((const void*)infer_kernel, kInferSmem);
   if (st == CGP_OK) {
     int per_sm = 0, sms = 0;
@@ -1268,7 +1322,6 @@ extern "C" int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, c
   a.phi1 = phi1;
   a.phi2 = phi2;
   a.xy = reinterpret_cast<const double2*>(g->m->xy_c);
-  a.dst = g->dst;
   a.src = g->src;
   a.in_ptr = g->in_ptr;
   a.ef = g->ef;
@@ -1276,8 +1329,7 @@ extern "C" int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, c
   a.Wm = g->Wm;
   a.Wu = g->Wu;
   a.h = g->h;
-  a.msg = g->msg;
-  a.f = g->f;
+  a.pq = g->pq;
   a.part = g->fpart;
   a.res = g->rres;
   a.scale = g->scale;
