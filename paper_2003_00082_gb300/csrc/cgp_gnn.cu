@@ -460,6 +460,9 @@ struct InferArgs {
   double* scale;  // [1]
   float* out;     // [n]
   double* x0;     // [n]
+  const int* nbr_ptr;  // [CN + 1] chunks holding the in-edge sources of each chunk (itself excluded)
+  const int* nbr;
+  unsigned* flags;     // [CN] phase whose projections each chunk has published
   unsigned* bar;
   int* timeout;
   long long spin_ns;
@@ -469,14 +472,19 @@ struct InferArgs {
 // b + grid, ...).  The input scales use the 128-row chunks of the shared
 // reduction order.  Each phase ends with the node projections [P | Q] of the
 // layer that follows, so a layer reads only Q of its in-edges' sources (the
-// one value other chunks contribute) and its own P.  Four grid barriers:
-// after the scale partials, after the encoder and after each of the first
-// two layers.  Every step runs the same arithmetic in the same order as the
-// batched kernels (features, encode, project, message_agg, update_fwd,
-// decode), so the result is the same bits.  A barrier that gives up writes
-// NaN to the block's x0 rows.
+// one value other chunks contribute) and its own P.  One grid barrier, after
+// the scale partials; after that a chunk publishes a flag (release) when its
+// projections for the next layer are stored, and a layer waits only for the
+// flags of the chunks that hold its in-edges' sources (acquire).  Since the
+// edges are symmetric, those are also the chunks that read its own
+// projections, so a chunk overwrites the buffer of two phases back only after
+// its readers have finished with it.  Every step runs the same arithmetic in
+// the same order as the batched kernels (features, encode, project,
+// message_agg, update_fwd, decode), so the result is the same bits.  A wait
+// that gives up writes NaN to the block's x0 rows.
 constexpr int NT = 16;    // nodes per inference chunk (one 16-row MMA tile)
 constexpr int EIC = 256;  // in-edge sources of a chunk kept in shared memory (more are read from global)
+constexpr int EU = 8;     // in-edges of a node whose loads are issued together
 constexpr size_t kInferSmem = (size_t)NL * 2 * H * LDP * sizeof(bf16)       // [A; B] of every layer
                               + (size_t)NL * H * LDU * sizeof(bf16)         // Wu of every layer
                               + (size_t)NT * LDU * sizeof(bf16)             // update tile [h | a]
@@ -499,6 +507,29 @@ __device__ __forceinline__ void chunk_project(const bf16* Xh, const bf16* W, int
       if (node < n1) *reinterpret_cast<float2*>(pq + (size_t)node * 2 * H + c) = make_float2(acc[2 * half], acc[2 * half + 1]);
     }
   }
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *f >= target (acquire), giving up after spin_ns or when another block gave up.
+__device__ __forceinline__ bool flag_wait(const unsigned* f, unsigned target, int* timeout, long long spin_ns) {
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+  while (ld_acquire(f) < target) {
+    if ((++spins & 127u) == 0) {
+      if (*(volatile int*)timeout) return false;
+      const unsigned long long now = global_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if ((long long)(now - t0) > spin_ns) {
+        atomicExch(timeout, 1);
+        return false;
+      }
+    }
+  }
+  return true;
 }
 
 __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
@@ -524,6 +555,20 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
     if (tid == 0) ok = barrier_arrive_wait(a.bar, a.timeout, gridDim.x, epoch, a.spin_ns) ? 1 : 0;
     __syncthreads();
     return ok != 0;
+  };
+  // the flags of chunk c's source chunks reach `target` (threads poll one each); false when a wait gave up
+  auto wait_sources = [&](int c, unsigned target) -> bool {
+    if (tid == 0) ok = 1;
+    __syncthreads();
+    for (int k = a.nbr_ptr[c] + tid; k < a.nbr_ptr[c + 1]; k += blockDim.x)
+      if (!flag_wait(a.flags + a.nbr[k], target, a.timeout, a.spin_ns)) ok = 0;
+    __syncthreads();
+    return ok != 0;
+  };
+  // after the chunk's projections are stored by every thread: publish them
+  auto publish = [&](int c, unsigned phase) {
+    __syncthreads();
+    if (tid == 0) st_release(a.flags + c, phase);
   };
   auto give_up = [&]() {
     for (int c = blockIdx.x; c < CN; c += gridDim.x) {
@@ -604,10 +649,9 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
       }
       __syncthreads();
       chunk_project(Xh, Wab, n0, n1, a.pq);
-      __syncthreads();
+      publish(c, 1);
     }
   }
-  if (!gsync()) { give_up(); return; }
   // ---- message-passing layers ----
   for (int l = 0; l < NL; ++l) {
     const bf16* hin = a.h + (size_t)l * n * H;
@@ -623,6 +667,7 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
         load_edges(c);
         __syncthreads();
       }
+      if (!wait_sources(c, l + 1)) { give_up(); return; }
       const int e0 = iptr[0];
       // the chunk's own h rows (the update's first half) and the messages summed into a (second half)
       for (int i = tid; i < NT * 8; i += blockDim.x) {
@@ -630,21 +675,45 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
         *reinterpret_cast<uint4*>(X + rr * LDU + piece * 8) =
             n0 + rr < n1 ? *reinterpret_cast<const uint4*>(hin + (size_t)(n0 + rr) * H + piece * 8) : make_uint4(0u, 0u, 0u, 0u);
       }
-      for (int t = tid; t < NT * H; t += blockDim.x) {
-        const int rr = t / H, ch = t % H, node = n0 + rr;
-        float acc = 0.0f;
+      {   // thread (node rr, channels c4 .. c4 + 3); the loads of up to EU in-edges are issued together
+        static_assert(NT * H / 4 == 256, "one (node, four channels) item per thread of a 256-thread block");
+        const int rr = tid >> 4, c4 = (tid & 15) * 4, node = n0 + rr;
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         if (node < n1) {
-          const float p = pin[(size_t)node * 2 * H + ch], c0 = cm[l][0][ch], c1 = cm[l][1][ch], c2 = cm[l][2][ch];
-          for (int e = iptr[rr]; e < iptr[rr + 1]; ++e) {
-            const int el = e - e0;
-            const int j = el < EIC ? srcs[el] : a.src[e];
-            const float z = message_z(p, pin[(size_t)j * 2 * H + H + ch], __bfloat162float(a.ef[4 * (size_t)e]),
-                                      __bfloat162float(a.ef[4 * (size_t)e + 1]), __bfloat162float(a.ef[4 * (size_t)e + 2]),
-                                      c0, c1, c2, bm[ch]);
-            acc += __bfloat162float(__float2bfloat16_rn(fmaxf(z, 0.0f)));
+          const float4 p4 = *reinterpret_cast<const float4*>(pin + (size_t)node * 2 * H + c4);
+          const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
+          const int ea = iptr[rr], eb = iptr[rr + 1];
+          for (int eu = ea; eu < eb; eu += EU) {
+            float4 qv[EU];
+            uint2 ev[EU];
+#pragma unroll
+            for (int u = 0; u < EU; ++u) {
+              const int e = eu + u;
+              if (e < eb) {
+                const int el = e - e0;
+                const int j = el < EIC ? srcs[el] : a.src[e];
+                qv[u] = *reinterpret_cast<const float4*>(pin + (size_t)j * 2 * H + H + c4);
+                ev[u] = *reinterpret_cast<const uint2*>(a.ef + 4 * (size_t)e);
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < EU; ++u) {
+              if (eu + u < eb) {
+                const bf16* eh = reinterpret_cast<const bf16*>(&ev[u]);
+                const float ex = __bfloat162float(eh[0]), ey = __bfloat162float(eh[1]), ez = __bfloat162float(eh[2]);
+                const float qq[4] = {qv[u].x, qv[u].y, qv[u].z, qv[u].w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                  const int ch = c4 + k;
+                  const float z = message_z(pp[k], qq[k], ex, ey, ez, cm[l][0][ch], cm[l][1][ch], cm[l][2][ch], bm[ch]);
+                  acc[k] += __bfloat162float(__float2bfloat16_rn(fmaxf(z, 0.0f)));
+                }
+              }
+            }
           }
         }
-        X[rr * LDU + H + ch] = __float2bfloat16_rn(acc);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) X[rr * LDU + H + c4 + k] = __float2bfloat16_rn(acc[k]);
       }
       __syncthreads();
       // update of the chunk's nodes: [h | a] x Wu, warp w computing outputs 8w .. 8w+7
@@ -668,10 +737,10 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
       __syncthreads();
       if (l + 1 < NL) {   // the next layer's projections of the new h
         chunk_project(Xh, Wab + (l + 1) * 2 * H * LDP, n0, n1, pout);
-        __syncthreads();
+        publish(c, l + 2);
       }
+      __syncthreads();
     }
-    if (l + 1 < NL && !gsync()) { give_up(); return; }
   }
   // ---- decoder of the block's own nodes ----
   const bf16* hl = a.h + (size_t)NL * n * H;
@@ -725,6 +794,9 @@ __global__ void decode_bwd_kernel(int rows, const float* __restrict__ P, const f
 // Blocks of the grid-stride backward kernels: enough to fill the GPU (a few
 // per SM at 32 KB of shared memory each), no more, so each block expands its
 // weight matrix once for many rows.
+// blocks of the partial-sum reductions: one per 32 outputs
+inline unsigned reduce_grid(int outputs) { return (unsigned)((outputs + 31) / 32); }
+
 inline unsigned bwd_grid(size_t threads) {
   const size_t need = (threads + 255) / 256;
   return (unsigned)(need < 1024 ? (need > 0 ? need : 1) : 1024);
@@ -771,35 +843,52 @@ __global__ void update_bwd_kernel(int rows, const float* __restrict__ dh, const 
 //   dP_i = sum over the in-edges of i of dz_e = da_i * (in-edges with z_e > 0),
 //   dQ_i = sum over the out-edges e of i, in edge order, of dz_e,
 //   dh_prev_i += dP_i A + dQ_i B  (A, B as their BF16 values),
-// and [dP | dQ] is kept for the weight gradients of A, B and bm.  A block
-// expands A and B to FP32 in shared memory once for all the rows it visits.
-constexpr size_t kMsgBwdSmem = (size_t)(H * 2 * H + 8 * 2 * H) * sizeof(float);   // A, B in FP32; 8 warps' dP | dQ
+// and [dP | dQ] is kept for the weight gradients of A, B and bm.  C's
+// gradient sum_e dz_e e_e^T = sum_i da_i (sum over the open in-edges of e_e)
+// is summed per warp over the rows it visits, then per block in warp order
+// into dc_part[block][H][4] (fourth column zero).  A block expands A and B to FP32 in shared
+// memory once for all the rows it visits.
+constexpr size_t kMsgBwdSmem = (size_t)(H * 2 * H + 8 * 3 * H) * sizeof(float);   // A, B in FP32; 8 warps' dP | dQ or dC
 __global__ void message_bwd_kernel(int n, int E, int rows, const int* __restrict__ in_ptr,
                                    const int* __restrict__ out_ptr, const int* __restrict__ out_edge,
                                    const int* __restrict__ dst, const unsigned long long* __restrict__ mask,
-                                   const float* __restrict__ da, const bf16* __restrict__ Wb, float* __restrict__ dpq,
-                                   float* __restrict__ dh_prev) {
+                                   const bf16* __restrict__ ef, const float* __restrict__ da,
+                                   const bf16* __restrict__ Wb, float* __restrict__ dpq, float* __restrict__ dh_prev,
+                                   float* __restrict__ dc_part) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* Wf = reinterpret_cast<float*>(smem);            // [H][2H]: A's row o, then B's row o
-  float* sd = Wf + H * 2 * H;                            // [warps][2H]: the warp's dP | dQ
+  float* sd = Wf + H * 2 * H;                            // [warps][3H]: the warp's dP | dQ; at the end its dC [H][3]
   for (int i = threadIdx.x; i < H * 2 * H; i += blockDim.x) Wf[i] = __bfloat162float(Wb[(i / (2 * H)) * KMP + i % (2 * H)]);
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  float* mine = sd + (threadIdx.x >> 5) * 2 * H;
+  float* mine = sd + (threadIdx.x >> 5) * 3 * H;
+  float dc[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
   const size_t total = (size_t)rows * 32;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(t / 32);
     const int s = r / n, i = r % n;
     const size_t nb = (size_t)s * n, eb = (size_t)s * E;
-    float dp[2], dq[2] = {0.0f, 0.0f};
+    float dp[2], dq[2] = {0.0f, 0.0f}, se[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
     int cnt[2] = {0, 0};
     for (int e = in_ptr[i]; e < in_ptr[i + 1]; ++e) {
       const unsigned long long mk = mask[eb + e];
-      cnt[0] += (int)((mk >> lane) & 1ull);
-      cnt[1] += (int)((mk >> (lane + 32)) & 1ull);
+      const uint2 ev = *reinterpret_cast<const uint2*>(ef + 4 * (size_t)e);
+      const bf16* eh = reinterpret_cast<const bf16*>(&ev);
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if ((mk >> (lane + 32 * q)) & 1ull) {
+          ++cnt[q];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) se[q][k] += __bfloat162float(eh[k]);
+        }
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) dp[q] = da[((size_t)r) * H + lane + 32 * q] * (float)cnt[q];
+    for (int q = 0; q < 2; ++q) {
+      const float g = da[((size_t)r) * H + lane + 32 * q];
+      dp[q] = g * (float)cnt[q];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dc[q][k] = fmaf(g, se[q][k], dc[q][k]);
+    }
     for (int k = out_ptr[i]; k < out_ptr[i + 1]; ++k) {
       const int e = out_edge[k];
       const unsigned long long mk = mask[eb + e];
@@ -828,6 +917,20 @@ __global__ void message_bwd_kernel(int n, int E, int rows, const int* __restrict
 #pragma unroll
     for (int q = 0; q < 2; ++q) dh_prev[(size_t)r * H + lane + 32 * q] += acc[q];
     __syncwarp();
+  }
+  // the block's dC ([H][4], the fourth column zero): warps' sums added in warp order
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) mine[(lane + 32 * q) * 3 + k] = dc[q][k];
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int j = threadIdx.x; j < H * 4; j += blockDim.x) {
+    const int o = j / 4, k = j % 4;
+    float t = 0.0f;
+    if (k < 3)
+      for (int w = 0; w < nw; ++w) t += sd[w * 3 * H + o * 3 + k];
+    dc_part[(size_t)blockIdx.x * H * 4 + j] = t;
   }
 }
 
@@ -910,18 +1013,6 @@ __global__ void wgrad_project_kernel(int rows, const bf16* __restrict__ h, const
                         [&](int r, int k) -> float { return __bfloat162float(h[(size_t)r * H + k]); }, part);
 }
 
-// Gradient of C over edge rows: D = dz_e = da_dst(e) * [z_e > 0], X = e_ij.
-__global__ void wgrad_edge_kernel(int n, int E, int rows, const int* __restrict__ dst, const bf16* __restrict__ ef,
-                                  const unsigned long long* __restrict__ mask, const float* __restrict__ da,
-                                  float* __restrict__ part) {
-  wgrad_chunk<3, H>(rows,
-                    [&](int r, int o) -> float {
-                      const int s = r / E, e = r % E;
-                      return ((mask[r] >> o) & 1ull) ? da[((size_t)s * n + dst[e]) * H + o] : 0.0f;
-                    },
-                    [&](int r, int k) -> float { return __bfloat162float(ef[4 * (size_t)(r % E) + k]); }, part);
-}
-
 __global__ void wgrad_update_kernel(int rows, const bf16* __restrict__ h, const bf16* __restrict__ a,
                                     const float* __restrict__ du, float* __restrict__ part) {
   wgrad_chunk<KU, H>(rows, [&](int r, int o) -> float { return du[(size_t)r * H + o]; },
@@ -943,15 +1034,34 @@ __global__ void wgrad_decode_kernel(int rows, const bf16* __restrict__ h, const 
                     [&](int r, int k) -> float { return __bfloat162float(h[(size_t)r * H + k]); }, part);
 }
 
-// Sum the chunk partials in chunk order into the gradient vector: G[o][k] at
-// gw + o*ldg + k for k < KX, the bias column at gb + o (dropped when gb < 0).
+// Sum of the chunk partials of output j (of `per`), the same order every
+// time: warp w of a block adds chunks w, w + 8, ... for 32 consecutive
+// outputs (coalesced), and the eight warp sums are added in warp order.
+// Every thread of the block must call it; returns the total on warp 0's
+// lanes for the output j = blockIdx.x * 32 + lane.
+__device__ __forceinline__ float reduce_chunks(int chunks, int per, const float* __restrict__ part) {
+  __shared__ float ws[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, j = blockIdx.x * 32 + lane;
+  float s = 0.0f;
+  if (j < per)
+    for (int c = w; c < chunks; c += 8) s += part[(size_t)c * per + j];
+  ws[w][lane] = s;
+  __syncthreads();
+  float t = 0.0f;
+  if (w == 0)
+    for (int q = 0; q < 8; ++q) t += ws[q][lane];
+  return t;
+}
+
+// Sum the chunk partials into the gradient vector: G[o][k] at gw + o*ldg + k
+// for k < KX, the bias column at gb + o (dropped when gb < 0).  Blocks of 256
+// threads, one per 32 outputs.
 __global__ void wgrad_reduce_kernel(int chunks, int NO, int KX, const float* __restrict__ part, float* __restrict__ G,
                                     int gw, int ldg, int gb) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int per = NO * (KX + 1);
-  if (j >= per) return;
-  float s = 0.0f;
-  for (int c = 0; c < chunks; ++c) s += part[(size_t)c * per + j];
+  const float s = reduce_chunks(chunks, per, part);
+  const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (threadIdx.x >= 32 || j >= per) return;
   const int o = j / (KX + 1), k = j % (KX + 1);
   if (k < KX)
     G[gw + o * ldg + k] = s;
@@ -963,11 +1073,10 @@ __global__ void wgrad_reduce_kernel(int chunks, int NO, int KX, const float* __r
 // from dP, H .. 2H-1 from dQ) and bm (the bias column of dP: every edge is the
 // in-edge of one node, so sum_i dP_i = sum_e dz_e).
 __global__ void wgrad_reduce_project_kernel(int chunks, const float* __restrict__ part, float* __restrict__ G, int off) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int per = 2 * H * (H + 1);
-  if (j >= per) return;
-  float s = 0.0f;
-  for (int c = 0; c < chunks; ++c) s += part[(size_t)c * per + j];
+  const float s = reduce_chunks(chunks, per, part);
+  const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (threadIdx.x >= 32 || j >= per) return;
   const int o = j / (H + 1), k = j % (H + 1);
   if (o < H) {
     if (k < H) G[off + L_WM + o * KM + k] = s;
@@ -1034,7 +1143,9 @@ struct cgp_gnn_s {
   size_t part_floats = 0;
   double* fpart = nullptr;        // [max_batch][C][3] partial sums of the input scales
   double* rres = nullptr;         // [n] fused inference: residual b - K phi1
-  unsigned char* ictrl = nullptr; // fused inference: barrier counter and timeout word
+  unsigned char* ictrl = nullptr; // fused inference: barrier counter, timeout word, then the chunk flags
+  size_t ictrl_bytes = 0;
+  int *nbr_ptr = nullptr, *nbr = nullptr;  // fused inference: source chunks of every node chunk
   int infer_grid = 0;             // co-resident blocks of the fused inference kernel (capped by the chunk count)
 };
 
@@ -1083,7 +1194,7 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
     const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
     const size_t sm = wg_smem(H, 1);
     wgrad_decode_kernel<<<chunks, 256, sm, s>>>(rn, g->h + (size_t)NL * rn * H, g->dout, g->part);
-    wgrad_reduce_kernel<<<1, 128, 0, s>>>(chunks, 1, H, g->part, g->G, OFF_WD, H, OFF_BD);
+    wgrad_reduce_kernel<<<reduce_grid(H + 1), 256, 0, s>>>(chunks, 1, H, g->part, g->G, OFF_WD, H, OFF_BD);
     decode_bwd_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, g->P, g->dout, g->dh);
   }
   float* dh = g->dh;
@@ -1102,21 +1213,21 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
       const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
       const size_t sm = wg_smem(KU, H);
       wgrad_update_kernel<<<chunks, 256, sm, s>>>(rn, hl, al_, g->du, g->part);
-      wgrad_reduce_kernel<<<(H * (KU + 1) + 255) / 256, 256, 0, s>>>(chunks, H, KU, g->part, g->G, off + L_WU, KU,
+      wgrad_reduce_kernel<<<reduce_grid(H * (KU + 1)), 256, 0, s>>>(chunks, H, KU, g->part, g->G, off + L_WU, KU,
                                                                     off + L_BU);
     }
-    // messages: dP, dQ and dh_prev += dP A + dQ B per node, then the gradients of A, B, bm (node rows) and C (edge rows)
-    message_bwd_kernel<<<bwd_grid((size_t)rn * 32), 256, kMsgBwdSmem, s>>>(n, E, rn, g->in_ptr, g->out_ptr, g->out_edge,
-                                                                         g->dst, mk, g->da, Wl, g->dpq, dh_prev);
+    // messages: dP, dQ and dh_prev += dP A + dQ B per node with C's gradient partials, then the
+    // gradients of C (block partials) and of A, B, bm (node rows)
+    {
+      const unsigned grid = bwd_grid((size_t)rn * 32);
+      message_bwd_kernel<<<grid, 256, kMsgBwdSmem, s>>>(n, E, rn, g->in_ptr, g->out_ptr, g->out_edge, g->dst, mk,
+                                                        g->ef, g->da, Wl, g->dpq, dh_prev, g->part);
+      wgrad_reduce_kernel<<<reduce_grid(H * 4), 256, 0, s>>>((int)grid, H, 3, g->part, g->G, off + L_WM + 2 * H, KM, -1);
+    }
     {
       const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
       wgrad_project_kernel<<<chunks, 256, wg_smem(H, 2 * H), s>>>(rn, hl, g->dpq, g->part);
-      wgrad_reduce_project_kernel<<<(2 * H * (H + 1) + 255) / 256, 256, 0, s>>>(chunks, g->part, g->G, off);
-    }
-    {
-      const int chunks = (re + WG_ROWS - 1) / WG_ROWS;
-      wgrad_edge_kernel<<<chunks, 256, wg_smem(3, H), s>>>(n, E, re, g->dst, g->ef, mk, g->da, g->part);
-      wgrad_reduce_kernel<<<(H * 4 + 255) / 256, 256, 0, s>>>(chunks, H, 3, g->part, g->G, off + L_WM + 2 * H, KM, -1);
+      wgrad_reduce_project_kernel<<<reduce_grid(2 * H * (H + 1)), 256, 0, s>>>(chunks, g->part, g->G, off);
     }
     std::swap(dh, dh_prev);
   }
@@ -1126,7 +1237,7 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
     const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
     const size_t sm = wg_smem(FIN, H);
     wgrad_encode_kernel<<<chunks, 256, sm, s>>>(rn, g->f, g->du, g->part);
-    wgrad_reduce_kernel<<<(H * (FIN + 1) + 255) / 256, 256, 0, s>>>(chunks, H, FIN, g->part, g->G, OFF_WE, FIN,
+    wgrad_reduce_kernel<<<reduce_grid(H * (FIN + 1)), 256, 0, s>>>(chunks, H, FIN, g->part, g->G, OFF_WE, FIN,
                                                                      OFF_BE);
   }
   CGP_CUDA(cudaGetLastError());
@@ -1167,6 +1278,18 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   }
   const int E = (int)dst.size();
   for (int e = 0; e < E; ++e) out_cnt[src[e] + 1]++;
+  // chunks of NT nodes holding the in-edge sources of each chunk of the fused inference (itself excluded)
+  const int CN = (n + NT - 1) / NT;
+  std::vector<int> nbr_ptr(CN + 1, 0), nbr;
+  for (int c = 0; c < CN; ++c) {
+    std::vector<int> cs;
+    for (int e = in_ptr[c * NT]; e < in_ptr[std::min(n, c * NT + NT)]; ++e)
+      if (src[e] / NT != c) cs.push_back(src[e] / NT);
+    std::sort(cs.begin(), cs.end());
+    cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+    nbr.insert(nbr.end(), cs.begin(), cs.end());
+    nbr_ptr[c + 1] = (int)nbr.size();
+  }
   std::vector<int> out_ptr(n + 1, 0), out_edge(E), fillp(n, 0);
   for (int i = 0; i < n; ++i) out_ptr[i + 1] = out_ptr[i] + out_cnt[i + 1];
   for (int e = 0; e < E; ++e) out_edge[out_ptr[src[e]] + fillp[src[e]]++] = e;   // ascending e per source
@@ -1194,7 +1317,8 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
                o_dh = take(rn * H * 4), o_dh2 = take(rn * H * 4), o_du = take(rn * H * 4), o_da = take(rn * H * 4),
                o_dpq = take(rn * 2 * H * 4),
                o_part = take(g->part_floats * 4), o_fpart = take(B * (size_t)((n + TILE - 1) / TILE) * 3 * 8),
-               o_ictrl = take(256), o_rres = take((size_t)n * 8);
+               o_ictrl = take(256 + (size_t)CN * 4), o_rres = take((size_t)n * 8),
+               o_nptr = take((size_t)(CN + 1) * 4), o_nbr = take(std::max<size_t>(1, nbr.size()) * 4);
   g->bytes = off;
   cudaError_t e = cudaMalloc(&g->base, g->bytes);
   if (e != cudaSuccess) {
@@ -1235,6 +1359,9 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   g->part = (float*)(bs + o_part);
   g->fpart = (double*)(bs + o_fpart);
   g->ictrl = (unsigned char*)(bs + o_ictrl);
+  g->ictrl_bytes = 256 + (size_t)CN * 4;
+  g->nbr_ptr = (int*)(bs + o_nptr);
+  g->nbr = (int*)(bs + o_nbr);
   g->rres = (double*)(bs + o_rres);
   auto up = [&](void* d, const void* h, size_t bytes) -> int {
     cudaError_t ee = cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice);
@@ -1243,7 +1370,9 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   int st = CGP_OK;
   if ((st = up(g->dst, dst.data(), E * 4)) || (st = up(g->src, src.data(), E * 4)) ||
       (st = up(g->in_ptr, in_ptr.data(), (n + 1) * 4)) || (st = up(g->out_ptr, out_ptr.data(), (n + 1) * 4)) ||
-      (st = up(g->out_edge, out_edge.data(), E * 4)) || (st = up(g->P, params, NPARAM * 4))) {
+      (st = up(g->out_edge, out_edge.data(), E * 4)) || (st = up(g->P, params, NPARAM * 4)) ||
+      (st = up(g->nbr_ptr, nbr_ptr.data(), (CN + 1) * 4)) ||
+      (!nbr.empty() && (st = up(g->nbr, nbr.data(), nbr.size() * 4)))) {
     cgp_gnn_destroy(g);
     return st;
   }
@@ -1257,7 +1386,6 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   if (st == CGP_OK) st = smem_optin((const void*)project_kernel, (size_t)(2 * H + TILE) * LDP * sizeof(bf16));
   if (st == CGP_OK) st = smem_optin((const void*)update_fwd_kernel, (size_t)(H + TILE) * LDU * sizeof(bf16));
   if (st == CGP_OK) st = smem_optin((const void*)wgrad_project_kernel, wg_smem(H, 2 * H));
-  if (st == CGP_OK) st = smem_optin((const void*)wgrad_edge_kernel, wg_smem(3, H));
   if (st == CGP_OK) st = smem_optin((const void*)wgrad_update_kernel, wg_smem(KU, H));
   if (st == CGP_OK) st = smem_optin((const void*)update_bwd_kernel, (size_t)H * KU * sizeof(float));
   if (st == CGP_OK) st = smem_optin((const void*)message_bwd_kernel, kMsgBwdSmem);
@@ -1335,10 +1463,13 @@ extern "C" int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, c
   a.scale = g->scale;
   a.out = g->out;
   a.x0 = x0;
+  a.nbr_ptr = g->nbr_ptr;
+  a.nbr = g->nbr;
+  a.flags = reinterpret_cast<unsigned*>(g->ictrl + 256);
   a.bar = reinterpret_cast<unsigned*>(g->ictrl);
   a.timeout = reinterpret_cast<int*>(g->ictrl + 128);
   a.spin_ns = 2000000000LL;
-  CGP_CUDA(cudaMemsetAsync(g->ictrl, 0, 256, s));
+  CGP_CUDA(cudaMemsetAsync(g->ictrl, 0, g->ictrl_bytes, s));
   void* args[] = {&a};
   CGP_CUDA(cudaLaunchCooperativeKernel((const void*)infer_kernel, dim3(g->infer_grid), dim3(256), args, kInferSmem, s));
   return CGP_OK;
