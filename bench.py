@@ -46,6 +46,8 @@ def renumbered(flags, precision):
     """Whether a solve with these tuning flags runs on renumbered rows: coordinate bisection (bit 2), or
     the O-grid tiles of the FP64 single-reduction form (bit 5, the O-grid registered as here)."""
     return bool(flags & 4) or (precision == "fp64" and bool(flags & 32) and not flags & 18)
+
+
 FP64_PEAK_TFLOPS = 1.25        # nominal dense FP64 of a GB300
 
 

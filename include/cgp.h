@@ -221,12 +221,11 @@ int cgp_poisson_solve_async(cgp_mesh m, const double* b, double* x, const cgp_so
  * CGP_ERR_INVALID_ARG.  Only opts->precision == CGP_FP64 is accepted.
  *
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  The address is kept together with the identity of the device's
- * CUDA context, so the first call after the caller resets the device
- * (cudaDeviceReset) looks it up again.  All calls share the one array:
- * calls that overlap on the GPU race on it, so serialise them (one stream,
- * one host thread at a time).
+ * device, with that device current).  The address is kept together with the
+ * identity of the device's CUDA context, so the first call after the caller
+ * resets the device (cudaDeviceReset) looks it up again.  All calls share the
+ * one array: calls that overlap on the GPU race on it, so serialise them (one
+ * stream, one host thread at a time).
  * info behaves as in cgp_poisson_solve (NULL: asynchronous).
  */
 #define CGP_STATIC_MAX_ROWS 65536

@@ -45,6 +45,7 @@ constexpr int KMP = 144;            // padded to a multiple of 16
 constexpr int KU = 2 * H;           // update input width
 constexpr int LDU = KU + 8;         // smem row strides (bank spread): update operands
 constexpr int LDP = H + 8;          // node-projection operands
+constexpr int kInferWElems = NL * 2 * H * LDP + NL * H * LDU;   // the fused inference's weight image (BF16)
 constexpr int TILE = 128;           // rows per tensor-core block (8 warps x 16)
 
 // parameter layout (FP32, row-major), identical to the oracle's order
@@ -452,7 +453,7 @@ struct InferArgs {
   const bf16* ef;
   const float* P;
   const bf16* Wm;
-  const bf16* Wu;
+  const bf16* Winf;   // kInferWElems: the shared-memory image of [A; B] and Wu
   bf16* h;        // [NL + 1][n][H]
   float* pq;      // [2][n][2H] node projections [P | Q], by layer parity
   double* part;   // [C][3]
@@ -485,8 +486,7 @@ struct InferArgs {
 constexpr int NT = 16;    // nodes per inference chunk (one 16-row MMA tile)
 constexpr int EIC = 256;  // in-edge sources of a chunk kept in shared memory (more are read from global)
 constexpr int EU = 8;     // in-edges of a node whose loads are issued together
-constexpr size_t kInferSmem = (size_t)NL * 2 * H * LDP * sizeof(bf16)       // [A; B] of every layer
-                              + (size_t)NL * H * LDU * sizeof(bf16)         // Wu of every layer
+constexpr size_t kInferSmem = (size_t)kInferWElems * sizeof(bf16)           // [A; B] and Wu of every layer
                               + (size_t)NT * LDU * sizeof(bf16)             // update tile [h | a]
                               + (size_t)NT * LDP * sizeof(bf16)             // projection tile h
                               + (size_t)EIC * sizeof(int);                  // sources of the chunk's in-edges
@@ -505,6 +505,36 @@ __device__ __forceinline__ void chunk_project(const bf16* Xh, const bf16* W, int
     for (int half = 0; half < 2; ++half) {
       const int node = n0 + gid + half * 8;
       if (node < n1) *reinterpret_cast<float2*>(pq + (size_t)node * 2 * H + c) = make_float2(acc[2 * half], acc[2 * half + 1]);
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// One bulk copy global -> shared of `bytes` (addresses 16-byte aligned, a
+// multiple of 16 bytes) whose completion is counted on mbarrier mb.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* mb) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(mb))
+               : "memory");
+}
+
+// Wait (one thread) for phase 0 of mbarrier mb, giving up after spin_ns.
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* mb, long long spin_ns) {
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(mb))
+        : "memory");
+    if (done) return true;
+    if ((++spins & 255u) == 0) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if ((long long)(now - t0) > spin_ns) return false;
     }
   }
 }
@@ -548,6 +578,16 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
   __shared__ int ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
   const int n = a.n, C = a.C, CN = (n + NT - 1) / NT;
+  // the dense weights' bulk copies complete on wbar; one thread waits for them
+  // (bounded; a block never leaves with copies in flight)
+  __shared__ __align__(8) unsigned long long wbar;
+  __shared__ int wready;
+  auto weights_wait = [&]() -> bool {
+    if (wready) return true;
+    const bool done = mbar_wait0(&wbar, a.spin_ns) || mbar_wait0(&wbar, a.spin_ns);
+    if (done) wready = 1;
+    return done;
+  };
   unsigned epoch = 0;
   auto gsync = [&]() -> bool {
     __syncthreads();
@@ -571,31 +611,28 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
     if (tid == 0) st_release(a.flags + c, phase);
   };
   auto give_up = [&]() {
+    if (tid == 0 && !weights_wait()) atomicExch(a.timeout, 1);
     for (int c = blockIdx.x; c < CN; c += gridDim.x) {
       const int i = c * NT + tid;
       if (tid < NT && i < n) a.x0[i] = __longlong_as_double(0x7FF8000000000000LL);
     }
   };
-  // all dense weights to shared memory once, by asynchronous 16-byte copies
-  // that complete while the first phase runs (waited for before the encoder's projection)
+  // all dense weights to shared memory once, by one bulk copy of their
+  // shared-memory image counted on an mbarrier, completing while the first
+  // phase runs (waited for before the encoder's projection)
   {
-    constexpr int NP = NL * 2 * H * (H / 8), NU = NL * H * KU / 8;
-    for (int i = tid; i < NP + NU; i += blockDim.x) {
-      const bf16* srcp;
-      bf16* dstp;
-      if (i < NP) {
-        const int lo = i / (H / 8), k8 = i % (H / 8);   // lo = layer * 2H + output
-        srcp = ab_row(a.Wm + (size_t)(lo / (2 * H)) * H * KMP, lo % (2 * H)) + k8 * 8;
-        dstp = Wab + lo * LDP + k8 * 8;
-      } else {
-        const int j = i - NP, lo = j / (KU / 8), k8 = j % (KU / 8);
-        srcp = a.Wu + (size_t)j * 8;
-        dstp = Wus + lo * LDU + k8 * 8;
-      }
-      const unsigned sa = (unsigned)__cvta_generic_to_shared(dstp);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(srcp) : "memory");
+    constexpr unsigned kWBytes = (unsigned)kInferWElems * sizeof(bf16);
+    static_assert(kWBytes % 16 == 0 && kWBytes < (1u << 20), "one bulk copy, counted by one mbarrier phase");
+    if (tid == 0) {
+      wready = 0;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&wbar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                   ::"r"(smem_addr(&wbar)), "r"(kWBytes)
+                   : "memory");
+      bulk_load(Wab, a.Winf, kWBytes, &wbar);
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
     for (int i = tid; i < NL * 2 * H; i += blockDim.x) {
       const int l = i / (2 * H), w = (i / H) % 2, ch = i % H;
       bias[l][w][ch] = a.P[layer_off(l) + (w == 0 ? L_BM : L_BU) + ch];
@@ -619,21 +656,46 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
     const int e0 = a.in_ptr[n0], e1 = a.in_ptr[n0 + cnt];
     for (int e = e0 + tid; e < min(e1, e0 + EIC); e += blockDim.x) srcs[e - e0] = a.src[e];
   };
-  if (one_chunk && (int)blockIdx.x < CN) load_edges(blockIdx.x);
+  // a single chunk's unscaled inputs (the residual recomputed: the same bits as its 128-row chunk's)
+  __shared__ double raw[NT][FIN];
+  if (one_chunk && (int)blockIdx.x < CN) {
+    load_edges(blockIdx.x);
+    const int i = blockIdx.x * NT + tid;
+    if (tid < NT && i < n) {
+      const double2 p = a.xy[i];
+      raw[tid][0] = residual_row(i, a.rowptr, a.col, a.K, a.b, a.phi1);
+      raw[tid][1] = a.phi1[i] - a.phi2[i];
+      raw[tid][2] = a.b[i];
+      raw[tid][3] = p.x;
+      raw[tid][4] = p.y;
+    }
+  }
   if (!gsync()) { give_up(); return; }
-  sample_scales(n, C, a.part, sc, isc);
+  // warp 1 waits for the weight copies while warp 0 folds the scales
+  __shared__ int wok;
+  if (tid == 32) wok = weights_wait() ? 1 : 0;
+  sample_scales(n, C, a.part, sc, isc);   // ends with the block's barrier
+  if (!wok) { give_up(); return; }
   if (blockIdx.x == 0 && tid == 0) a.scale[0] = sc[1];
   // ---- features, encoder and the first layer's projections of the block's node chunks ----
-  asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's weight copies; the barrier below shows all
   {
     const double ir = isc[0], id = isc[1], ib = isc[2];
     __shared__ float fs[NT * FIN];
     for (int c = blockIdx.x; c < CN; c += gridDim.x) {
       const int n0 = c * NT, n1 = min(n, n0 + NT), cnt = n1 - n0;
       const int i = n0 + tid;
-      if (tid < NT && i < n)
-        features_row(i, __ldcg(a.res + i), a.b, a.phi1, a.phi2, nullptr, a.xy, ir, id, ib, fs + tid * FIN, nullptr);
-      __syncthreads();   // also orders every thread's weight copies before the projection
+      if (tid < NT && i < n) {
+        if (one_chunk) {   // as features_row computes them
+          fs[tid * FIN + 0] = (float)(raw[tid][0] * ir);
+          fs[tid * FIN + 1] = (float)(raw[tid][1] * id);
+          fs[tid * FIN + 2] = (float)(raw[tid][2] * ib);
+          fs[tid * FIN + 3] = (float)(raw[tid][3] / 15.0);
+          fs[tid * FIN + 4] = (float)(raw[tid][4] / 15.0);
+        } else {
+          features_row(i, __ldcg(a.res + i), a.b, a.phi1, a.phi2, nullptr, a.xy, ir, id, ib, fs + tid * FIN, nullptr);
+        }
+      }
+      __syncthreads();
       for (int t = tid; t < NT * H; t += blockDim.x) {
         const int rr = t / H, ch = t % H;
         bf16 hv = __float2bfloat16_rn(0.0f);
@@ -1099,8 +1161,12 @@ __global__ void adam_kernel(int count, float* __restrict__ P, const float* __res
   P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
 }
 
-// BF16 copies of the dense weights: Wm padded to KMP columns, Wu as is.
-__global__ void refresh_bf16_kernel(const float* __restrict__ P, bf16* __restrict__ Wm, bf16* __restrict__ Wu) {
+// BF16 copies of the dense weights: Wm padded to KMP columns, Wu as is, and
+// the fused inference's shared-memory image of both (kInferWElems: [A; B] of
+// every layer in rows of LDP, then Wu in rows of LDU, padding zero), which it
+// loads with one bulk copy.
+__global__ void refresh_bf16_kernel(const float* __restrict__ P, bf16* __restrict__ Wm, bf16* __restrict__ Wu,
+                                    bf16* __restrict__ Winf) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int per_m = H * KMP, per_u = H * KU;
   if (t < NL * per_m) {
@@ -1110,6 +1176,17 @@ __global__ void refresh_bf16_kernel(const float* __restrict__ P, bf16* __restric
   } else if (t < NL * (per_m + per_u)) {
     const int q = t - NL * per_m, l = q / per_u, i = q % per_u;
     Wu[q] = __float2bfloat16_rn(P[layer_off(l) + L_WU + i]);
+  } else if (t < NL * (per_m + per_u) + kInferWElems) {
+    const int q = t - NL * (per_m + per_u);
+    float w = 0.0f;
+    if (q < NL * 2 * H * LDP) {
+      const int l = q / (2 * H * LDP), o = (q / LDP) % (2 * H), k = q % LDP;
+      if (k < H) w = P[layer_off(l) + L_WM + (o % H) * KM + (o / H) * H + k];
+    } else {
+      const int q2 = q - NL * 2 * H * LDP, l = q2 / (H * LDU), o = (q2 / LDU) % H, k = q2 % LDU;
+      if (k < KU) w = P[layer_off(l) + L_WU + o * KU + k];
+    }
+    Winf[q] = __float2bfloat16_rn(w);
   }
 }
 
@@ -1133,6 +1210,7 @@ struct cgp_gnn_s {
   // parameters
   float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
   bf16 *Wm = nullptr, *Wu = nullptr;
+  bf16* Winf = nullptr;   // the fused inference's shared-memory image of the dense weights
   // activations and gradients (max_batch samples)
   float *f = nullptr, *z0 = nullptr, *u = nullptr, *out = nullptr, *target = nullptr, *dout = nullptr, *loss = nullptr;
   double* scale = nullptr;
@@ -1245,8 +1323,8 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
 }
 
 int refresh(cgp_gnn_s* g, cudaStream_t s) {
-  const int total = NL * H * (KMP + KU);
-  refresh_bf16_kernel<<<(total + 255) / 256, 256, 0, s>>>(g->P, g->Wm, g->Wu);
+  const int total = NL * H * (KMP + KU) + kInferWElems;
+  refresh_bf16_kernel<<<(total + 255) / 256, 256, 0, s>>>(g->P, g->Wm, g->Wu, g->Winf);
   CGP_CUDA(cudaGetLastError());
   return CGP_OK;
 }
@@ -1309,7 +1387,8 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   const size_t o_dst = take(E * 4), o_src = take(E * 4), o_in = take((n + 1) * 4), o_op = take((n + 1) * 4),
                o_oe = take(E * 4), o_ell = take(8), o_ef = take((size_t)E * 4 * 2), o_P = take(NPARAM * 4),
                o_G = take(NPARAM * 4), o_M = take(NPARAM * 4), o_V = take(NPARAM * 4),
-               o_Wm = take((size_t)NL * H * KMP * 2), o_Wu = take((size_t)NL * H * KU * 2), o_f = take(rn * FIN * 4),
+               o_Wm = take((size_t)NL * H * KMP * 2), o_Wu = take((size_t)NL * H * KU * 2),
+               o_Winf = take((size_t)kInferWElems * 2), o_f = take(rn * FIN * 4),
                o_z0 = take(rn * H * 4), o_u = take((size_t)NL * rn * H * 4), o_out = take(rn * 4),
                o_t = take(rn * 4), o_do = take(rn * 4), o_loss = take(8), o_sc = take(B * 8),
                o_h = take((size_t)(NL + 1) * rn * H * 2), o_mask = take((size_t)NL * re * 8),
@@ -1339,6 +1418,7 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   g->V = (float*)(bs + o_V);
   g->Wm = (bf16*)(bs + o_Wm);
   g->Wu = (bf16*)(bs + o_Wu);
+  g->Winf = (bf16*)(bs + o_Winf);
   g->f = (float*)(bs + o_f);
   g->z0 = (float*)(bs + o_z0);
   g->u = (float*)(bs + o_u);
@@ -1455,7 +1535,7 @@ extern "C" int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, c
   a.ef = g->ef;
   a.P = g->P;
   a.Wm = g->Wm;
-  a.Wu = g->Wu;
+  a.Winf = g->Winf;
   a.h = g->h;
   a.pq = g->pq;
   a.part = g->fpart;
