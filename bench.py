@@ -66,8 +66,8 @@ def workload_config(precision="fp64"):
 SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_pcg_batch.cu", "cgp_pipe.cu", "cgp_solver.cuh", "cgp_sync.h", "cgp_fixed.h",
                   "cgp_internal.h")
 SOLVER_TRAFFIC = {
-    "sha256": "42ef0bf3a5dac1d074a5d246116bac004dc76d0907180c2e384ecfd6671164ee",
-    "fp64": 13984768 + 406528,
+    "sha256": "f585b3484a3dbdd670b5ac07a986ada8a60ab8092e3787626d29d36214f435e3",
+    "fp64": 10376704 + 300032,
 }
 
 
