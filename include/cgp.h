@@ -331,9 +331,12 @@ int cgp_poisson_solve_batched(const cgp_mesh* meshes, int count, const double* c
  *                  16 x co-resident blocks) one cooperative launch runs the
  *                  whole forward, else the batched training forward does;
  *                  both take the same arithmetic steps in the same order,
- *                  so the same bits.  The cooperative launch's grid barriers
- *                  give up after about two seconds and then leave NaN in x0,
- *                  which the solve reports as CGP_ERR_NONFINITE.
+ *                  so the same bits.  The cooperative launch's waits (one
+ *                  grid barrier, then per-chunk flags of the neighbouring
+ *                  chunks) give up after about two seconds and then leave
+ *                  NaN in x0, which the solve reports as CGP_ERR_NONFINITE.
+ *                  Calls on one network must not overlap on the GPU (they
+ *                  share its activations and synchronisation words).
  * cgp_gnn_train_step  forward, loss, backward and one Adam step on `batch`
  *                  samples stacked sample-major (device [batch][n_c] each,
  *                  phi_t the solutions to learn); loss_dev (device float,

@@ -68,6 +68,22 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// FP32 value rounded to TF32 (10 explicit mantissa bits, nearest, ties away), as its bits.
+__device__ __forceinline__ unsigned to_tf32(float v) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+
+// d += A[16 x 8] B[8 x 8], TF32 operands, FP32 accumulation.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
 // One warp: acc[16 x 64] += X[16 rows x K] * W^T, X row-major (ldx), W stored
 // as [64 outputs][K] (K contiguous, ldw), K a multiple of 16.
 template <int K>
@@ -610,6 +626,7 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
     __syncthreads();
     if (tid == 0) st_release(a.flags + c, phase);
   };
+  // a wait gave up (every thread of the block calls this, then returns)
   auto give_up = [&]() {
     if (tid == 0 && !weights_wait()) atomicExch(a.timeout, 1);
     for (int c = blockIdx.x; c < CN; c += gridDim.x) {
@@ -864,39 +881,58 @@ inline unsigned bwd_grid(size_t threads) {
   return (unsigned)(need < 1024 ? (need > 0 ? need : 1) : 1024);
 }
 
-// du = dh * [u > 0];  [dh_prev | da] = du Wu (Wu as its BF16 values); dh_prev += dh.
-// One warp per row (grid-stride): lane l forms outputs l, l + 32, l + 64,
-// l + 96, so each masked gradient is read once per warp, not once per
-// output; every output still sums o = 0 .. H-1 in order.  A block expands Wu
-// to FP32 in shared memory once for all the rows it visits.
-__global__ void update_bwd_kernel(int rows, const float* __restrict__ dh, const float* __restrict__ u,
-                                  const bf16* __restrict__ Wb, float* __restrict__ du, float* __restrict__ dh_prev,
-                                  float* __restrict__ da) {
-  static_assert(KU == 4 * 32 && H == 2 * 32, "one warp per row, four outputs per lane");
+// du = dh * [u > 0];  [dh_prev | da] = du Wu;  dh_prev += dh.  On the tensor
+// cores: Wu as its BF16 values (exact in TF32), du rounded to TF32, FP32
+// accumulation in a fixed order.  A block takes TILE rows (warp w rows
+// 16w .. 16w + 15, all 2H outputs); du is also stored for the weight gradient.
+constexpr int LDWU = KU + 8;   // shared row strides, 8 and 4 banks apart row to row
+constexpr int LDDU = H + 4;
+constexpr size_t kUpdBwdSmem = (size_t)(H * LDWU + TILE * LDDU) * sizeof(float);
+__global__ void __launch_bounds__(256) update_bwd_kernel(int rows, const float* __restrict__ dh,
+                                                         const float* __restrict__ u, const bf16* __restrict__ Wb,
+                                                         float* __restrict__ du, float* __restrict__ dh_prev,
+                                                         float* __restrict__ da) {
+  static_assert(TILE == 8 * 16 && KU == 2 * H, "eight warps of 16 rows, outputs [dh | da]");
   extern __shared__ __align__(16) unsigned char smem[];
-  float* Wf = reinterpret_cast<float*>(smem);          // [H][KU]
-  for (int i = threadIdx.x; i < H * KU; i += blockDim.x) Wf[i] = __bfloat162float(Wb[i]);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const size_t total = (size_t)rows * 32;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / 32);
-    const float* dhr = dh + (size_t)r * H;
-    const float* ur = u + (size_t)r * H;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int o = 0; o < H; ++o) {
-      const float g = ur[o] > 0.0f ? dhr[o] : 0.0f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(g, Wf[o * KU + lane + 32 * q], acc[q]);
+  float* Wf = reinterpret_cast<float*>(smem);          // [H][LDWU]: row o of Wu (TF32 bits)
+  float* Us = Wf + H * LDWU;                           // [TILE][LDDU]: du (TF32 bits)
+  for (int i = threadIdx.x; i < H * KU; i += blockDim.x)
+    Wf[(i / KU) * LDWU + i % KU] = __uint_as_float(to_tf32(__bfloat162float(Wb[i])));
+  const int r0 = blockIdx.x * TILE;
+  for (int i = threadIdx.x; i < TILE * H; i += blockDim.x) {
+    const int rr = i / H, o = i % H, r = r0 + rr;
+    float g = 0.0f;
+    if (r < rows) {
+      g = u[(size_t)r * H + o] > 0.0f ? dh[(size_t)r * H + o] : 0.0f;
+      du[(size_t)r * H + o] = g;
     }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int k = lane + 32 * q;
-      dh_prev[(size_t)r * H + k] = dhr[k] + acc[q];
-      du[(size_t)r * H + k] = ur[k] > 0.0f ? dhr[k] : 0.0f;
-      da[(size_t)r * H + k] = acc[q + 2];
-    }
+    Us[rr * LDDU + o] = __uint_as_float(to_tf32(g));
   }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  float acc[KU / 8][4];
+#pragma unroll
+  for (int nt = 0; nt < KU / 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+  const float* A = Us + (warp * 16 + gid) * LDDU + tig;
+#pragma unroll
+  for (int k0 = 0; k0 < H; k0 += 8) {
+    const unsigned a0 = __float_as_uint(A[k0]), a1 = __float_as_uint(A[8 * LDDU + k0]);
+    const unsigned a2 = __float_as_uint(A[k0 + 4]), a3 = __float_as_uint(A[8 * LDDU + k0 + 4]);
+    const float* B = Wf + (k0 + tig) * LDWU + gid;
+#pragma unroll
+    for (int nt = 0; nt < KU / 8; ++nt)
+      mma_tf32(acc[nt], a0, a1, a2, a3, __float_as_uint(B[nt * 8]), __float_as_uint(B[4 * LDWU + nt * 8]));
+  }
+#pragma unroll
+  for (int nt = 0; nt < KU / 8; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + warp * 16 + gid + (q >> 1) * 8, c = nt * 8 + tig * 2 + (q & 1);
+      if (r < rows) {
+        if (c < H) dh_prev[(size_t)r * H + c] = dh[(size_t)r * H + c] + acc[nt][q];
+        else da[(size_t)r * H + c - H] = acc[nt][q];
+      }
+    }
 }
 
 // Backward of the split message layer for one node row r = (s, i), one warp
@@ -1005,64 +1041,63 @@ __global__ void encode_bwd_kernel(int rows, const float* __restrict__ dh, const 
 
 // Weight gradient partials: for a chunk of ROWS rows, G[o][k] = sum_r D[r][o] X[r][k]
 // and G[o][K] = sum_r D[r][o] (the bias); D and X entries come from `load_d`
-// and `load_x`.
+// and `load_x`.  When NO is a multiple of 16 the chunk is a product on the
+// tensor cores (TF32 operands, FP32 accumulation over the chunk's rows in
+// order); otherwise FP32 FMAs.
 constexpr int WG_ROWS = 128;
-// shared-memory row stride of the inputs of a weight-gradient chunk (KX
-// inputs and the bias column, padded to 16-byte rows) and the chunk's bytes
-__host__ __device__ constexpr int wg_xs(int KX) { return (KX + 1 + 3) / 4 * 4; }
-constexpr size_t wg_smem(int KX, int NO) { return (size_t)WG_ROWS * (NO + wg_xs(KX)) * sizeof(float); }
+// shared-memory row strides of a weight-gradient chunk: inputs (KX and the
+// bias column, padded to 8) and outputs (NO + 8): both 8 banks apart row to
+// row, so the MMA fragments' loads are free of conflicts
+__host__ __device__ constexpr int wg_xs(int KX) { return (KX + 1 + 7) / 8 * 8; }
+__host__ __device__ constexpr int wg_ds(int NO) { return NO % 16 == 0 ? NO + 8 : NO; }
+constexpr size_t wg_smem(int KX, int NO) { return (size_t)WG_ROWS * (wg_ds(NO) + wg_xs(KX)) * sizeof(float); }
 
 template <int KX, int NO, typename LoadD, typename LoadX>
 __device__ void wgrad_chunk(int rows, LoadD load_d, LoadX load_x, float* __restrict__ part) {
-  constexpr int XS = wg_xs(KX);
+  constexpr int XS = wg_xs(KX), DS = wg_ds(NO);
+  constexpr bool MMA = NO % 16 == 0;
   extern __shared__ __align__(16) unsigned char smem[];
-  float* Ds = reinterpret_cast<float*>(smem);          // [WG_ROWS][NO]
-  float* Xs = Ds + WG_ROWS * NO;                       // [WG_ROWS][XS]: KX inputs, the bias 1, zero padding
+  float* Ds = reinterpret_cast<float*>(smem);          // [WG_ROWS][DS]
+  float* Xs = Ds + WG_ROWS * DS;                       // [WG_ROWS][XS]: KX inputs, the bias 1, zero padding
   const int r0 = blockIdx.x * WG_ROWS;
   for (int i = threadIdx.x; i < WG_ROWS * NO; i += blockDim.x) {
     const int rr = i / NO, o = i % NO, r = r0 + rr;
-    Ds[i] = r < rows ? load_d(r, o) : 0.0f;
+    const float v = r < rows ? load_d(r, o) : 0.0f;
+    Ds[rr * DS + o] = MMA ? __uint_as_float(to_tf32(v)) : v;
   }
   for (int i = threadIdx.x; i < WG_ROWS * XS; i += blockDim.x) {
     const int rr = i / XS, k = i % XS, r = r0 + rr;
-    Xs[i] = (r < rows) ? (k < KX ? load_x(r, k) : (k == KX ? 1.0f : 0.0f)) : 0.0f;
+    const float v = (r < rows) ? (k < KX ? load_x(r, k) : (k == KX ? 1.0f : 0.0f)) : 0.0f;
+    Xs[i] = MMA ? __uint_as_float(to_tf32(v)) : v;
   }
   __syncthreads();
   float* out = part + (size_t)blockIdx.x * NO * (KX + 1);
-  if constexpr (NO % 4 == 0) {
-    // 4 x 4 tiles of (o, k) per thread: two 16-byte shared loads feed 16 FMAs.
-    // Each output still sums rr = 0 .. WG_ROWS-1 in order, as one output per
-    // thread would.
-    constexpr int NTK = XS / 4;
-    for (int tile = threadIdx.x; tile < (NO / 4) * NTK; tile += blockDim.x) {
-      const int to = tile / NTK, tk = tile % NTK;
-      float acc[4][4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-      for (int rr = 0; rr < WG_ROWS; ++rr) {
-        const float4 dv = *reinterpret_cast<const float4*>(Ds + rr * NO + 4 * to);
-        const float4 xv = *reinterpret_cast<const float4*>(Xs + rr * XS + 4 * tk);
-        const float dd[4] = {dv.x, dv.y, dv.z, dv.w}, xx[4] = {xv.x, xv.y, xv.z, xv.w};
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(dd[a], xx[b], acc[a][b]);
+  if constexpr (MMA) {
+    // tile (m, n): outputs 16m .. 16m+15 x inputs 8n .. 8n+7; warps take tiles in turn
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    constexpr int MT = NO / 16, NTL = XS / 8;
+    for (int tile = warp; tile < MT * NTL; tile += nw) {
+      const int o0 = (tile / NTL) * 16, n0 = (tile % NTL) * 8;
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+      for (int k0 = 0; k0 < WG_ROWS; k0 += 8) {
+        const float* d0 = Ds + (k0 + tig) * DS + o0 + gid;
+        const float* d1 = d0 + 4 * DS;
+        const float* x0 = Xs + (k0 + tig) * XS + n0 + gid;
+        mma_tf32(acc, __float_as_uint(d0[0]), __float_as_uint(d0[8]), __float_as_uint(d1[0]), __float_as_uint(d1[8]),
+                 __float_as_uint(x0[0]), __float_as_uint(x0[4 * XS]));
       }
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int k = 4 * tk + b;
-          if (k <= KX) out[(4 * to + a) * (KX + 1) + k] = acc[a][b];
-        }
+      for (int q = 0; q < 4; ++q) {
+        const int o = o0 + gid + (q >> 1) * 8, k = n0 + tig * 2 + (q & 1);
+        if (k <= KX) out[o * (KX + 1) + k] = acc[q];
+      }
     }
   } else {
     for (int j = threadIdx.x; j < NO * (KX + 1); j += blockDim.x) {
       const int o = j / (KX + 1), k = j % (KX + 1);
       float s = 0.0f;
-      for (int rr = 0; rr < WG_ROWS; ++rr) s = fmaf(Ds[rr * NO + o], Xs[rr * XS + k], s);
+      for (int rr = 0; rr < WG_ROWS; ++rr) s = fmaf(Ds[rr * DS + o], Xs[rr * XS + k], s);
       out[j] = s;
     }
   }
@@ -1285,7 +1320,7 @@ int gnn_backward(cgp_gnn_s* g, int B, cudaStream_t s) {
     const float* ul = g->u + (size_t)l * rn * H;
     const int off = layer_off(l);
     // node update
-    update_bwd_kernel<<<bwd_grid((size_t)rn * 32), 256, (size_t)H * KU * sizeof(float), s>>>(
+    update_bwd_kernel<<<(rn + TILE - 1) / TILE, 256, kUpdBwdSmem, s>>>(
         rn, dh, ul, g->Wu + (size_t)l * H * KU, g->du, dh_prev, g->da);
     {
       const int chunks = (rn + WG_ROWS - 1) / WG_ROWS;
@@ -1467,7 +1502,7 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   if (st == CGP_OK) st = smem_optin((const void*)update_fwd_kernel, (size_t)(H + TILE) * LDU * sizeof(bf16));
   if (st == CGP_OK) st = smem_optin((const void*)wgrad_project_kernel, wg_smem(H, 2 * H));
   if (st == CGP_OK) st = smem_optin((const void*)wgrad_update_kernel, wg_smem(KU, H));
-  if (st == CGP_OK) st = smem_optin((const void*)update_bwd_kernel, (size_t)H * KU * sizeof(float));
+  if (st == CGP_OK) st = smem_optin((const void*)update_bwd_kernel, kUpdBwdSmem);
   if (st == CGP_OK) st = smem_optin((const void*)message_bwd_kernel, kMsgBwdSmem);
   if (st == CGP_OK) st = smem_optin((const void*)infer_kernel, kInferSmem);
   if (st == CGP_OK) {
@@ -1548,8 +1583,8 @@ extern "C" int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, c
   a.flags = reinterpret_cast<unsigned*>(g->ictrl + 256);
   a.bar = reinterpret_cast<unsigned*>(g->ictrl);
   a.timeout = reinterpret_cast<int*>(g->ictrl + 128);
-  a.spin_ns = 2000000000LL;
   CGP_CUDA(cudaMemsetAsync(g->ictrl, 0, g->ictrl_bytes, s));
+  a.spin_ns = 2000000000LL;
   void* args[] = {&a};
   CGP_CUDA(cudaLaunchCooperativeKernel((const void*)infer_kernel, dim3(g->infer_grid), dim3(256), args, kInferSmem, s));
   return CGP_OK;
