@@ -47,6 +47,7 @@ constexpr int LDU = KU + 8;         // smem row strides (bank spread): update op
 constexpr int LDP = H + 8;          // node-projection operands
 constexpr int kInferWElems = NL * 2 * H * LDP + NL * H * LDU;   // the fused inference's weight image (BF16)
 constexpr int TILE = 128;           // rows per tensor-core block (8 warps x 16)
+constexpr int SROWS = 16;           // rows per partial sum of the input scales
 
 // parameter layout (FP32, row-major), identical to the oracle's order
 constexpr int OFF_WE = 0, OFF_BE = OFF_WE + H * FIN;
@@ -146,6 +147,12 @@ __global__ void edge_length_kernel(int E, const int* __restrict__ dst, const int
   }
 }
 
+// The coordinate inputs of every node, (float)(x / 15) and (float)(y / 15).
+__global__ void coord_feature_kernel(int n, const double2* __restrict__ xy, float2* __restrict__ xyf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) xyf[i] = make_float2((float)(xy[i].x / 15.0), (float)(xy[i].y / 15.0));
+}
+
 __global__ void edge_feature_kernel(int E, const int* __restrict__ dst, const int* __restrict__ src,
                                     const double2* __restrict__ xy, const double* __restrict__ ell,
                                     bf16* __restrict__ ef) {
@@ -176,8 +183,9 @@ __device__ __forceinline__ double residual_row(int i, const int* __restrict__ ro
 
 // Input scales in one fixed reduction order, shared by the batched forward
 // and the fused inference kernel so both produce the same bits.  Chunk c of a
-// sample holds rows [c TILE, (c+1) TILE); thread t < TILE takes row
-// c TILE + t.  A chunk's partial sums of r^2, d^2 and b^2 are warp
+// sample holds rows [c SROWS, (c+1) SROWS) (one fused-inference chunk, so
+// every block of that kernel forms its own); thread t < SROWS takes row
+// c SROWS + t.  A chunk's partial sums of r^2, d^2 and b^2 are warp
 // butterflies added over the warps in order; a sample's totals add the chunk
 // partials per lane (chunks lane, lane + 32, ...) and finish with a butterfly.
 __device__ __forceinline__ void chunk_partials(int n, int c, const int* __restrict__ rowptr,
@@ -185,9 +193,9 @@ __device__ __forceinline__ void chunk_partials(int n, int c, const int* __restri
                                                const double* __restrict__ bs, const double* __restrict__ p1,
                                                const double* __restrict__ p2, double* red, double* out,
                                                double* __restrict__ r_out) {
-  const int t = threadIdx.x, i = c * TILE + t, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  const int t = threadIdx.x, i = c * SROWS + t, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
   double v[3] = {0.0, 0.0, 0.0};
-  if (t < TILE && i < n) {
+  if (t < SROWS && i < n) {
     const double r = residual_row(i, rowptr, col, K, bs, p1);
     if (r_out) r_out[i] = r;
     const double dd = p1[i] - p2[i];
@@ -209,47 +217,54 @@ __device__ __forceinline__ void chunk_partials(int n, int c, const int* __restri
   __syncthreads();
 }
 
-// Warp 0: the sample's scales sc[q] = sqrt(total_q / n) (1 when zero) from its
-// C chunk partials, and their inverses isc[q] = 1 / sc[q].
+// Warp q (q < 3): scale q of the sample, sc[q] = sqrt(total_q / n) (1 when
+// zero), from its C chunk partials, and its inverse isc[q] = 1 / sc[q].  The
+// three components run on three warps (three schedulers): GB300's FP64 pipe
+// is narrow, and one warp's chain of FP64 sums, square root and divisions
+// is the latency here.
 __device__ __forceinline__ void sample_scales(int n, int C, const double* __restrict__ part, double* sc, double* isc) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    double a[3] = {0.0, 0.0, 0.0};
-    for (int ch = lane; ch < C; ch += 32) {
-      const double v0 = __ldcg(part + ch * 3), v1 = __ldcg(part + ch * 3 + 1), v2 = __ldcg(part + ch * 3 + 2);
-      a[0] += v0;
-      a[1] += v1;
-      a[2] += v2;
-    }
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = threadIdx.x >> 5; q < 3; q += nw) {
+    double a = 0.0;
+    constexpr int U = 8;   // chunks per lane whose loads are issued together
+    for (int base = 0; base < C; base += 32 * U) {
+      double v[U];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
-      if (lane == q) {   // three lanes, one scale each
-        const double rr = sqrt(a[q] / n);
-        sc[q] = rr > 1e-30 ? rr : 1.0;
-        isc[q] = 1.0 / sc[q];
+      for (int u = 0; u < U; ++u) {
+        const int ch = base + lane + 32 * u;
+        v[u] = ch < C ? __ldcg(part + ch * 3 + q) : 0.0;
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u)   // chunks lane, lane + 32, ... in order
+        if (base + lane + 32 * u < C) a += v[u];
+    }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) {
+      const double rr = sqrt(a / n);
+      sc[q] = rr > 1e-30 ? rr : 1.0;
+      isc[q] = 1.0 / sc[q];
     }
   }
   __syncthreads();
 }
 
 // Features of row i with residual r (and its target when phi_t is given), scales inverted by the caller.
+// xyf: the coordinate inputs (float)(x / 15), (float)(y / 15), formed once per mesh.
 __device__ __forceinline__ void features_row(int i, double r, const double* __restrict__ bs,
                                              const double* __restrict__ p1, const double* __restrict__ p2,
-                                             const double* __restrict__ pt, const double2* __restrict__ xy,
+                                             const double* __restrict__ pt, const float2* __restrict__ xyf,
                                              double ir, double id, double ib, float* __restrict__ fi,
                                              float* __restrict__ ti) {
-  const double2 p = xy[i];
+  const float2 p = xyf[i];
   fi[0] = (float)(r * ir);
   fi[1] = (float)((p1[i] - p2[i]) * id);
   fi[2] = (float)(bs[i] * ib);
-  fi[3] = (float)(p.x / 15.0);
-  fi[4] = (float)(p.y / 15.0);
+  fi[3] = p.x;
+  fi[4] = p.y;
   if (pt) *ti = (float)((pt[i] - p1[i]) * id);
 }
 
-// Batched forward, first pass: partial sums of every (sample, chunk).
+// Batched forward, first pass: partial sums of every (sample, chunk); one warp per chunk.
 __global__ void features_partial_kernel(int n, int C, const int* __restrict__ rowptr, const int* __restrict__ col,
                                         const double* __restrict__ K, const double* __restrict__ b,
                                         const double* __restrict__ phi1, const double* __restrict__ phi2,
@@ -262,15 +277,17 @@ __global__ void features_partial_kernel(int n, int C, const int* __restrict__ ro
   if (threadIdx.x < 3) part[((size_t)s * C + c) * 3 + threadIdx.x] = out[threadIdx.x];
 }
 
-// Batched forward, second pass: scales, input features and (when phi_t is given) targets.
-__global__ void features_rows_kernel(int n, int C, const int* __restrict__ rowptr, const int* __restrict__ col,
+// Batched forward, second pass: scales (from the C scale chunks), input
+// features and (when phi_t is given) targets of TILE rows per block (R row
+// blocks per sample).
+__global__ void features_rows_kernel(int n, int C, int R, const int* __restrict__ rowptr, const int* __restrict__ col,
                                      const double* __restrict__ K, const double* __restrict__ b,
                                      const double* __restrict__ phi1, const double* __restrict__ phi2,
-                                     const double* __restrict__ phi_t, const double2* __restrict__ xy,
+                                     const double* __restrict__ phi_t, const float2* __restrict__ xyf,
                                      const double* __restrict__ part, float* __restrict__ f,
                                      double* __restrict__ scale, float* __restrict__ target) {
   __shared__ double sc[3], isc[3];
-  const int s = blockIdx.x / C, c = blockIdx.x % C;
+  const int s = blockIdx.x / R, c = blockIdx.x % R;
   const size_t base = (size_t)s * n;
   sample_scales(n, C, part + (size_t)s * C * 3, sc, isc);
   if (c == 0 && threadIdx.x == 0) scale[s] = sc[1];
@@ -278,7 +295,7 @@ __global__ void features_rows_kernel(int n, int C, const int* __restrict__ rowpt
   const int i = c * TILE + threadIdx.x;
   if (threadIdx.x < TILE && i < n)
     features_row(i, residual_row(i, rowptr, col, K, b + base, phi1 + base), b + base, phi1 + base, phi2 + base,
-                 phi_t ? phi_t + base : nullptr, xy, ir, id, ib, f + (base + i) * FIN, target + base + i);
+                 phi_t ? phi_t + base : nullptr, xyf, ir, id, ib, f + (base + i) * FIN, target + base + i);
 }
 
 __global__ void encode_kernel(int rows, const float* __restrict__ P, const float* __restrict__ f,
@@ -463,7 +480,7 @@ struct InferArgs {
   const double* b;
   const double* phi1;
   const double* phi2;
-  const double2* xy;
+  const float2* xyf;
   const int* src;
   const int* in_ptr;
   const bf16* ef;
@@ -486,7 +503,7 @@ struct InferArgs {
 };
 
 // Layers and decoder work on node chunks of NT nodes (block b takes chunks b,
-// b + grid, ...).  The input scales use the 128-row chunks of the shared
+// b + grid, ...).  The input scales use the 16-row chunks of the shared
 // reduction order.  Each phase ends with the node projections [P | Q] of the
 // layer that follows, so a layer reads only Q of its in-edges' sources (the
 // one value other chunks contribute) and its own P.  One grid barrier, after
@@ -594,15 +611,14 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
   __shared__ int ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
   const int n = a.n, C = a.C, CN = (n + NT - 1) / NT;
-  // the dense weights' bulk copies complete on wbar; one thread waits for them
-  // (bounded; a block never leaves with copies in flight)
-  __shared__ __align__(8) unsigned long long wbar;
-  __shared__ int wready;
-  auto weights_wait = [&]() -> bool {
-    if (wready) return true;
-    const bool done = mbar_wait0(&wbar, a.spin_ns) || mbar_wait0(&wbar, a.spin_ns);
-    if (done) wready = 1;
-    return done;
+  // the dense weights arrive as 2 NL bulk copies, in the order they are used
+  // ([A; B] of layer l: copy 2l, Wu of layer l: copy 2l + 1), each on its own
+  // mbarrier; one thread waits for the copy a phase needs (bounded; a block
+  // never leaves with copies in flight)
+  __shared__ __align__(8) unsigned long long wbar[2 * NL];
+  __shared__ int wfail;
+  auto weights_wait = [&](int j) -> bool {
+    return mbar_wait0(&wbar[j], a.spin_ns) || mbar_wait0(&wbar[j], a.spin_ns);
   };
   unsigned epoch = 0;
   auto gsync = [&]() -> bool {
@@ -628,27 +644,37 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
   };
   // a wait gave up (every thread of the block calls this, then returns)
   auto give_up = [&]() {
-    if (tid == 0 && !weights_wait()) atomicExch(a.timeout, 1);
+    if (tid == 0) {
+      bool all = true;
+      for (int j = 0; j < 2 * NL; ++j) all = weights_wait(j) && all;
+      if (!all) atomicExch(a.timeout, 1);
+    }
     for (int c = blockIdx.x; c < CN; c += gridDim.x) {
       const int i = c * NT + tid;
       if (tid < NT && i < n) a.x0[i] = __longlong_as_double(0x7FF8000000000000LL);
     }
   };
-  // all dense weights to shared memory once, by one bulk copy of their
-  // shared-memory image counted on an mbarrier, completing while the first
-  // phase runs (waited for before the encoder's projection)
+  // all dense weights to shared memory once, from their shared-memory image
+  // in global memory, completing while the first phases run
   {
-    constexpr unsigned kWBytes = (unsigned)kInferWElems * sizeof(bf16);
-    static_assert(kWBytes % 16 == 0 && kWBytes < (1u << 20), "one bulk copy, counted by one mbarrier phase");
+    constexpr unsigned kAB = 2 * H * LDP * sizeof(bf16), kU = H * LDU * sizeof(bf16);
+    static_assert(kAB % 16 == 0 && kU % 16 == 0, "bulk copies of whole 16-byte units");
     if (tid == 0) {
-      wready = 0;
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&wbar)) : "memory");
+      wfail = 0;
+      for (int j = 0; j < 2 * NL; ++j)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&wbar[j])) : "memory");
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
-                   ::"r"(smem_addr(&wbar)), "r"(kWBytes)
-                   : "memory");
-      bulk_load(Wab, a.Winf, kWBytes, &wbar);
+      for (int j = 0; j < 2 * NL; ++j) {
+        const int l = j / 2;
+        const unsigned bytes = (j & 1) ? kU : kAB;
+        bf16* dst = (j & 1) ? Wus + l * H * LDU : Wab + l * 2 * H * LDP;
+        const bf16* src = a.Winf + ((j & 1) ? NL * 2 * H * LDP + l * H * LDU : l * 2 * H * LDP);
+        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                     ::"r"(smem_addr(&wbar[j])), "r"(bytes)
+                     : "memory");
+        bulk_load(dst, src, bytes, &wbar[j]);
+      }
     }
     for (int i = tid; i < NL * 2 * H; i += blockDim.x) {
       const int l = i / (2 * H), w = (i / H) % 2, ch = i % H;
@@ -659,12 +685,6 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
       cm[l][k][ch] = __bfloat162float(a.Wm[(size_t)l * H * KMP + ch * KMP + 2 * H + k]);
     }
   }
-  // ---- scale partials (128-row chunks) ----
-  for (int c = blockIdx.x; c < C; c += gridDim.x) {
-    chunk_partials(n, c, a.rowptr, a.col, a.K, a.b, a.phi1, a.phi2, red, sc, a.res);
-    if (tid < 3) a.part[c * 3 + tid] = sc[tid];
-    __syncthreads();
-  }
   // a block with a single node chunk keeps its in-edge sources for all layers
   const bool one_chunk = CN <= (int)gridDim.x;
   auto load_edges = [&](int c) {
@@ -673,24 +693,45 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
     const int e0 = a.in_ptr[n0], e1 = a.in_ptr[n0 + cnt];
     for (int e = e0 + tid; e < min(e1, e0 + EIC); e += blockDim.x) srcs[e - e0] = a.src[e];
   };
-  // a single chunk's unscaled inputs (the residual recomputed: the same bits as its 128-row chunk's)
+  // Threads TILE.. load the encoder's weights and, in a block with a single
+  // chunk, the chunk's in-edges and unscaled inputs (the residual recomputed:
+  // the same bits as its scale chunk's), while threads 0 .. SROWS-1 form the
+  // scale partials: the two chains of dependent loads overlap.
   __shared__ double raw[NT][FIN];
-  if (one_chunk && (int)blockIdx.x < CN) {
-    load_edges(blockIdx.x);
-    const int i = blockIdx.x * NT + tid;
-    if (tid < NT && i < n) {
-      const double2 p = a.xy[i];
-      raw[tid][0] = residual_row(i, a.rowptr, a.col, a.K, a.b, a.phi1);
-      raw[tid][1] = a.phi1[i] - a.phi2[i];
-      raw[tid][2] = a.b[i];
-      raw[tid][3] = p.x;
-      raw[tid][4] = p.y;
+  __shared__ float we[H][FIN + 1];   // encoder weights, the bias last
+  static_assert(NT <= TILE, "the side threads cover a chunk");
+  if (tid >= TILE) {
+    const int l = tid - TILE, ls = blockDim.x - TILE;
+    for (int i = l; i < H * (FIN + 1); i += ls) {
+      const int ch = i / (FIN + 1), k = i % (FIN + 1);
+      we[ch][k] = k < FIN ? a.P[OFF_WE + ch * FIN + k] : a.P[OFF_BE + ch];
     }
+    if (one_chunk && (int)blockIdx.x < CN) {
+      const int n0 = blockIdx.x * NT, cnt = min(NT, n - n0);
+      if (l <= cnt) iptr[l] = a.in_ptr[n0 + l];
+      const int e0 = a.in_ptr[n0], e1 = a.in_ptr[n0 + cnt];
+      for (int e = e0 + l; e < min(e1, e0 + EIC); e += ls) srcs[e - e0] = a.src[e];
+      const int i = n0 + l;
+      if (l < NT && i < n) {
+        const float2 p = a.xyf[i];
+        raw[l][0] = residual_row(i, a.rowptr, a.col, a.K, a.b, a.phi1);
+        raw[l][1] = a.phi1[i] - a.phi2[i];
+        raw[l][2] = a.b[i];
+        raw[l][3] = p.x;
+        raw[l][4] = p.y;
+      }
+    }
+  }
+  // ---- scale partials (16-row chunks: a block's own chunk when it has one) ----
+  for (int c = blockIdx.x; c < C; c += gridDim.x) {
+    chunk_partials(n, c, a.rowptr, a.col, a.K, a.b, a.phi1, a.phi2, red, sc, a.res);
+    if (tid < 3) a.part[c * 3 + tid] = sc[tid];
+    __syncthreads();
   }
   if (!gsync()) { give_up(); return; }
   // warp 1 waits for the weight copies while warp 0 folds the scales
   __shared__ int wok;
-  if (tid == 32) wok = weights_wait() ? 1 : 0;
+  if (tid == 32) wok = weights_wait(0) ? 1 : 0;   // [A; B] of layer 0
   sample_scales(n, C, a.part, sc, isc);   // ends with the block's barrier
   if (!wok) { give_up(); return; }
   if (blockIdx.x == 0 && tid == 0) a.scale[0] = sc[1];
@@ -706,10 +747,10 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
           fs[tid * FIN + 0] = (float)(raw[tid][0] * ir);
           fs[tid * FIN + 1] = (float)(raw[tid][1] * id);
           fs[tid * FIN + 2] = (float)(raw[tid][2] * ib);
-          fs[tid * FIN + 3] = (float)(raw[tid][3] / 15.0);
-          fs[tid * FIN + 4] = (float)(raw[tid][4] / 15.0);
+          fs[tid * FIN + 3] = (float)raw[tid][3];
+          fs[tid * FIN + 4] = (float)raw[tid][4];
         } else {
-          features_row(i, __ldcg(a.res + i), a.b, a.phi1, a.phi2, nullptr, a.xy, ir, id, ib, fs + tid * FIN, nullptr);
+          features_row(i, __ldcg(a.res + i), a.b, a.phi1, a.phi2, nullptr, a.xyf, ir, id, ib, fs + tid * FIN, nullptr);
         }
       }
       __syncthreads();
@@ -717,10 +758,9 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
         const int rr = t / H, ch = t % H;
         bf16 hv = __float2bfloat16_rn(0.0f);
         if (rr < cnt) {
-          const float* w = a.P + OFF_WE + ch * FIN;
-          float z = a.P[OFF_BE + ch];
+          float z = we[ch][FIN];
 #pragma unroll
-          for (int k = 0; k < FIN; ++k) z = fmaf(w[k], fs[rr * FIN + k], z);
+          for (int k = 0; k < FIN; ++k) z = fmaf(we[ch][k], fs[rr * FIN + k], z);
           hv = __float2bfloat16_rn(fmaxf(z, 0.0f));
           a.h[(size_t)(n0 + rr) * H + ch] = hv;
         }
@@ -794,7 +834,9 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) X[rr * LDU + H + c4 + k] = __float2bfloat16_rn(acc[k]);
       }
+      if (tid == 0 && !weights_wait(2 * l + 1)) wfail = 1;   // Wu of this layer
       __syncthreads();
+      if (wfail) { give_up(); return; }
       // update of the chunk's nodes: [h | a] x Wu, warp w computing outputs 8w .. 8w+7
       {
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -813,7 +855,9 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
           *reinterpret_cast<__nv_bfloat162*>(Xh + rr * LDP + ch) = node < n1 ? o : __floats2bfloat162_rn(0.0f, 0.0f);
         }
       }
+      if (l + 1 < NL && tid == 0 && !weights_wait(2 * (l + 1))) wfail = 1;   // [A; B] of the next layer
       __syncthreads();
+      if (wfail) { give_up(); return; }
       if (l + 1 < NL) {   // the next layer's projections of the new h
         chunk_project(Xh, Wab + (l + 1) * 2 * H * LDP, n0, n1, pout);
         publish(c, l + 2);
@@ -893,20 +937,35 @@ __global__ void __launch_bounds__(256) update_bwd_kernel(int rows, const float* 
                                                          float* __restrict__ du, float* __restrict__ dh_prev,
                                                          float* __restrict__ da) {
   static_assert(TILE == 8 * 16 && KU == 2 * H, "eight warps of 16 rows, outputs [dh | da]");
+  static_assert((H * KU / 8) % 256 == 0 && (TILE * H / 4) % 256 == 0, "whole staging rounds of 256 threads");
   extern __shared__ __align__(16) unsigned char smem[];
   float* Wf = reinterpret_cast<float*>(smem);          // [H][LDWU]: row o of Wu (TF32 bits)
   float* Us = Wf + H * LDWU;                           // [TILE][LDDU]: du (TF32 bits)
-  for (int i = threadIdx.x; i < H * KU; i += blockDim.x)
-    Wf[(i / KU) * LDWU + i % KU] = __uint_as_float(to_tf32(__bfloat162float(Wb[i])));
+  // staging with 16-byte loads, every thread's loads issued together (256 threads)
+#pragma unroll
+  for (int q = 0; q < H * KU / 8 / 256; ++q) {
+    const int i = threadIdx.x + 256 * q, o = i / (KU / 8), k8 = (i % (KU / 8)) * 8;
+    const uint4 w = *reinterpret_cast<const uint4*>(Wb + (size_t)o * KU + k8);
+    const bf16* wh = reinterpret_cast<const bf16*>(&w);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Wf[o * LDWU + k8 + j] = __uint_as_float(to_tf32(__bfloat162float(wh[j])));
+  }
   const int r0 = blockIdx.x * TILE;
-  for (int i = threadIdx.x; i < TILE * H; i += blockDim.x) {
-    const int rr = i / H, o = i % H, r = r0 + rr;
-    float g = 0.0f;
+#pragma unroll
+  for (int q = 0; q < TILE * H / 4 / 256; ++q) {
+    const int i = threadIdx.x + 256 * q, rr = i / (H / 4), o4 = (i % (H / 4)) * 4, r = r0 + rr;
+    float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (r < rows) {
-      g = u[(size_t)r * H + o] > 0.0f ? dh[(size_t)r * H + o] : 0.0f;
-      du[(size_t)r * H + o] = g;
+      const float4 uu = *reinterpret_cast<const float4*>(u + (size_t)r * H + o4);
+      const float4 dd = *reinterpret_cast<const float4*>(dh + (size_t)r * H + o4);
+      g[0] = uu.x > 0.0f ? dd.x : 0.0f;
+      g[1] = uu.y > 0.0f ? dd.y : 0.0f;
+      g[2] = uu.z > 0.0f ? dd.z : 0.0f;
+      g[3] = uu.w > 0.0f ? dd.w : 0.0f;
+      *reinterpret_cast<float4*>(du + (size_t)r * H + o4) = make_float4(g[0], g[1], g[2], g[3]);
     }
-    Us[rr * LDDU + o] = __uint_as_float(to_tf32(g));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Us[rr * LDDU + o4 + j] = __uint_as_float(to_tf32(g[j]));
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
@@ -1060,11 +1119,13 @@ __device__ void wgrad_chunk(int rows, LoadD load_d, LoadX load_x, float* __restr
   float* Ds = reinterpret_cast<float*>(smem);          // [WG_ROWS][DS]
   float* Xs = Ds + WG_ROWS * DS;                       // [WG_ROWS][XS]: KX inputs, the bias 1, zero padding
   const int r0 = blockIdx.x * WG_ROWS;
+#pragma unroll 8
   for (int i = threadIdx.x; i < WG_ROWS * NO; i += blockDim.x) {
     const int rr = i / NO, o = i % NO, r = r0 + rr;
     const float v = r < rows ? load_d(r, o) : 0.0f;
     Ds[rr * DS + o] = MMA ? __uint_as_float(to_tf32(v)) : v;
   }
+#pragma unroll 8
   for (int i = threadIdx.x; i < WG_ROWS * XS; i += blockDim.x) {
     const int rr = i / XS, k = i % XS, r = r0 + rr;
     const float v = (r < rows) ? (k < KX ? load_x(r, k) : (k == KX ? 1.0f : 0.0f)) : 0.0f;
@@ -1241,6 +1302,7 @@ struct cgp_gnn_s {
   // graph
   int *dst = nullptr, *src = nullptr, *in_ptr = nullptr, *out_ptr = nullptr, *out_edge = nullptr;
   double* ell = nullptr;
+  float2* xyf = nullptr;   // [n] coordinate inputs x / 15, y / 15
   bf16* ef = nullptr;
   // parameters
   float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
@@ -1275,10 +1337,9 @@ int smem_optin(const void* fn, size_t bytes) {
 int gnn_forward(cgp_gnn_s* g, int B, const double* b, const double* phi1, const double* phi2, const double* phi_t,
                 double* x0, cudaStream_t s) {
   const int n = g->n, E = g->E, rn = B * n, re = B * E;
-  const double2* xy = reinterpret_cast<const double2*>(g->m->xy_c);
-  const int C = (n + TILE - 1) / TILE;
-  features_partial_kernel<<<B * C, 256, 0, s>>>(n, C, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, g->fpart);
-  features_rows_kernel<<<B * C, 256, 0, s>>>(n, C, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, phi_t, xy,
+  const int C = (n + SROWS - 1) / SROWS, R = (n + TILE - 1) / TILE;
+  features_partial_kernel<<<B * C, 32, 0, s>>>(n, C, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, g->fpart);
+  features_rows_kernel<<<B * R, 256, 0, s>>>(n, C, R, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, phi_t, g->xyf,
                                              g->fpart, g->f, g->scale, g->target);
   encode_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, g->P, g->f, g->z0, g->h);
   const size_t smem_p = (size_t)(2 * H + TILE) * LDP * sizeof(bf16), smem_u = (size_t)(H + TILE) * LDU * sizeof(bf16);
@@ -1420,7 +1481,7 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = al(off + bytes); return o; };
   const size_t o_dst = take(E * 4), o_src = take(E * 4), o_in = take((n + 1) * 4), o_op = take((n + 1) * 4),
-               o_oe = take(E * 4), o_ell = take(8), o_ef = take((size_t)E * 4 * 2), o_P = take(NPARAM * 4),
+               o_oe = take(E * 4), o_ell = take(8), o_xyf = take((size_t)n * 8), o_ef = take((size_t)E * 4 * 2), o_P = take(NPARAM * 4),
                o_G = take(NPARAM * 4), o_M = take(NPARAM * 4), o_V = take(NPARAM * 4),
                o_Wm = take((size_t)NL * H * KMP * 2), o_Wu = take((size_t)NL * H * KU * 2),
                o_Winf = take((size_t)kInferWElems * 2), o_f = take(rn * FIN * 4),
@@ -1430,7 +1491,7 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
                o_pq = take(std::max<size_t>(B, 2) * n * 2 * H * 4), o_agg = take((size_t)NL * rn * H * 2),
                o_dh = take(rn * H * 4), o_dh2 = take(rn * H * 4), o_du = take(rn * H * 4), o_da = take(rn * H * 4),
                o_dpq = take(rn * 2 * H * 4),
-               o_part = take(g->part_floats * 4), o_fpart = take(B * (size_t)((n + TILE - 1) / TILE) * 3 * 8),
+               o_part = take(g->part_floats * 4), o_fpart = take(B * (size_t)((n + SROWS - 1) / SROWS) * 3 * 8),
                o_ictrl = take(256 + (size_t)CN * 4), o_rres = take((size_t)n * 8),
                o_nptr = take((size_t)(CN + 1) * 4), o_nbr = take(std::max<size_t>(1, nbr.size()) * 4);
   g->bytes = off;
@@ -1446,6 +1507,7 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   g->out_ptr = (int*)(bs + o_op);
   g->out_edge = (int*)(bs + o_oe);
   g->ell = (double*)(bs + o_ell);
+  g->xyf = (float2*)(bs + o_xyf);
   g->ef = (bf16*)(bs + o_ef);
   g->P = (float*)(bs + o_P);
   g->G = (float*)(bs + o_G);
@@ -1497,6 +1559,7 @@ extern "C" int cgp_gnn_create(cgp_mesh mesh, int max_batch, const float* params,
   const double2* xy = reinterpret_cast<const double2*>(m->xy_c);
   edge_length_kernel<<<1, 1024>>>(E, g->dst, g->src, xy, g->ell);
   edge_feature_kernel<<<(E + 255) / 256, 256>>>(E, g->dst, g->src, xy, g->ell, g->ef);
+  coord_feature_kernel<<<(n + 255) / 256, 256>>>(n, xy, g->xyf);
   st = refresh(g, 0);
   if (st == CGP_OK) st = smem_optin((const void*)project_kernel, (size_t)(2 * H + TILE) * LDP * sizeof(bf16));
   if (st == CGP_OK) st = smem_optin((const void*)update_fwd_kernel, (size_t)(H + TILE) * LDU * sizeof(bf16));
@@ -1557,14 +1620,14 @@ extern "C" int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, c
   if ((g->n + NT - 1) / NT > g->infer_grid) return gnn_forward(g, 1, b, phi1, phi2, nullptr, x0, s);
   InferArgs a{};
   a.n = g->n;
-  a.C = (g->n + TILE - 1) / TILE;
+  a.C = (g->n + SROWS - 1) / SROWS;
   a.rowptr = g->m->rowptr;
   a.col = g->m->col;
   a.K = g->m->K;
   a.b = b;
   a.phi1 = phi1;
   a.phi2 = phi2;
-  a.xy = reinterpret_cast<const double2*>(g->m->xy_c);
+  a.xyf = g->xyf;
   a.src = g->src;
   a.in_ptr = g->in_ptr;
   a.ef = g->ef;
