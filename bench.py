@@ -1014,6 +1014,19 @@ def oracle_all_cores(procs, warm_steps, timed_steps):
     return procs * 2 * timed_steps / wall, wall
 
 
+def replica_totals(dev_ms, e2e_ms, solves, world, device="cpu"):
+    """N independent replicas of the workload, one per rank: the job's times are the slowest rank's
+    (max over ranks of each rank's device-timed and end-to-end intervals) and its solves all ranks'.
+    No data-path collective: this is the only exchange, after the timed region."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms, e2e_ms = float(t[0]), float(t[1])
+    return dev_ms, e2e_ms, solves * world
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -1188,13 +1201,8 @@ def main():
     if refs_path:
         import shutil
         shutil.rmtree(os.path.dirname(refs_path), ignore_errors=True)
-    dev_ms, e2e_ms = res["dev_ms"], res["e2e_ms"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=f"cuda:{local_rank}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms, e2e_ms = float(t[0]), float(t[1])
-    total_solves = res["solves"] * world
+    dev_ms, e2e_ms, total_solves = replica_totals(res["dev_ms"], res["e2e_ms"], res["solves"], world,
+                                                  f"cuda:{local_rank}")
     if rank == 0:
         peak = res["peak"]
         line = {
