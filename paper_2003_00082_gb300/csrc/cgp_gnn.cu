@@ -15,14 +15,16 @@
 // The update [h | a] Wu^T runs on the tensor cores the same way.  Its
 // backward is per node as well: dP_i is da_i times the count of the ReLU's
 // open in-edges, dQ_j a sum over the out-edges, and the weight gradients of
-// A and B are sums over node rows; only C's gradient visits the edges.
+// A and B are sums over node rows; C's gradient is summed over each node's
+// in-edges.  The backward's node GEMMs (du Wu and every weight gradient) run
+// on the tensor cores as TF32 x TF32 -> FP32 mma.sync tiles.
 // Activations h, messages m, aggregates a and the dense weights are stored
 // in BF16 (the messages only as they are summed); projections, master
 // weights, Adam moments, gradients and every sum are FP32.  Aggregations and
 // all gradient sums run in a fixed order (no atomics), so training is
 // deterministic.  Inference of one sample (cgp_gnn_predict) is a single
-// cooperative kernel with four grid barriers instead of the launches of the
-// batched forward.
+// cooperative kernel (one grid barrier, then flags between neighbouring node
+// chunks) instead of the launches of the batched forward.
 #include <cuda_bf16.h>
 
 #include <algorithm>
