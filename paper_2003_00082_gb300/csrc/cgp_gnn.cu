@@ -186,45 +186,44 @@ __device__ __forceinline__ double residual_row(int i, const int* __restrict__ ro
 // Input scales in one fixed reduction order, shared by the batched forward
 // and the fused inference kernel so both produce the same bits.  Chunk c of a
 // sample holds rows [c SROWS, (c+1) SROWS) (one fused-inference chunk, so
-// every block of that kernel forms its own); thread t < SROWS takes row
-// c SROWS + t.  A chunk's partial sums of r^2, d^2 and b^2 are warp
-// butterflies added over the warps in order; a sample's totals add the chunk
-// partials per lane (chunks lane, lane + 32, ...) and finish with a butterfly.
+// every block of that kernel forms its own); lane t < SROWS of warp 0 takes
+// row c SROWS + t.  A chunk's partial sums of r^2, d^2 and b^2 are butterflies
+// over those lanes; a sample's totals add the chunk partials per lane
+// (chunks lane, lane + 32, ...) and finish with a butterfly.
+static_assert(SROWS == 16, "a chunk is the first 16 lanes of one warp");
 __device__ __forceinline__ void chunk_partials(int n, int c, const int* __restrict__ rowptr,
                                                const int* __restrict__ col, const double* __restrict__ K,
                                                const double* __restrict__ bs, const double* __restrict__ p1,
-                                               const double* __restrict__ p2, double* red, double* out,
+                                               const double* __restrict__ p2, double* out,
                                                double* __restrict__ r_out) {
-  const int t = threadIdx.x, i = c * SROWS + t, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
-  double v[3] = {0.0, 0.0, 0.0};
-  if (t < SROWS && i < n) {
-    const double r = residual_row(i, rowptr, col, K, bs, p1);
-    if (r_out) r_out[i] = r;
-    const double dd = p1[i] - p2[i];
-    v[0] = r * r;
-    v[1] = dd * dd;
-    v[2] = bs[i] * bs[i];
-  }
+  const int t = threadIdx.x, i = c * SROWS + t;
+  if (t < 32) {
+    double v[3] = {0.0, 0.0, 0.0};
+    if (t < SROWS && i < n) {
+      const double r = residual_row(i, rowptr, col, K, bs, p1);
+      if (r_out) r_out[i] = r;
+      const double dd = p1[i] - p2[i];
+      v[0] = r * r;
+      v[1] = dd * dd;
+      v[2] = bs[i] * bs[i];
+    }
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    if (lane == 0) red[q * 32 + warp] = v[q];
-  }
-  __syncthreads();
-  if (t < 3) {   // one thread per component, warps in order
-    double a = 0.0;
-    for (int w = 0; w < nw; ++w) a += red[t * 32 + w];
-    out[t] = a;
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+      for (int o = SROWS / 2; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+      if (t == q) out[q] = v[q];
+    }
   }
   __syncthreads();
 }
 
-// Warp q (q < 3): scale q of the sample, sc[q] = sqrt(total_q / n) (1 when
+// Warp q (q < 3): scale q of the sample, sc[q] = sqrt(total_q inv_n) (1 when
 // zero), from its C chunk partials, and its inverse isc[q] = 1 / sc[q].  The
 // three components run on three warps (three schedulers): GB300's FP64 pipe
 // is narrow, and one warp's chain of FP64 sums, square root and divisions
 // is the latency here.
-__device__ __forceinline__ void sample_scales(int n, int C, const double* __restrict__ part, double* sc, double* isc) {
+__device__ __forceinline__ void sample_scales(double inv_n, int C, const double* __restrict__ part, double* sc,
+                                              double* isc) {
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int q = threadIdx.x >> 5; q < 3; q += nw) {
     double a = 0.0;
@@ -242,7 +241,7 @@ __device__ __forceinline__ void sample_scales(int n, int C, const double* __rest
     }
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (lane == 0) {
-      const double rr = sqrt(a / n);
+      const double rr = sqrt(a * inv_n);
       sc[q] = rr > 1e-30 ? rr : 1.0;
       isc[q] = 1.0 / sc[q];
     }
@@ -271,18 +270,18 @@ __global__ void features_partial_kernel(int n, int C, const int* __restrict__ ro
                                         const double* __restrict__ K, const double* __restrict__ b,
                                         const double* __restrict__ phi1, const double* __restrict__ phi2,
                                         double* __restrict__ part) {
-  __shared__ double red[3 * 32];
   const int s = blockIdx.x / C, c = blockIdx.x % C;
   const size_t base = (size_t)s * n;
   __shared__ double out[3];
-  chunk_partials(n, c, rowptr, col, K, b + base, phi1 + base, phi2 + base, red, out, nullptr);
+  chunk_partials(n, c, rowptr, col, K, b + base, phi1 + base, phi2 + base, out, nullptr);
   if (threadIdx.x < 3) part[((size_t)s * C + c) * 3 + threadIdx.x] = out[threadIdx.x];
 }
 
 // Batched forward, second pass: scales (from the C scale chunks), input
 // features and (when phi_t is given) targets of TILE rows per block (R row
 // blocks per sample).
-__global__ void features_rows_kernel(int n, int C, int R, const int* __restrict__ rowptr, const int* __restrict__ col,
+__global__ void features_rows_kernel(int n, double inv_n, int C, int R, const int* __restrict__ rowptr,
+                                     const int* __restrict__ col,
                                      const double* __restrict__ K, const double* __restrict__ b,
                                      const double* __restrict__ phi1, const double* __restrict__ phi2,
                                      const double* __restrict__ phi_t, const float2* __restrict__ xyf,
@@ -291,7 +290,7 @@ __global__ void features_rows_kernel(int n, int C, int R, const int* __restrict_
   __shared__ double sc[3], isc[3];
   const int s = blockIdx.x / R, c = blockIdx.x % R;
   const size_t base = (size_t)s * n;
-  sample_scales(n, C, part + (size_t)s * C * 3, sc, isc);
+  sample_scales(inv_n, C, part + (size_t)s * C * 3, sc, isc);
   if (c == 0 && threadIdx.x == 0) scale[s] = sc[1];
   const double ir = isc[0], id = isc[1], ib = isc[2];
   const int i = c * TILE + threadIdx.x;
@@ -476,6 +475,7 @@ __global__ void decode_kernel(int rows, int n, const float* __restrict__ P, cons
 // ---------------------------------------------------------------------------
 struct InferArgs {
   int n, C;
+  double inv_n;   // 1 / n
   const int* rowptr;
   const int* col;
   const double* K;
@@ -605,7 +605,6 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
   bf16* X = Wus + NL * H * LDU;                            // [NT][LDU]: h | a of the update
   bf16* Xh = X + NT * LDU;                                 // [NT][LDP]: h of the projection
   int* srcs = reinterpret_cast<int*>(Xh + NT * LDP);       // [EIC]
-  __shared__ double red[3 * 32];
   __shared__ double sc[3], isc[3];
   __shared__ float bias[NL][2][H];   // bm, bu of every layer
   __shared__ float cm[NL][3][H];     // C of every layer (as its BF16 values)
@@ -726,7 +725,7 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
   }
   // ---- scale partials (16-row chunks: a block's own chunk when it has one) ----
   for (int c = blockIdx.x; c < C; c += gridDim.x) {
-    chunk_partials(n, c, a.rowptr, a.col, a.K, a.b, a.phi1, a.phi2, red, sc, a.res);
+    chunk_partials(n, c, a.rowptr, a.col, a.K, a.b, a.phi1, a.phi2, sc, a.res);
     if (tid < 3) a.part[c * 3 + tid] = sc[tid];
     __syncthreads();
   }
@@ -734,7 +733,7 @@ __global__ void __launch_bounds__(256) infer_kernel(InferArgs a) {
   // warp 1 waits for the weight copies while warp 0 folds the scales
   __shared__ int wok;
   if (tid == 32) wok = weights_wait(0) ? 1 : 0;   // [A; B] of layer 0
-  sample_scales(n, C, a.part, sc, isc);   // ends with the block's barrier
+  sample_scales(a.inv_n, C, a.part, sc, isc);   // ends with the block's barrier
   if (!wok) { give_up(); return; }
   if (blockIdx.x == 0 && tid == 0) a.scale[0] = sc[1];
   // ---- features, encoder and the first layer's projections of the block's node chunks ----
@@ -1341,7 +1340,7 @@ int gnn_forward(cgp_gnn_s* g, int B, const double* b, const double* phi1, const 
   const int n = g->n, E = g->E, rn = B * n, re = B * E;
   const int C = (n + SROWS - 1) / SROWS, R = (n + TILE - 1) / TILE;
   features_partial_kernel<<<B * C, 32, 0, s>>>(n, C, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, g->fpart);
-  features_rows_kernel<<<B * R, 256, 0, s>>>(n, C, R, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, phi_t, g->xyf,
+  features_rows_kernel<<<B * R, 256, 0, s>>>(n, 1.0 / n, C, R, g->m->rowptr, g->m->col, g->m->K, b, phi1, phi2, phi_t, g->xyf,
                                              g->fpart, g->f, g->scale, g->target);
   encode_kernel<<<(rn * H + 255) / 256, 256, 0, s>>>(rn, g->P, g->f, g->z0, g->h);
   const size_t smem_p = (size_t)(2 * H + TILE) * LDP * sizeof(bf16), smem_u = (size_t)(H + TILE) * LDU * sizeof(bf16);
@@ -1623,6 +1622,7 @@ extern "C" int cgp_gnn_predict(cgp_gnn g, const double* b, const double* phi1, c
   InferArgs a{};
   a.n = g->n;
   a.C = (g->n + SROWS - 1) / SROWS;
+  a.inv_n = 1.0 / g->n;
   a.rowptr = g->m->rowptr;
   a.col = g->m->col;
   a.K = g->m->K;
