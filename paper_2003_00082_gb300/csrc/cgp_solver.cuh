@@ -71,6 +71,15 @@ struct Desc {
 // null space and b, x0 and x are not projected to mean zero.
 __device__ __forceinline__ bool is_fixed(const Desc& d, int i) { return d.fixed && d.fixed[i]; }
 
+// Tests of a double on its bits (integer instructions).
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7FF) != 0x7FF;
+}
+__device__ __forceinline__ bool positive_bits(double x) { return __double_as_longlong(x) > 0; }   // > +0 or NaN
+__device__ __forceinline__ bool nonneg_le(double x, double y) {   // x <= y for x, y >= 0
+  return __double_as_longlong(x) <= __double_as_longlong(y);
+}
+
 template <typename V>
 __device__ __forceinline__ V warp_sum(V v) {
 #pragma unroll
@@ -1133,22 +1142,24 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       }
     };
     // scalars (thread 0): sc[0] alpha, sc[1] beta, sc[2] gamma, sc[5] (r,r), isc[0] stop flag;
-    // sc[3] = 1 / gamma_old and sc[6] = 1 / alpha_old are prepared off the critical path
+    // sc[3] = 1 / gamma_old, sc[6] = 1 / alpha_old and sc[7] = sc[3] sc[6] are prepared off the critical path
     int k = 0;
     auto derive = [&](Shared& S) {
       const double g = S.tot[0], dl = S.tot[1], rr = S.tot[2];
+      // the tests look at the bits (integer pipe): this thread's chain of FP64
+      // operations is the latency of every iteration on GB300's narrow FP64 pipe
       int st = -1;
-      if (!isfinite(g) || !isfinite(dl) || !isfinite(rr)) st = CGP_ERR_NONFINITE;
-      else if (rr <= S.sc[4]) st = CGP_OK;
+      if (!finite_bits(g) || !finite_bits(dl) || !finite_bits(rr)) st = CGP_ERR_NONFINITE;
+      else if (nonneg_le(rr, S.sc[4])) st = CGP_OK;   // (r,r) and (tol |b|)^2 are >= 0
       else if (its + k >= d.max_it) st = CGP_ERR_NOT_CONVERGED;
       double beta = 0.0, alpha;
       if (k == 0) {
         alpha = g / dl;
-      } else {
+      } else {   // dl - beta gamma / alpha_old with beta = gamma / gamma_old; sc[7] = 1 / (gamma_old alpha_old)
         beta = g * S.sc[3];
-        alpha = g / (dl - beta * g * S.sc[6]);
+        alpha = g / fma(-g * g, S.sc[7], dl);
       }
-      if (st < 0 && !(g > 0.0 && alpha > 0.0 && isfinite(alpha))) st = CGP_ERR_BREAKDOWN;
+      if (st < 0 && !(positive_bits(g) && positive_bits(alpha) && finite_bits(alpha))) st = CGP_ERR_BREAKDOWN;
       S.isc[0] = st;
       S.sc[0] = alpha;
       S.sc[1] = beta;
@@ -1166,6 +1177,7 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       if (tid == 32 || (bd == 32 && tid == 0)) {
         sh.sc[3] = 1.0 / sh.sc[2];
         sh.sc[6] = 1.0 / sh.sc[0];
+        sh.sc[7] = sh.sc[3] * sh.sc[6];
       }
       const double alpha = sh.sc[0], beta = sh.sc[1];
       const double* Rc = (k & 1) ? R1 : R0;
