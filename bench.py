@@ -66,8 +66,8 @@ def workload_config(precision="fp64"):
 SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_pcg_batch.cu", "cgp_pipe.cu", "cgp_solver.cuh", "cgp_sync.h", "cgp_fixed.h",
                   "cgp_internal.h")
 SOLVER_TRAFFIC = {
-    "sha256": "f585b3484a3dbdd670b5ac07a986ada8a60ab8092e3787626d29d36214f435e3",
-    "fp64": 10376704 + 300032,
+    "sha256": "91a6d63842945a739b3959d7ba1f76d7ae73c757451096e81fd34abc0d317406",
+    "fp64": 10376960 + 316416,
 }
 
 
