@@ -276,8 +276,9 @@ int cgp_poisson_solve_noalloc(int n, const int* rowptr, const int* col, const do
  *                     fit on an SM) and flags (bit 0: rows in global
  *                     memory; bit 1: FP64 textbook iteration, as for
  *                     cgp_set_tuning; bit 2: one packed launch, not waves;
- *                     bit 3: tagged reductions and bit 4: pipelined FP64
- *                     iteration, as for cgp_set_tuning; bits 5-6: waves
+ *                     bit 3: tagged reductions (FP64 and mixed) and
+ *                     bit 4: pipelined FP64 iteration, as for
+ *                     cgp_set_tuning; bits 5-6: waves
  *                     with 256 << k rows per block).  INVALID_ARG for other
  *                     bits.
  * cgp_batch_autotune  times a set of launch shapes on the batch's own
@@ -442,11 +443,13 @@ int cgp_mesh_set_ogrid(cgp_mesh m, int n_theta, int n_r);
  *         is a compact patch of the mesh (smaller halos; b and x pass through
  *         a gather and a scatter launch; the renumbered system is built once
  *         per block count and boundary condition, about 12 nnz + 45 n_c
- *         bytes); bit 3 (FP64 single-reduction form only) passes each
- *         grid-wide reduction through tagged 128-bit slots that show by
- *         themselves when every block has stored its partial sum, instead of
- *         a barrier counter followed by a read of the slots (the same totals,
- *         bit for bit); bit 4 (FP64, rows in shared memory, at least 256
+ *         bytes); bit 3 (the FP64 single-reduction form, and the FP32 inner
+ *         iterations of MIXED) passes each grid-wide reduction through tagged
+ *         slots that show by themselves when every block has stored its
+ *         partial sum, polled while the barrier counter fills, instead of a
+ *         read of the slots after the barrier (FP32: the same totals, bit for
+ *         bit; FP64: 64-bit fixed-point partials, exact up to a truncation
+ *         2^-54 below a warp's or block's largest term); bit 4 (FP64, rows in shared memory, at least 256
  *         threads per block and 1, 2 or 4 lanes per row; otherwise the
  *         single-reduction form runs) runs the pipelined iteration of
  *         Ghysels and Vanroose: four warps of every block complete the
@@ -481,8 +484,8 @@ int cgp_get_tuning(cgp_mesh m, int what, int* block, int* lanes, int* blocks, in
  * the caller's right-hand side b (device [n_c]) for every candidate of
  * threads per block {256, 512}, lanes per CSR row {1, 2, 4}, grid size (a
  * few counts around the SM count, and 1..16 blocks for small systems),
- * shared-memory residency, the row order (flag bit 2) and, for FP64, the
- * iteration form (flag bits 1 and 4), the reduction form (flag bit 3) and,
+ * shared-memory residency, the row order (flag bit 2), the reduction form
+ * (flag bit 3) and, for FP64, the iteration form (flag bits 1 and 4) and,
  * on meshes registered with cgp_mesh_set_ogrid, the O-grid tiles with the
  * stencil product (flag bit 5); only candidates that converge count,
  * and keeps the fastest with cgp_set_tuning.  Every candidate meets the

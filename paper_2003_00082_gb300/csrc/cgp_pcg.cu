@@ -1431,14 +1431,18 @@ extern "C" int cgp_batch_autotune(cgp_batch batch, void* stream, double* best_ms
   const int lanes[2] = {1, 2};
   const int per_sm[2] = {1, 2};
   const int rows[3] = {0, 2, 3};   // waves: 256, 1024 or 2048 rows a block (flags bits 5-6)
-  const int nflags = batch->opts.precision == CGP_MIXED ? 2 : 4;
+  // iteration flags: rows in global memory (bit 0), tagged reductions (bit 3), and for FP64 the textbook form (bit 1)
+  const int mixed_fl[3] = {0, 1, 8}, fp64_fl[6] = {0, 1, 2, 3, 8, 9};
+  const bool mixed_b = batch->opts.precision == CGP_MIXED;
+  const int* base_fl = mixed_b ? mixed_fl : fp64_fl;
+  const int nflags = mixed_b ? 3 : 6;
   for (int fl = 0; fl < 2 * nflags; ++fl)   // bit 2 (one packed launch instead of waves) on top
     for (int rw : rows)
       for (int bk : blocks)
         for (int ln : lanes)
           for (int ps : per_sm) {
             if (rw && (fl >= nflags || ps > 1)) continue;   // more rows a block: waves, one block per SM
-            BatchShape cand{bk, ln, ps, (fl % nflags) | (fl >= nflags ? 4 : 0) | (rw << 5)};
+            BatchShape cand{bk, ln, ps, base_fl[fl % nflags] | (fl >= nflags ? 4 : 0) | (rw << 5)};
             if (batch_plan_any(batch, cand, o) != CGP_OK) continue;
             float t = 1e30f;
             for (int rep = 0; rep < 2; ++rep) {
@@ -1565,14 +1569,14 @@ extern "C" int cgp_autotune(cgp_mesh m, int precision, const double* b, double* 
   const SolverTuning saved = m->tune[what];
   SolverTuning best{};
   float best_t = 1e30f;
-  // bit 1 (classic FP64 iteration), bit 3 (tagged reductions of the
-  // single-reduction form), bit 4 (pipelined iteration, rows resident,
-  // reductions always tagged) and bit 5 (O-grid tiles with the stencil
-  // product, single-reduction form, registered O-grids only) only for FP64;
-  // bit 2 (bisection order) for both
+  // bit 1 (classic FP64 iteration), bit 4 (pipelined iteration, rows
+  // resident, reductions always tagged) and bit 5 (O-grid tiles with the
+  // stencil product, single-reduction form, registered O-grids only) only for
+  // FP64; bit 2 (bisection order) and bit 3 (tagged reductions: of the
+  // single-reduction form, or of the FP32 inner iterations) for both
   std::vector<int> flag_set;
   for (int fl = 0; fl < 64; ++fl) {
-    if (precision == CGP_MIXED && (fl & 58)) continue;
+    if (precision == CGP_MIXED && (fl & 50)) continue;   // mixed: bits 0, 2 and 3
     if ((fl & 2) && (fl & 8)) continue;
     if ((fl & 16) && (fl & 11)) continue;
     if ((fl & 32) && ((fl & 23) || m->st_nt <= 0)) continue;

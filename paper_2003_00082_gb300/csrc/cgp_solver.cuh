@@ -1286,6 +1286,22 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
 // FP32 reductions of the inner solve: warp trees on the FP32 pipe, one slot
 // per block, every block sums the slots in the same order (deterministic).
 // ---------------------------------------------------------------------------
+// Tagged FP32 partials (tuning flag bit 3): the partial of component c of
+// reduction red from block blk is one 64-bit word, the FP32 bits low and
+// red + 1 high, in the tagged-slot area (a single-copy atomic store; the
+// block zeroes its words at launch start).  Banks by the reduction's parity.
+__device__ __forceinline__ unsigned long long* ftag_slot(const Desc& d, int red, int c, int blk) {
+  return reinterpret_cast<unsigned long long*>(d.tpart) + ((size_t)((red & 1) * 3 + c) * d.part_stride + blk);
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 template <int NC>
 __device__ __forceinline__ void put_partials_f(const Desc& d, int lb, int red, const float (&v)[NC], Shared& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1294,15 +1310,79 @@ __device__ __forceinline__ void put_partials_f(const Desc& d, int lb, int red, c
     const float s = warp_sum(v[c]);
     if (lane == 0) sh.fred[c][warp] = s;
   }
+  if (d.tagged && threadIdx.x == 0) sh.tflag = 1;
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       float s = lane < nw ? sh.fred[c][lane] : 0.0f;
       s = warp_sum(s);
-      if (lane == 0) d.fpart[((red & 1) * NCOMP + c) * d.part_stride + lb] = s;
+      if (lane == 0) {
+        if (d.tagged)
+          st_relaxed_u64(ftag_slot(d, red, c, lb),
+                         ((unsigned long long)(unsigned)(red + 1) << 32) | (unsigned long long)__float_as_uint(s));
+        else
+          d.fpart[((red & 1) * NCOMP + c) * d.part_stride + lb] = s;
+      }
     }
   }
+}
+
+// One warp: component c of tagged FP32 reduction red, summed in the order
+// of get_totals_f_then (lane l adds blocks l, l + 32, ..., then a butterfly):
+// the same bits.  Each lane polls its words with relaxed loads, all issued
+// before any is examined, until they carry the tag.  Gives up (false on every
+// lane) after d.spin_ns or when another block has given up.
+__device__ __forceinline__ bool ftagged_total(const Desc& d, int red, int c, float& total) {
+  constexpr int PRE = 8;
+  const int lane = threadIdx.x & 31;
+  const unsigned tag = (unsigned)(red + 1);
+  int* const timeout = &d.res->timeout;
+  float acc = 0.0f;
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+  for (int base = 0; base < d.nblk; base += 32 * PRE) {
+    unsigned long long w[PRE];
+    unsigned pend = 0;
+#pragma unroll
+    for (int t = 0; t < PRE; ++t) {
+      w[t] = 0ull;
+      if (base + lane + 32 * t < d.nblk) pend |= 1u << t;
+    }
+    const unsigned have = pend;
+    while (true) {
+      const unsigned pm = pend;
+#pragma unroll
+      for (int t = 0; t < PRE; ++t)
+        if (pm & (1u << t)) w[t] = ld_relaxed_u64(ftag_slot(d, red, c, base + lane + 32 * t));
+#pragma unroll
+      for (int t = 0; t < PRE; ++t)
+        if ((pm & (1u << t)) && (unsigned)(w[t] >> 32) == tag) pend &= ~(1u << t);
+      if (__all_sync(0xffffffffu, pend == 0)) break;
+      if ((++spins & 63u) == 0) {
+        int give_up = 0;
+        if (lane == 0) {
+          if (*(volatile int*)timeout) {
+            give_up = 1;
+          } else {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) {
+              t0 = now;
+            } else if ((long long)(now - t0) > d.spin_ns) {
+              atomicExch(timeout, 1);
+              give_up = 1;
+            }
+          }
+        }
+        if (__shfl_sync(0xffffffffu, give_up, 0)) return false;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < PRE; ++t)
+      if (have & (1u << t)) acc += __uint_as_float((unsigned)w[t]);
+  }
+  total = warp_sum(acc);
+  return true;
 }
 
 template <int NC, typename F>
@@ -1320,6 +1400,37 @@ __device__ __forceinline__ void get_totals_f_then(const Desc& d, int red, Shared
     if (lane == 0) derive(sh);
   }
   __syncthreads();
+}
+
+// Finish of an FP32 inner reduction, after put_partials_f and grp.arrive().
+// Untagged: the barrier, then warp 0 reads the slots (get_totals_f_then)
+// while the other threads run stage().  Tagged (d.tagged): warps 0 .. NC-1
+// poll the tagged words while one more thread waits on the barrier, so the
+// totals are known when it completes; then stage() and the derivation.
+template <int NC, typename F, typename G>
+__device__ __forceinline__ bool red_finish_f(const Desc& d, Group& grp, int red, Shared& sh, F derive, G stage) {
+  if (!d.tagged) {
+    if (!grp.wait(sh)) return false;
+    stage();
+    get_totals_f_then<NC>(d, red, sh, derive);
+    return true;
+  }
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < NC; c += nw) {
+    float t;
+    if (!ftagged_total(d, red, c, t)) {
+      if ((threadIdx.x & 31) == 0) sh.tflag = 0;
+      break;
+    }
+    if ((threadIdx.x & 31) == 0) sh.ftot[c] = t;
+  }
+  if (threadIdx.x == (nw > NC ? 32 * NC : 0) && !grp.wait_one()) sh.tflag = 0;
+  __syncthreads();
+  if (!sh.tflag) return false;
+  stage();
+  if (threadIdx.x == 0) derive(sh);
+  __syncthreads();
+  return true;
 }
 
 // FP32 SpMV over the block's rows reading the global CSR: own columns from
@@ -1460,6 +1571,9 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
   double* bp = d.bp + r0;
   double* r64 = d.r + r0;
 
+  // tagged inner reductions: this block's words start empty; the first
+  // barrier orders that before any block reads them
+  if (d.tagged && tid < 6) *ftag_slot(d, tid / 3, tid % 3, lb) = 0ull;
   // ---- projected b and x0 ----
   {
     double v2[2] = {0.0, 0.0};
@@ -1563,7 +1677,7 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
                         [&](int j) { return d.dinv32[j] * __ldcg(R0 + j); }, op);
       }
       put_partials_f<3>(d, lb, red, v3, sh);
-      if (!grp.sync(sh)) return;
+      grp.arrive();   // finished below by red_finish_f (nothing in between writes what other blocks read)
     }
     // scalars (thread 0): sc[0] alpha, sc[1] beta, sc[2] gamma, isc[0] stop flag
     int k = 0;
@@ -1593,24 +1707,45 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
       const double floor = 0.5 * d.tol * bnorm;
       sh.fsc[5] = (float)(floor * floor);
     }
-    // RES: while warp 0 fetches the reduction's totals, the other warps stage
-    // the halo inputs r_j, w_j, s_j of the coming iteration, so the two global
-    // round trips overlap
-    const bool staged = RES && bd > 32;
+    // RES: after the barrier, the threads above the reduction's warps stage
+    // the halo inputs r_j, w_j, s_j of the coming iteration.  Untagged, into
+    // shared memory while warp 0 fetches the totals (the two global round
+    // trips overlap).  Tagged, the totals are already known: a thread's first
+    // HREG entries go to registers and are consumed by the same thread after
+    // the own-row update, so the loads overlap the derivation and that update;
+    // further entries go through shared memory (the same thread reads them).
+    constexpr int HREG = 2;
+    const int TWs = d.tagged ? 96 : 32;
+    const bool staged = RES && bd > TWs;
+    float hR[HREG], hW[HREG], hS[HREG];
+#pragma unroll
+    for (int q = 0; q < HREG; ++q) hR[q] = hW[q] = hS[q] = 0.0f;
     auto stage = [&](int kk) {
-      if (!staged || tid < 32) return;
+      if (!staged || tid < TWs) return;
       const float* Rc = (kk & 1) ? R1 : R0;
       const float* Wc = (kk & 1) ? W1 : W0;
       const float* Sc = (kk & 1) ? S1 : S0;
-      for (int h = tid - 32; h < nh; h += bd - 32) {
+      const int hs = bd - TWs;
+      int h = tid - TWs;
+      if (d.tagged) {
+#pragma unroll
+        for (int q = 0; q < HREG; ++q, h += hs) {
+          if (h < nh) {
+            const int j = hid[h];
+            hR[q] = __ldcg(Rc + j);
+            hW[q] = __ldcg(Wc + j);
+            if (kk > 0) hS[q] = __ldcg(Sc + j);
+          }
+        }
+      }
+      for (; h < nh; h += hs) {
         const int j = hid[h];
         stR[h] = __ldcg(Rc + j);
         stW[h] = __ldcg(Wc + j);
         if (kk > 0) stS[h] = __ldcg(Sc + j);
       }
     };
-    stage(0);
-    get_totals_f_then<3>(d, red, sh, derive);
+    if (!red_finish_f<3>(d, grp, red, sh, derive, [&] { stage(0); })) return;
     ++red;
     bool bad = false;
     while (true) {
@@ -1646,7 +1781,23 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
         return dj * fmaf(-alpha, sj, __ldcg(Rc + j));
       };
       if constexpr (RES) {
-        if (staged) {
+        if (staged && d.tagged) {
+          if (tid >= TWs) {   // the entries this thread staged
+            const int hs = bd - TWs;
+            int h = tid - TWs;
+#pragma unroll
+            for (int q = 0; q < HREG; ++q, h += hs) {
+              if (h < nh) {
+                const float sj = k == 0 ? hW[q] : fmaf(beta, hS[q], hW[q]);
+                ext[nloc + h] = dih[h] * fmaf(-alpha, sj, hR[q]);
+              }
+            }
+            for (; h < nh; h += hs) {
+              const float sj = k == 0 ? stW[h] : fmaf(beta, stS[h], stW[h]);
+              ext[nloc + h] = dih[h] * fmaf(-alpha, sj, stR[h]);
+            }
+          }
+        } else if (staged) {
           for (int h = tid; h < nh; h += bd) {
             const float sj = k == 0 ? stW[h] : fmaf(beta, stS[h], stW[h]);
             ext[nloc + h] = dih[h] * fmaf(-alpha, sj, stR[h]);
@@ -1672,10 +1823,9 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
                         [&](int j) { return halo_u(j, d.dinv32[j]); }, op);
       }
       put_partials_f<3>(d, lb, red, v3, sh);
-      if (!grp.sync(sh)) return;
+      grp.arrive();
       ++k;
-      stage(k);
-      get_totals_f_then<3>(d, red, sh, derive);
+      if (!red_finish_f<3>(d, grp, red, sh, derive, [&] { stage(k); })) return;
       ++red;
     }
     total += k;

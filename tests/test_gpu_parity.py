@@ -221,7 +221,8 @@ def test_fp64_solve_with_initial_guess(pair, cgp):
 
 
 MIXED_SHAPES = [(0, 0, 0, 0), (128, 1, 3, 0), (128, 2, 5, 1), (256, 4, 7, 0), (64, 8, 2, 1), (64, 1, 13, 0),
-                (0, 0, 0, 4), (128, 1, 5, 5), (256, 2, 7, 4)]
+                (0, 0, 0, 4), (128, 1, 5, 5), (256, 2, 7, 4), (256, 1, 7, 8), (128, 2, 13, 12), (512, 1, 3, 8),
+                (64, 1, 2, 8)]
 
 
 @pytest.mark.parametrize("block,lanes,blocks,flags", MIXED_SHAPES)
