@@ -1107,8 +1107,8 @@ def profile_case(case):
         prec = cgp.CGP_MIXED if case == "mixed" else cgp.CGP_FP64
         what = cgp.CGP_TUNE_SOLVE_MIXED if case == "mixed" else cgp.CGP_TUNE_SOLVE_FP64
         # the shape the autotuner picks on GB300 (FP64: O-grid tiles with the stencil product and tagged
-        # reductions; mixed: rows renumbered by coordinate bisection)
-        cgp.cgp_set_tuning(m.handle, what, 512, 1, 152, 4 if case == "mixed" else 40)
+        # reductions; mixed: tagged FP32 inner reductions)
+        cgp.cgp_set_tuning(m.handle, what, 512, 1, 152, 8 if case == "mixed" else 40)
         for _ in range(2):
             x.zero_()
             info = cgp.cgp_poisson_solve(m.handle, b, x, tol=TOL, precision=prec)
