@@ -66,8 +66,8 @@ def workload_config(precision="fp64"):
 SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_pcg_batch.cu", "cgp_pipe.cu", "cgp_solver.cuh", "cgp_sync.h", "cgp_fixed.h",
                   "cgp_internal.h")
 SOLVER_TRAFFIC = {
-    "sha256": "91a6d63842945a739b3959d7ba1f76d7ae73c757451096e81fd34abc0d317406",
-    "fp64": 10376960 + 316416,
+    "sha256": "4d36b4922f8f522f18c14ffed354ae48571aa678add0ba4e87afc564a55bb2a8",
+    "fp64": 10376192 + 293632,
 }
 
 
