@@ -1761,19 +1761,23 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
       float* Rn = (k & 1) ? R0 : R1;
       float* Wn = (k & 1) ? W0 : W1;
       float* Sn = (k & 1) ? S0 : S1;
-      // own rows: p, s, e, r, u
+      // own rows: s, r and u_(k+1) (RES: into the product's input, while iu
+      // keeps u_k for the update of p and e during the reduction's wait; without
+      // RES also p and e here)
       for (int i = tid; i < nloc; i += bd) {
-        const float pi = k == 0 ? iu[i] : fmaf(beta, ip[i], iu[i]);
         const float si = k == 0 ? iw[i] : fmaf(beta, is[i], iw[i]);
-        ip[i] = pi;
+        if (!RES) {
+          const float pi = k == 0 ? iu[i] : fmaf(beta, ip[i], iu[i]);
+          ip[i] = pi;
+          ie[i] = fmaf(alpha, pi, ie[i]);
+        }
         is[i] = si;
-        ie[i] = fmaf(alpha, pi, ie[i]);
         const float ri = fmaf(-alpha, si, ir[i]);
         ir[i] = ri;
-        iu[i] = di[i] * ri;
+        if (RES) ext[i] = di[i] * ri;
+        else iu[i] = di[i] * ri;
         Rn[r0 + i] = ri;
         Sn[r0 + i] = si;
-        if (RES) ext[i] = di[i] * ri;
       }
       // halo: u_j = D^-1_j (r_j - alpha (w_j + beta s_j)) from the owner's published values
       auto halo_u = [&](int j, float dj) {
@@ -1811,7 +1815,7 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
       auto op = [&](int il, float s) {
         iw[il] = s;
         Wn[r0 + il] = s;
-        const float u = iu[il], r = ir[il];
+        const float u = RES ? ext[il] : iu[il], r = ir[il];
         v3[0] = fmaf(r, u, v3[0]);
         v3[1] = fmaf(s, u, v3[1]);
         v3[2] = fmaf(r, r, v3[2]);
@@ -1824,6 +1828,14 @@ __device__ void solve_mixed(const Desc& d, int lb, Shared& sh) {
       }
       put_partials_f<3>(d, lb, red, v3, sh);
       grp.arrive();
+      if constexpr (RES) {   // p_k = u_k + beta p_(k-1), e += alpha p_k, then u_(k+1), while the other blocks arrive
+        for (int i = tid; i < nloc; i += bd) {
+          const float pi = k == 0 ? iu[i] : fmaf(beta, ip[i], iu[i]);
+          ip[i] = pi;
+          ie[i] = fmaf(alpha, pi, ie[i]);
+          iu[i] = ext[i];
+        }
+      }
       ++k;
       if (!red_finish_f<3>(d, grp, red, sh, derive, [&] { stage(k); })) return;
       ++red;
