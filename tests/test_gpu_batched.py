@@ -112,6 +112,23 @@ def test_batched_launch_shapes(cgp, systems, block, lanes, per_sm, flags):
     batch.close()
 
 
+@pytest.mark.parametrize("block,lanes,per_sm,flags", [(512, 1, 1, 8), (512, 1, 1, 104), (256, 2, 1, 8), (512, 1, 0, 12)])
+def test_batched_mixed_tagged_shapes(cgp, systems, block, lanes, per_sm, flags):
+    """Mixed precision with tagged FP32 inner reductions (flag bit 3), alone, with 2048 rows a block and in
+    one packed launch: every instance still reaches the oracle's answer."""
+    bs = [T(s["b"]) for s in systems]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch = cgp.Batch([s["mesh"] for s in systems], bs, xs, tol=1e-10, precision=cgp.CGP_MIXED)
+    batch.set_tuning(block, lanes, per_sm, flags)
+    batch.solve()
+    infos, _ = batch.info()
+    for s, x, info in zip(systems, xs, infos):
+        assert info["status"] == cgp.CGP_OK, info
+        assert info["rel_res_true"] <= 1.1e-10
+        assert rel(x.cpu().numpy(), s["exact"]) <= 1e-7
+    batch.close()
+
+
 def test_batched_solve_replays_in_a_cuda_graph(cgp, systems):
     bs = [T(s["b"]) for s in systems]
     xs = [torch.zeros_like(b) for b in bs]
