@@ -66,8 +66,8 @@ def workload_config(precision="fp64"):
 SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_pcg_batch.cu", "cgp_pipe.cu", "cgp_solver.cuh", "cgp_sync.h", "cgp_fixed.h",
                   "cgp_internal.h")
 SOLVER_TRAFFIC = {
-    "sha256": "4d36b4922f8f522f18c14ffed354ae48571aa678add0ba4e87afc564a55bb2a8",
-    "fp64": 10376192 + 293632,
+    "sha256": "2bc5add2d51982cd3c52c3d2d1ca5824f6bf1c678c4003edf0f0df86d33ab555",
+    "fp64": 10377472 + 358144,
 }
 
 
