@@ -516,9 +516,10 @@ def run_mine(args, rank, world, local_rank, refs_path=None):
     return result
 
 
-def run_batched(cgp, inputs, configs, torch, dev, flush, peak, reps=5):
+def run_batched(cgp, inputs, configs, torch, dev, flush, peak, reps=5, tuning=None):
     """64 uneven CGP potential solves (n_theta in {64,...,512}), mixed precision, in the batched persistent
-    solver (wave-scheduled launches or one packed launch, as its autotuner picks) replayed from a CUDA graph."""
+    solver (wave-scheduled launches or one packed launch, as its autotuner picks, or the shape `tuning` =
+    (block, lanes, blocks_per_sm, flags) fixes) replayed from a CUDA graph."""
     insts = configs.batched_instances()
     meshes, bs, xs = [], [], []
     for inst in insts:
@@ -533,7 +534,11 @@ def run_batched(cgp, inputs, configs, torch, dev, flush, peak, reps=5):
         bs.append(b)
         xs.append(torch.zeros_like(b))
     batch = cgp.Batch(meshes, bs, xs, tol=TOL, precision=cgp.CGP_MIXED, inner_tol=1e-4)
-    tune_ms = batch.autotune()
+    if tuning is None:
+        tune_ms = batch.autotune()
+    else:
+        batch.set_tuning(*tuning)
+        tune_ms = None
     # capture the launch once; replays need no host work
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
@@ -1133,8 +1138,11 @@ def profile_case(case):
         net.close()
         m.close()
     elif case == "batched":
+        # the shape the batch autotuner picks on GB300 (waves of 2048 rows a block, one 512-thread block per
+        # SM, tagged FP32 inner reductions), so that a profiler sees the timed launches and no candidates;
+        # two replays of the captured waves
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        out = run_batched(cgp, inputs, configs, torch, dev, flush, read_peaks()[0], reps=1)
+        out = run_batched(cgp, inputs, configs, torch, dev, flush, read_peaks()[0], reps=1, tuning=(512, 1, 1, 104))
         print(json.dumps({"case": case, "value": out["value"], "launch": out["launch"]}))
     else:
         out = spmv_bench(cgp, inputs, torch, dev, read_peaks()[0], reps=2)
