@@ -62,22 +62,28 @@ def workload_config(precision="fp64"):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one persistent
 # solver launch, from one ncu capture of `bench.py --profile-case <precision>`
 # (the bench's launch shape).  They hold only for the kernel sources they were
-# taken on: when the sources' hash differs the traffic is reported as null.
+# taken on and for the captured launch's tuning flags: when the sources' hash
+# or the benchmarked flags differ the traffic is reported as null.
 SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_pcg_batch.cu", "cgp_pipe.cu", "cgp_solver.cuh", "cgp_sync.h", "cgp_fixed.h",
                   "cgp_internal.h")
 SOLVER_TRAFFIC = {
     "sha256": "2bc5add2d51982cd3c52c3d2d1ca5824f6bf1c678c4003edf0f0df86d33ab555",
     "fp64": 10377472 + 358144,
+    "flags": {"fp64": 40},
 }
 
 
-def solver_traffic(precision):
+def solver_traffic(precision, flags=None):
     import hashlib
     h = hashlib.sha256()
     for f in SOLVER_SOURCES:
         with open(os.path.join(ROOT, "paper_2003_00082_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return SOLVER_TRAFFIC.get(precision) if h.hexdigest() == SOLVER_TRAFFIC["sha256"] else None
+    if h.hexdigest() != SOLVER_TRAFFIC["sha256"]:
+        return None
+    if flags is not None and SOLVER_TRAFFIC["flags"].get(precision) not in (None, flags):
+        return None
+    return SOLVER_TRAFFIC.get(precision)
 
 
 def read_peaks():
@@ -1220,7 +1226,7 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic", "config": workload_config(args.precision),
             "roofline": {"bound": "hbm", "achieved": res["achieved"], "peak": peak, "unit": "GB/s",
-                         "frac": res["achieved"] / peak, "traffic": solver_traffic(args.precision),
+                         "frac": res["achieved"] / peak, "traffic": solver_traffic(args.precision, res["tuned"][args.precision]["flags"]),
                          "kernel": "pcg_persistent_kernel",
                          "alg_bytes_per_launch": res["alg_bytes_per_launch"],
                          "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({res['peak_kind']})",

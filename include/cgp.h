@@ -456,13 +456,18 @@ int cgp_mesh_set_ogrid(cgp_mesh m, int n_theta, int n_r);
  *         iteration's grid reduction and fetch the next halo while the others
  *         form the next product, at the price of three more FP64 vector
  *         operations per row and recurrences that drift sooner (a restart
- *         from the true residual near tight tolerances); bit 5 (FP64
- *         single-reduction form, meshes registered with cgp_mesh_set_ogrid,
- *         rows in shared memory) renumbers the rows into near-rectangular
- *         tiles of the O-grid's (angle, ring) index grid, one per block, and
- *         forms every product with the seven-point stencil on the block's
- *         padded box (no column indices; bit 2 is then ignored); other bits
- *         must be 0.
+ *         from the true residual near tight tolerances); bit 5 (FP64,
+ *         meshes registered with cgp_mesh_set_ogrid, rows in shared memory)
+ *         renumbers the rows into near-rectangular tiles of the O-grid's
+ *         (angle, ring) index grid, one per block, and forms every product
+ *         with the seven-point stencil on the block's padded box (no column
+ *         indices; bit 2 is then ignored); with bit 4 as well and at least
+ *         256 threads per block the tiles run the pipelined iteration
+ *         without a grid barrier in the loop: three warps poll every block's
+ *         tagged partial sums while the others form the next product, and
+ *         each block publishes its w behind a flag (release) that the blocks
+ *         reading its rows wait for (acquire, bounded; cgp_autotune does not
+ *         try this form); other bits must be 0.
  *         SpMV: bit 0 uses the O-grid stencil form (cgp_mesh_set_ogrid) with
  *         one thread per row (lanes ignored).
  * Invalid shapes are rejected with INVALID_ARG.  cgp_autotune sets these.

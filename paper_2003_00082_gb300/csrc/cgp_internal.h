@@ -146,6 +146,7 @@ struct cgp_mesh_impl {
   float* fpart = nullptr;    // [8 * max_blocks] FP32 partial sums
   double* part = nullptr;    // [max_blocks * 32] per-block fixed-point partial sums
   unsigned long long* tpart = nullptr;  // [2][3][max_blocks] tagged 128-bit partial sums
+  unsigned* nflag = nullptr; // [max_blocks] pipelined tiles: published-w counts of the blocks
   unsigned* bar = nullptr;   // grid barrier counter
   SolveResult* res = nullptr;
   SolveResult* h_res = nullptr;  // pinned host mirror

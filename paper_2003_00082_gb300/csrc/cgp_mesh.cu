@@ -295,7 +295,8 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
          o_bp = take(n * 8), o_r = take(n * 8), o_z = take(n * 8), o_p = take(n * 8), o_p2 = take(n * 8), o_q = take(n * 8),
          o_pub64 = take(18 * n * 8), o_f32pub = take(6 * n * 4), o_f32own = take(6 * n * 4),
          o_fpart = take((size_t)m->max_blocks * 8 * 4), o_part = take((size_t)m->max_blocks * 32 * 8),
-         o_tpart = take((size_t)m->max_blocks * 6 * 16), o_bar = take(256),
+         o_tpart = take((size_t)m->max_blocks * 6 * 16), o_nflag = take((size_t)m->max_blocks * 4),
+         o_bar = take(256),
          o_res = take(sizeof(SolveResult));
   m->d_bytes = off;
   cudaError_t e = cudaMalloc(&m->d_base, m->d_bytes);
@@ -330,6 +331,7 @@ extern "C" int cgp_assemble(const double* xy_c, int n_c, const int* tri_c, int t
   m->fpart = (float*)(base + o_fpart);
   m->part = (double*)(base + o_part);
   m->tpart = (unsigned long long*)(base + o_tpart);
+  m->nflag = (unsigned*)(base + o_nflag);
   m->bar = (unsigned*)(base + o_bar);
   m->res = (SolveResult*)(base + o_res);
   e = cudaMallocHost(&m->h_res, sizeof(SolveResult));

@@ -53,6 +53,8 @@ __global__ void __launch_bounds__(MAX_BLOCK) pcg_persistent_kernel(Desc d) {
     solve_mixed<T, RES>(d, blockIdx.x, sh);
   else if (d.classic)
     solve_fp64<T, RES>(d, blockIdx.x, sh);
+  else if (RES && d.pipelined && d.stencil)
+    solve_fp64_pl<T>(d, blockIdx.x, sh);
   else
     solve_fp64_sr<T, RES>(d, blockIdx.x, sh);
 }
@@ -135,6 +137,7 @@ struct LaunchPlan {
   int halo_cap = 0;
   bool res = false;
   bool stencil = false;   // resident O-grid tiles with the stencil product
+  bool pl = false;        // ... in the pipelined iteration (solve_fp64_pl)
   HaloPlan halo;
 };
 
@@ -505,6 +508,16 @@ size_t res_smem_stencil(int chunk, int max_halo, int box_cap) {
   return (s + 15) / 16 * 16;
 }
 
+// The same for the pipelined iteration on the tiles (solve_fp64_pl): eleven
+// vectors, the padded box, D^-1 of the halo and the seven planes; box
+// positions and product order of the rows, box positions and global rows of
+// the halo.
+size_t res_smem_stencil_pl(int chunk, int max_halo, int box_cap) {
+  const size_t s = 8 * ((size_t)18 * chunk + (size_t)box_cap + (size_t)max_halo) +
+                   4 * (2 * (size_t)chunk + 2 * (size_t)max_halo);
+  return (s + 15) / 16 * 16;
+}
+
 // Bound on the barrier epochs of one solve (the counter must stay below 2^31).
 long long max_epochs(const cgp_solve_opts& o) {
   return 16LL + 4LL * (long long)std::max(o.max_it, 1) + 8LL * std::max(o.max_sweeps, 1) + 8LL * 16;
@@ -537,9 +550,9 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
   out.nblk = nblk;
   out.block = block;
   // tuning flag bit 2: rows renumbered by coordinate bisection (compact chunks, smaller halos);
-  // bit 5 (FP64 single-reduction form on a registered O-grid): rows renumbered into index-grid
-  // tiles, whose resident product uses the seven-point stencil
-  const bool tiles = m && (tu.flags & 32) && !mixed && !(tu.flags & 18) && m->st_nt > 0;
+  // bit 5 (FP64 single-reduction or pipelined form on a registered O-grid): rows renumbered into
+  // index-grid tiles, whose resident product uses the seven-point stencil
+  const bool tiles = m && (tu.flags & 32) && !mixed && !(tu.flags & 2) && m->st_nt > 0;
   PermSystem* ps = nullptr;
   if (m && ((tu.flags & 4) || tiles)) {
     int st = get_perm_system(m, nblk, ps, tiles ? 1 : 0);
@@ -557,7 +570,10 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
       return CGP_OK;
     }
     const size_t limit = (size_t)std::max(0, optin_smem(device) - (int)fa.sharedSizeBytes - 1024);
-    const size_t smem = res_smem_stencil(chunk, ps->st_max_halo, ps->box_cap);
+    // bit 4 with the tiles: the pipelined iteration, given three polling warps and five computing ones
+    const bool pl = (tu.flags & 16) && block >= 256 && nblk <= 2048;
+    const size_t smem = pl ? res_smem_stencil_pl(chunk, ps->st_max_halo, ps->box_cap)
+                           : res_smem_stencil(chunk, ps->st_max_halo, ps->box_cap);
     if (smem > limit) return CGP_OK;
     if (cudaFuncSetAttribute((const void*)fnr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
@@ -570,6 +586,7 @@ int plan_solve(cgp_mesh_impl* m, int device, int n, int max_blocks, const Solver
     out.halo_cap = ps->st_max_halo;
     out.res = true;
     out.stencil = true;
+    out.pl = pl;
     return CGP_OK;
   }
   const int chunk = (n + nblk - 1) / nblk;
@@ -727,6 +744,8 @@ int launch_solve(cgp_mesh_impl* m, const double* b, double* x, const cgp_solve_o
       d.hptr = ps->st_hptr;
       d.hidx = ps->st_hidx;
       d.hpos = ps->st_hpos;
+      d.pipelined = plan.pl ? 1 : 0;
+      d.nflag = m->nflag;
     }
     perm_gather_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, ps->perm, b, x, o.use_x0, ps->bbuf, ps->xbuf);
     CGP_CUDA(cudaGetLastError());
@@ -1571,15 +1590,18 @@ extern "C" int cgp_autotune(cgp_mesh m, int precision, const double* b, double* 
   float best_t = 1e30f;
   // bit 1 (classic FP64 iteration), bit 4 (pipelined iteration, rows
   // resident, reductions always tagged) and bit 5 (O-grid tiles with the
-  // stencil product, single-reduction form, registered O-grids only) only for
-  // FP64; bit 2 (bisection order) and bit 3 (tagged reductions: of the
+  // stencil product, single-reduction form, registered O-grids only) only
+  // for FP64; bit 2 (bisection order) and bit 3 (tagged reductions: of the
   // single-reduction form, or of the FP32 inner iterations) for both
   std::vector<int> flag_set;
   for (int fl = 0; fl < 64; ++fl) {
     if (precision == CGP_MIXED && (fl & 50)) continue;   // mixed: bits 0, 2 and 3
     if ((fl & 2) && (fl & 8)) continue;
     if ((fl & 16) && (fl & 11)) continue;
-    if ((fl & 32) && ((fl & 23) || m->st_nt <= 0)) continue;
+    if ((fl & 32) && ((fl & 7) || m->st_nt <= 0)) continue;
+    // the pipelined iteration on the tiles (bits 4 and 5) ties the single-reduction tiles from x0 = 0
+    // and loses its margin to the restart from the true residual on warm starts: not a candidate
+    if ((fl & 48) == 48) continue;
     flag_set.push_back(fl);
   }
   for (int fl : flag_set)

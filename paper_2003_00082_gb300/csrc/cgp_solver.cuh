@@ -42,6 +42,7 @@ struct Desc {
   float* fpart;       // mixed: FP32 partial slots [2][NCOMP][part_stride]
   double* part;
   unsigned long long* tpart;  // FP64 single-reduction: tagged slots [2][3][part_stride] (128-bit)
+  unsigned* nflag;    // FP64 pipelined tiles: per block, the count of its published w (release)
   int part_stride;
   unsigned* bar;
   SolveResult* res;
@@ -51,8 +52,8 @@ struct Desc {
   int max_it, max_sweeps, use_x0, mixed;
   int classic;        // FP64: two barriers per iteration (Saad, Alg. 9.1) instead of the single-reduction form
   int tagged;         // FP64 single-reduction: reductions through tagged slots instead of the group barrier
-  int pipelined;      // FP64: pipelined iteration (kernels of cgp_pipe.cu; rows resident only)
-  int stencil;        // FP64 single-reduction, rows resident: O-grid tiles with the seven-point stencil product
+  int pipelined;      // FP64: pipelined iteration (CSR: kernels of cgp_pipe.cu; tiles: solve_fp64_pl; rows resident only)
+  int stencil;        // FP64, rows resident: O-grid tiles with the seven-point stencil product
   int box_cap;        // stencil: doubles of a block's padded box
   const double* planes;  // stencil: [7][n] coefficients (offsets as in stencil_offset)
   const int* bpos;    // stencil: [n] box position of every row
@@ -1276,6 +1277,402 @@ __device__ void solve_fp64_sr(const Desc& d, int lb, Shared& sh) {
       const double xi = x[i] - mxf;
       x[i] = xi;
       if (RES) d.x[r0 + i] = xi;
+    }
+    if (!grp.sync(sh)) return;
+  }
+  finish(d, lb, status, its, restarts, sqrt(rr_rec) / bnorm, sqrt(rr_true) / bnorm, bnorm);
+}
+
+// FP64 Jacobi-PCG in the pipelined form of Ghysels and Vanroose on O-grid
+// tiles (tuning flag bits 4 and 5, rows resident, at least 256 threads per
+// block): the product of an iteration is formed while the iteration's one
+// grid-wide reduction completes, so the reduction's latency hides behind
+// FP64 work instead of adding to it.
+//
+// With u = D^-1 r, w = K u, m = D^-1 w and n = K m, the recurrences
+//   z = n + beta z,  s = w + beta s,  r -= alpha s,  u = D^-1 r,
+//   w -= alpha z,    p = u + beta p,  x += alpha p
+// keep s = K p and z = K D^-1 s, and (r,u), (w,u), (r,r) are the scalars of
+// the single-reduction form.  Iteration k of a block:
+//   (A) all warps: z, s, r, u, w of the own rows with alpha_k, beta_k;
+//       w_(k+1) published; the partial sums of (r,u), (w,u), (r,r) stored
+//       in the block's tagged slots; the block's flag released (it counts
+//       the block's published w);
+//   (B) warps 0-2 poll every block's slots of their component, and thread 0
+//       derives alpha_(k+1), beta_(k+1); meanwhile the other warps put
+//       m = D^-1 w of the own rows into the box, form n = K m on the rows
+//       whose stencil stays inside the tile, update p_k and x_(k+1), wait
+//       (acquire) for the flags of the blocks that own the tile's halo, load
+//       their w, and form n on the tile's edge rows.
+// The loop has no grid barrier: the tagged slots carry the totals and the
+// flags the halo.  A block rewrites a copy of w (two, by parity) or a bank
+// of slots only after it has seen every block's partial sums of the
+// reduction in between, which every block stores after reading the older
+// copy.  The recurrences drift from b - K x sooner than the single-reduction
+// form's: convergence is confirmed on the true residual, and a loss of
+// positive alpha after the first iteration restarts from the true residual
+// (at most kMaxRestarts times in all).
+//
+// On GB300 the form is bound by the FP64 pipe: 19 FP64 operations per row
+// against the single-reduction form's 15 fill about 4.4 us of the iteration
+// at 512x256 on 152 blocks, and the neighbours' flags arrive about when the
+// tile's inner product ends, so the iteration (6.7 us) gains little on the
+// single-reduction form (6.9 us) and a restart near tol 1e-8 takes the rest.
+// It is selected with cgp_set_tuning only (cgp_autotune leaves it out).
+constexpr int kPlMinBlock = 256;   // three polling warps and at least five computing ones
+constexpr int kPlMaxNbr = 64;      // blocks owning a tile's halo rows (itself across the periodic seam)
+constexpr int kPlMaxBlocks = 2048; // blocks of a launch (the owners' bitmap)
+
+// Barrier of nthreads threads (whole warps) on barrier id (not 0, which
+// __syncthreads uses); the warp's lanes are reconverged first.
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  __syncwarp();
+  asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <int T>
+__device__ void solve_fp64_pl(const Desc& d, int lb, Shared& sh) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ int nbr[kPlMaxNbr];
+  __shared__ unsigned owners[kPlMaxBlocks / 32];
+  __shared__ int n_nbr, n_in, hflag;
+  const int tid = threadIdx.x, bd = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int chunk = (d.n + d.nblk - 1) / d.nblk;
+  const int r0 = min(d.n, lb * chunk), r1 = min(d.n, r0 + chunk), nloc = r1 - r0;
+  const size_t n = d.n;
+  int* const timeout = &d.res->timeout;
+  Group grp{d.bar, timeout, (unsigned)d.nblk, 0u, d.spin_ns};
+  int red = 0;
+  // published (global): r of a pass's first product; w by parity of the publication count
+  double* const R0 = d.pub64;
+  double* const W0 = d.pub64 + 2 * n;
+  double* const W1 = d.pub64 + 3 * n;
+  // shared memory: own vectors, seven coefficient planes, the padded box, D^-1 of the halo;
+  // box positions of the own rows, the rows in product order (inside the tile, then its
+  // edge), box positions and global rows of the halo entries
+  double* base = reinterpret_cast<double*>(dsm);
+  double* x = base;
+  double* r = base + chunk;
+  double* uA = base + 2 * chunk;   // u_k and u_(k+1) alternate
+  double* uB = base + 3 * chunk;
+  double* w = base + 4 * chunk;
+  double* p = base + 5 * chunk;
+  double* s = base + 6 * chunk;
+  double* z = base + 7 * chunk;
+  double* nv = base + 8 * chunk;
+  double* dil = base + 9 * chunk;
+  double* bp = base + 10 * chunk;
+  double* planes = base + 11 * chunk;
+  double* box = planes + 7 * chunk;
+  double* dih = box + d.box_cap;
+  int* spos = reinterpret_cast<int*>(dih + d.halo_cap);
+  int* ord = spos + chunk;
+  int* hpos = ord + chunk;
+  int* hid = hpos + d.halo_cap;
+  const int h0 = d.hptr[lb], nh = d.hptr[lb + 1] - h0;
+  const int Ba = d.bdim[lb];
+  if (!d.tpart || !d.nflag || bd < kPlMinBlock || d.nblk > kPlMaxBlocks || nh > d.halo_cap) {
+    finish(d, lb, CGP_ERR_INVALID_ARG, 0, 0, 0.0, 0.0, 0.0);
+    return;
+  }
+  for (int q = tid; q < d.box_cap; q += bd) box[q] = 0.0;
+  for (int k = 0; k < 7; ++k)
+    for (int i = tid; i < nloc; i += bd) planes[k * chunk + i] = d.planes[(size_t)k * n + r0 + i];
+  for (int i = tid; i < nloc; i += bd) {
+    spos[i] = d.bpos[r0 + i];
+    dil[i] = d.dinv[r0 + i];
+  }
+  for (int h = tid; h < nh; h += bd) {
+    const int j = d.hidx[h0 + h];
+    hpos[h] = d.hpos[h0 + h];
+    hid[h] = j;
+    dih[h] = d.dinv[j];
+  }
+  for (int q = tid; q < kPlMaxBlocks / 32; q += bd) owners[q] = 0u;
+  // this block's slots and flag start empty; the first group barrier orders
+  // that before any block reads them
+  if (tid < 6) *tag_slot(d, tid / 3, tid % 3, lb) = make_ulonglong2(0ull, 0ull);
+  if (tid == 0) d.nflag[lb] = 0u;
+  __syncthreads();
+  // rows whose seven box neighbours are all own rows (marked in the box), and
+  // the blocks that own the halo rows
+  for (int i = tid; i < nloc; i += bd) box[spos[i]] = 1.0;
+  for (int h = tid; h < nh; h += bd) {
+    const int o = hid[h] / chunk;
+    atomicOr(&owners[o >> 5], 1u << (o & 31));
+  }
+  __syncthreads();
+  const int o1 = stencil_offset(1, Ba), o2 = stencil_offset(2, Ba), o3 = stencil_offset(3, Ba);
+  const int o4 = stencil_offset(4, Ba), o5 = stencil_offset(5, Ba), o6 = stencil_offset(6, Ba);
+  if (warp == 0) {
+    const unsigned below = (1u << lane) - 1u;
+    int cnt = 0;
+    for (int pass = 0; pass < 2; ++pass) {   // the tile's inner rows, then its edge rows, each in row order
+      for (int b0 = 0; b0 < nloc; b0 += 32) {
+        const int i = b0 + lane;
+        bool take = false;
+        if (i < nloc) {
+          const int q = spos[i];
+          const bool inner = box[q + o1] == 1.0 && box[q + o2] == 1.0 && box[q + o3] == 1.0 &&
+                             box[q + o4] == 1.0 && box[q + o5] == 1.0 && box[q + o6] == 1.0;
+          take = pass == 0 ? inner : !inner;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        if (take) ord[cnt + __popc(bal & below)] = i;
+        cnt += __popc(bal);
+      }
+      if (pass == 0 && lane == 0) n_in = cnt;
+    }
+  } else if (warp == 1 && lane == 0) {
+    int c = 0;
+    for (int q = 0; q < (d.nblk + 31) / 32; ++q)
+      for (unsigned bits = owners[q]; bits; bits &= bits - 1u) {
+        if (c < kPlMaxNbr) nbr[c] = 32 * q + __ffs(bits) - 1;
+        ++c;
+      }
+    n_nbr = c;
+  }
+  __syncthreads();
+  if (n_nbr > kPlMaxNbr) {
+    finish(d, lb, CGP_ERR_INVALID_ARG, 0, 0, 0.0, 0.0, 0.0);
+    return;
+  }
+  for (int q = tid; q < d.box_cap; q += bd) box[q] = 0.0;   // the ring outside the domain stays zero
+  const int ni = n_in;
+
+  // the product's row i from the box (own values, halo values, zeros on the ring)
+  auto stencil_at = [&](int i) {
+    const int q = spos[i];
+    double a = planes[i] * box[q];
+    a = fma(planes[chunk + i], box[q + o1], a);
+    a = fma(planes[2 * chunk + i], box[q + o2], a);
+    a = fma(planes[3 * chunk + i], box[q + o3], a);
+    a = fma(planes[4 * chunk + i], box[q + o4], a);
+    a = fma(planes[5 * chunk + i], box[q + o5], a);
+    return fma(planes[6 * chunk + i], box[q + o6], a);
+  };
+
+  // ---- means of b and x0 ----
+  {
+    double v2[2] = {0.0, 0.0};
+    for (int i = tid; i < nloc; i += bd) {
+      v2[0] += d.b[r0 + i];
+      if (d.use_x0) v2[1] += d.x[r0 + i];
+    }
+    put_partials<2>(d, lb, red, v2, sh);
+    if (!grp.sync(sh)) return;
+    get_totals<2>(d, red, sh);
+    ++red;
+  }
+  // ---- projected b and x0; x0 published for the first product ----
+  {
+    const double mb = d.fixed ? 0.0 : sh.tot[0] / d.n, mx = d.fixed ? 0.0 : sh.tot[1] / d.n;
+    double v1[1] = {0.0};
+    for (int i = tid; i < nloc; i += bd) {
+      const double bi = is_fixed(d, r0 + i) ? 0.0 : d.b[r0 + i] - mb;
+      bp[i] = bi;
+      v1[0] += bi * bi;
+      const double xi = (d.use_x0 && !is_fixed(d, r0 + i)) ? d.x[r0 + i] - mx : 0.0;
+      x[i] = xi;
+      d.x[r0 + i] = xi;
+    }
+    red_start<1>(d, grp, lb, red, v1, sh);
+    if (!red_finish<1>(d, grp, red, sh)) return;
+    ++red;
+  }
+  const double bnorm = sqrt(sh.tot[0]);
+  if (!isfinite(bnorm)) { finish(d, lb, CGP_ERR_NONFINITE, 0, 0, 0.0, 0.0, bnorm); return; }
+  if (bnorm == 0.0) {
+    for (int i = tid; i < nloc; i += bd) d.x[r0 + i] = 0.0;
+    finish(d, lb, CGP_OK, 0, 0, 0.0, 0.0, 0.0);
+    return;
+  }
+  const double stop = d.tol * bnorm, stop2 = stop * stop;
+  if (tid == 0) sh.sc[4] = stop2;
+
+  int its = 0, restarts = 0, status = CGP_ERR_NOT_CONVERGED, pending = -1;
+  unsigned pub = 0;   // publications of w so far (the same count in every block)
+  double rr_rec = 0.0, rr_true = 0.0;
+  bool first = true;
+
+  // scalars of reduction kk (thread 0): sc[0] alpha, sc[1] beta, sc[2] gamma, sc[5] (r,r), isc[0]
+  // stop flag; sc[3] = 1 / gamma_old, sc[7] = 1 / (gamma_old alpha_old) come from thread 32
+  auto derive = [&](int kk) {
+    const double g = sh.tot[0], dl = sh.tot[1], rr = sh.tot[2];
+    int st = -1;
+    if (!finite_bits(g) || !finite_bits(dl) || !finite_bits(rr)) st = CGP_ERR_NONFINITE;
+    else if (nonneg_le(rr, sh.sc[4])) st = CGP_OK;
+    else if (its + kk >= d.max_it) st = CGP_ERR_NOT_CONVERGED;
+    double beta = 0.0, alpha;
+    if (kk == 0) {
+      alpha = g / dl;
+    } else {
+      beta = g * sh.sc[3];
+      alpha = g / fma(-g * g, sh.sc[7], dl);
+    }
+    if (st < 0 && !(positive_bits(g) && positive_bits(alpha) && finite_bits(alpha))) st = CGP_ERR_BREAKDOWN;
+    sh.isc[0] = st;
+    sh.sc[0] = alpha;
+    sh.sc[1] = beta;
+    sh.sc[2] = g;
+    sh.sc[5] = rr;
+  };
+  // (B) of reduction kk, whose partials the block has stored and whose w is the pub-th
+  // publication: warps 0-2 poll the slots, thread 0 derives; the other warps form n = K D^-1 w
+  // and, when px, p_(kk-1) and x_kk from u_(kk-1) (uc) with the previous scalars
+  auto phase_b = [&](int kk, bool px, double alpha, double beta, const double* uc) -> bool {
+    if (warp < 3) {
+      if (tid == 32 && kk > 0) {
+        sh.sc[3] = 1.0 / sh.sc[2];
+        sh.sc[6] = 1.0 / sh.sc[0];
+        sh.sc[7] = sh.sc[3] * sh.sc[6];
+      }
+      double t;
+      if (!tagged_total<kSlot64Shift>(d, red, warp, t)) {
+        if (lane == 0) sh.tflag = 0;
+      } else if (lane == 0) {
+        sh.tot[warp] = t;
+      }
+      named_sync(2, 96);
+      if (tid == 0 && sh.tflag) derive(kk);
+    } else {
+      const int t0 = tid - 96, nt = bd - 96;
+      const double* Wp = (pub & 1) ? W1 : W0;
+      for (int i = t0; i < nloc; i += nt) box[spos[i]] = dil[i] * w[i];
+      named_sync(1, nt);
+      for (int j = t0; j < ni; j += nt) {
+        const int i = ord[j];
+        nv[i] = stencil_at(i);
+      }
+      if (px) {
+        for (int i = t0; i < nloc; i += nt) {
+          const double pi = kk == 1 ? uc[i] : fma(beta, p[i], uc[i]);
+          p[i] = pi;
+          x[i] = fma(alpha, pi, x[i]);
+        }
+      }
+      if (t0 < n_nbr && !wait_at_least(d.nflag + nbr[t0], pub, timeout, d.spin_ns)) hflag = 0;
+      named_sync(1, nt);
+      if (hflag) {
+        for (int h = t0; h < nh; h += nt) box[hpos[h]] = dih[h] * __ldcg(Wp + hid[h]);
+        named_sync(1, nt);
+        for (int j = ni + t0; j < nloc; j += nt) {
+          const int i = ord[j];
+          nv[i] = stencil_at(i);
+        }
+      }
+    }
+    __syncthreads();
+    return sh.tflag && hflag;
+  };
+
+  while (true) {
+    // ---- true residual of the published x: r = bp - K x, u = D^-1 r; r published ----
+    {
+      double v1[1] = {0.0};
+      for (int i = tid; i < nloc; i += bd) box[spos[i]] = x[i];
+      for (int h = tid; h < nh; h += bd) box[hpos[h]] = __ldcg(d.x + hid[h]);
+      __syncthreads();
+      for (int i = tid; i < nloc; i += bd) {
+        const double t = bp[i] - stencil_at(i);
+        r[i] = t;
+        uA[i] = dil[i] * t;
+        R0[r0 + i] = t;
+        v1[0] += t * t;
+      }
+      red_start<1>(d, grp, lb, red, v1, sh);
+      if (!red_finish<1>(d, grp, red, sh)) return;   // also publishes r for the first product
+      ++red;
+    }
+    rr_true = sh.tot[0];
+    if (first) rr_rec = rr_true;
+    if (!isfinite(rr_true)) { status = CGP_ERR_NONFINITE; break; }
+    if (rr_true <= stop2) { status = CGP_OK; break; }
+    if (pending >= 0) { status = pending; break; }
+    if (its >= d.max_it || restarts >= kMaxRestarts) { status = CGP_ERR_NOT_CONVERGED; break; }
+    if (!first) ++restarts;
+    first = false;
+
+    // ---- w_0 = K u_0 (halo u_j = D^-1_j r_j), published; the first reduction and n_0 ----
+    {
+      ++pub;
+      double* Wp = (pub & 1) ? W1 : W0;
+      double v3[3] = {0.0, 0.0, 0.0};
+      for (int i = tid; i < nloc; i += bd) box[spos[i]] = uA[i];
+      for (int h = tid; h < nh; h += bd) box[hpos[h]] = dih[h] * __ldcg(R0 + hid[h]);
+      __syncthreads();
+      for (int i = tid; i < nloc; i += bd) {
+        const double a = stencil_at(i);
+        w[i] = a;
+        Wp[r0 + i] = a;
+        const double ui = uA[i], ri = r[i];
+        v3[0] += ri * ui;
+        v3[1] += a * ui;
+        v3[2] += ri * ri;
+      }
+      if (tid == 0) hflag = 1;
+      put_partials64<3>(d, lb, red, v3, sh);   // its block barrier also orders the box reads above
+      if (tid == 0) st_release_u32(d.nflag + lb, pub);
+    }
+    if (!phase_b(0, false, 0.0, 0.0, nullptr)) return;
+    ++red;
+    int k = 0;
+    double* uc = uA;   // u_k
+    double* un = uB;   // u_(k+1)
+    while (true) {
+      const int st = sh.isc[0];
+      if (st >= 0) {
+        if (st == CGP_ERR_BREAKDOWN && k > 0) break;   // the recurrences drifted: restart from the true residual
+        if (st != CGP_OK) pending = st;
+        break;
+      }
+      // (A) z_k, s_k, r_(k+1), u_(k+1), w_(k+1) of the own rows; w published; partials; flag
+      const double alpha = sh.sc[0], beta = sh.sc[1];
+      ++pub;
+      double* Wp = (pub & 1) ? W1 : W0;
+      double v3[3] = {0.0, 0.0, 0.0};
+      for (int i = tid; i < nloc; i += bd) {
+        const double zi = k == 0 ? nv[i] : fma(beta, z[i], nv[i]);
+        const double si = k == 0 ? w[i] : fma(beta, s[i], w[i]);
+        z[i] = zi;
+        s[i] = si;
+        const double ri = fma(-alpha, si, r[i]);
+        r[i] = ri;
+        const double ui = dil[i] * ri;
+        un[i] = ui;
+        const double wi = fma(-alpha, zi, w[i]);
+        w[i] = wi;
+        Wp[r0 + i] = wi;
+        v3[0] += ri * ui;
+        v3[1] += wi * ui;
+        v3[2] += ri * ri;
+      }
+      if (tid == 0) hflag = 1;
+      put_partials64<3>(d, lb, red, v3, sh);
+      if (tid == 0) st_release_u32(d.nflag + lb, pub);
+      // (B) n_(k+1), p_k and x_(k+1) while the reduction of iteration k + 1 completes
+      if (!phase_b(k + 1, true, alpha, beta, uc)) return;
+      ++red;
+      ++k;
+      double* t = uc;
+      uc = un;
+      un = t;
+    }
+    its += k;
+    rr_rec = sh.sc[5];
+    // ---- x -= mean(x), published for the true residual ----
+    {
+      double v1[1] = {0.0};
+      for (int i = tid; i < nloc; i += bd) v1[0] += x[i];
+      red_start<1>(d, grp, lb, red, v1, sh);
+      if (!red_finish<1>(d, grp, red, sh)) return;
+      ++red;
+    }
+    const double mxf = d.fixed ? 0.0 : sh.tot[0] / d.n;
+    for (int i = tid; i < nloc; i += bd) {
+      const double xi = x[i] - mxf;
+      x[i] = xi;
+      d.x[r0 + i] = xi;
     }
     if (!grp.sync(sh)) return;
   }

@@ -12,6 +12,10 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -40,17 +44,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Thread 0 of the block: wait for the `epoch`-th completion of the barrier
-// over nblk blocks (after this block's arrival); returns false when the wait
-// gave up.
-__device__ __forceinline__ bool barrier_wait(unsigned* bar, int* timeout, unsigned nblk, unsigned epoch,
-                                             long long spin_ns) {
-  const unsigned target = epoch * nblk;
+// One thread: wait until the word at p (which only grows) reaches target,
+// polling with acquire loads (the load that sees it is itself the acquire,
+// so no further round trip follows); false when the wait gave up after
+// spin_ns of wall-clock time or because another block gave up first.
+__device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned target, int* timeout, long long spin_ns) {
   unsigned long long t0 = 0;
   unsigned spins = 0;
-  // acquire on every poll: the load that sees the count complete is itself the
-  // acquire, so no further round trip follows it
-  while (ld_acquire(bar) < target) {
+  while (ld_acquire(p) < target) {
     if ((++spins & 127u) == 0) {
       if (*(volatile int*)timeout) return false;
       const unsigned long long now = global_ns();
@@ -63,6 +64,14 @@ __device__ __forceinline__ bool barrier_wait(unsigned* bar, int* timeout, unsign
     }
   }
   return true;
+}
+
+// Thread 0 of the block: wait for the `epoch`-th completion of the barrier
+// over nblk blocks (after this block's arrival); returns false when the wait
+// gave up.
+__device__ __forceinline__ bool barrier_wait(unsigned* bar, int* timeout, unsigned nblk, unsigned epoch,
+                                             long long spin_ns) {
+  return wait_at_least(bar, epoch * nblk, timeout, spin_ns);
 }
 
 // Thread 0 of the block: arrive, then wait as above.

@@ -173,7 +173,7 @@ SHAPES = [(128, 1, 1), (128, 2, 5), (128, 4, 3), (256, 8, 7), (64, 32, 2), (64, 
           (384, 4, 3)]
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 5, 6, 8, 9, 12, 13, 16, 20, 32, 40, 33])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4, 5, 6, 8, 9, 12, 13, 16, 20, 32, 40, 33, 48, 49])
 @pytest.mark.parametrize("block,lanes,blocks", SHAPES)
 def test_fp64_solve_matches_oracle(pair, cgp, block, lanes, blocks, flags):
     """Both FP64 iterations (bit 1: textbook, else single-reduction) in both storage modes (bit 0),
@@ -181,7 +181,8 @@ def test_fp64_solve_matches_oracle(pair, cgp, block, lanes, blocks, flags):
     single-reduction form's reductions behind the group barrier or through tagged slots (bit 3),
     the pipelined iteration (bit 4; with fewer than 256 threads or 8 or 32 lanes per row it runs
     the single-reduction form), and the O-grid tiles with the stencil product (bit 5, on the
-    registered O-grids; the CSR form elsewhere and when rows are not resident).
+    registered O-grids; the CSR form elsewhere and when rows are not resident), in the
+    single-reduction form or, with bit 4 and at least 256 threads, the pipelined one.
 
     The single-reduction form takes the same steps in exact arithmetic; its
     recurrences round differently, so its count may differ by a little more,
@@ -424,6 +425,7 @@ FULL_SIZE_SHAPES = {
     "fp64-152x512-bisection-pipelined": (0, 512, 1, 152, 20),
     # the O-grid tiles with the seven-point stencil product inside the resident solver
     "fp64-152x512-ogrid-tiles-tagged": (0, 512, 1, 152, 40),
+    "fp64-152x512-ogrid-tiles-pipelined": (0, 512, 1, 152, 48),
     "fp64-152x256-mesh-order-pipelined": (0, 256, 2, 152, 16),
     "fp64-default": (0, 0, 0, 0, 0),
     # the mixed shape the autotuner picks: one 512-thread block per SM, bisection order
@@ -630,7 +632,7 @@ def test_velocity_correction_matches_oracle(cgp, levels, name):
 # ----------------------------------------------------------------------------
 # far-field Dirichlet variant
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("precision,flags", [(0, 0), (0, 1), (0, 2), (1, 0), (0, 4), (1, 4), (0, 12), (0, 20), (0, 40)])
+@pytest.mark.parametrize("precision,flags", [(0, 0), (0, 1), (0, 2), (1, 0), (0, 4), (1, 4), (0, 12), (0, 20), (0, 40), (0, 48)])
 @pytest.mark.parametrize("name", ["square", "ogrid-7x3", "ogrid-33x17", "ogrid-64x32"])
 def test_far_field_dirichlet_solve_matches_oracle(cgp, name, precision, flags):
     xy, tri = meshes()[name]
