@@ -67,8 +67,8 @@ def workload_config(precision="fp64"):
 SOLVER_SOURCES = ("cgp_pcg.cu", "cgp_pcg_batch.cu", "cgp_pipe.cu", "cgp_solver.cuh", "cgp_sync.h", "cgp_fixed.h",
                   "cgp_internal.h")
 SOLVER_TRAFFIC = {
-    "sha256": "2bc5add2d51982cd3c52c3d2d1ca5824f6bf1c678c4003edf0f0df86d33ab555",
-    "fp64": 10377472 + 358144,
+    "sha256": "bd624dbe15e1ef9e4fd16d5f924229b690a886bbac437062f633aa27336c60dd",
+    "fp64": 10377984 + 335616,
     "flags": {"fp64": 40},
 }
 
